@@ -1,0 +1,375 @@
+"""Throughput benchmark of the two-fluid D3Q19 colour-gradient step.
+
+One bench "step" is one lattice time step (all of: pull streaming, moments,
+gradients, collision, perturbation, recolouring, store) over the whole
+lattice.  Workload (default): moving droplet in uniform flow, 128^3 periodic,
+radius 20, background velocity (0.05, 0, 0), density ratio 10, viscosity
+ratio 1, sigma = 0.005, beta = 0.7, FP32 storage and arithmetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage f32|f16|bf16] [--kernel fused|two_pass] [--n 128]
+
+Prints one JSON line.  `value` is whole-job MLUPS with the populations
+resident in HBM (inputs of 637 MB, larger than the 129 MB L2, so no flush is
+needed between steps); `e2e` is the same metric through the C ABI with host
+buffers (initial fields uploaded from pinned host memory, every step's FP64
+diagnostics read back, final moments downloaded, all inside the timed
+region).  Multi-GPU runs are independent replicas (one lattice per rank):
+the step has no cross-lattice exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS (two-fluid D3Q19) and % of HBM roofline; FP16-store vs FP32 "
+          "at stated error")
+BYTES_PER_VALUE = {"f32": 4, "f16": 2, "bf16": 2}
+
+
+def workload(n):
+    """Moving droplet in uniform flow (density ratio 10, sigma = 0.005)."""
+    return dict(nx=n, ny=n, nz=n, wall=(0, 0, 0), improved=True,
+                rho_in_R=10.0, rho_in_B=1.0, alpha_R=0.97, alpha_B=0.7,
+                tau_R=1.0, tau_B=1.0, tau_e=1.0, tau_q=1.0, tau_pi=1.0,
+                A_R=0.01125, A_B=0.01125, beta=0.7, delta=0.98,
+                force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0))
+
+
+def workload_fields(n):
+    from paper_1904_03618_gb300 import workloads
+    return workloads.droplet(n, n, n, 20.0 * n / 128.0, 10.0, 1.0,
+                             velocity=(0.05, 0.0, 0.0))
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+             "--format=csv,noheader,nounits", "-lms", "100"],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, storage, n):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (source hash recorded beside it)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fused_step_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("lbm_fused.cu", "lbm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
+    key = "%s_%s" % (kernel, storage)
+    if vals.get("source_sha256") != h.hexdigest()[:16] or key + "_bytes_per_cell" not in vals:
+        return None
+    return float(vals[key + "_bytes_per_cell"]) * n ** 3
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(n_sample, seconds):
+    """Time the FP64 oracle, as it stands, on the host cores on a bounded
+    sample of the workload (a smaller cube of the same case)."""
+    import oracle
+    from paper_1904_03618_gb300 import workloads
+    pd = workload(n_sample)
+    p = oracle.params_from(pd)
+    rR, rB, u = workloads.droplet(n_sample, n_sample, n_sample, 20.0 * n_sample / 128.0,
+                                  10.0, 1.0, velocity=(0.05, 0.0, 0.0))
+    f = oracle.init(p, rR, rB, u)
+    t0 = time.perf_counter()
+    f = oracle.step(p, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    f = oracle.step(p, f, steps)
+    dt = time.perf_counter() - t0
+    cells = n_sample ** 3 * steps
+    return {"value": cells / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d^3 lattice of the same case, %d steps, %.1f s" % (
+                n_sample, steps, dt)}, steps, dt
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores.  Each
+    bench step is one oracle time step on a cube of the same case whose size
+    is chosen so that warm-up plus timed steps take about two minutes."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1904_03618_gb300 import workloads
+    probe = 24
+    pp = oracle.params_from(workload(probe))
+    fr, fb, fu = workloads.droplet(probe, probe, probe, 20.0 * probe / 128.0, 10.0, 1.0,
+                                   velocity=(0.05, 0.0, 0.0))
+    fp = oracle.init(pp, fr, fb, fu)
+    t0 = time.perf_counter()
+    oracle.step(pp, fp, 2)
+    rate = 2 * probe ** 3 / (time.perf_counter() - t0)
+    budget = 120.0 / (args.steps + args.warmup)
+    ns = int(max(8, min(args.n, (rate * budget) ** (1.0 / 3.0))))
+    pd = workload(ns)
+    p = oracle.params_from(pd)
+    rR, rB, u = workloads.droplet(ns, ns, ns, 20.0 * ns / 128.0, 10.0, 1.0,
+                                  velocity=(0.05, 0.0, 0.0))
+    f = oracle.init(p, rR, rB, u)
+    for _ in range(args.warmup):
+        f = oracle.step(p, f, 1)
+    per_step = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        f = oracle.step(p, f, 1)
+        per_step.append(time.perf_counter() - t0)
+    mean = statistics.mean(per_step)
+    mlups = ns ** 3 / mean / 1e6
+    cb = {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(),
+          "kind": "oracle",
+          "sample": "each step: one FP64 oracle step on a %d^3 cube of the same case "
+                    "(%d steps timed)" % (ns, args.steps)}
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(args, world), "cpu_baseline": cb,
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_block(args, world):
+    return {"workload": "moving droplet in uniform flow, %d^3 periodic D3Q19 two-fluid, "
+                        "R=%g, u=(0.05,0,0), density ratio 10, viscosity ratio 1, "
+                        "sigma=0.005, beta=0.7" % (args.n, 20.0 * args.n / 128.0),
+            "lattice": [args.n, args.n, args.n], "storage": args.storage,
+            "kernel": args.kernel, "model": "improved (Eq. 18 + Eq. 45 correction)",
+            "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
+            "l2_policy": "inputs larger than L2 (%.0f MB populations)" % (
+                args.n ** 3 * 38 * BYTES_PER_VALUE[args.storage] / 1e6)}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1904_03618_gb300 import lbm
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = args.n
+    N = n ** 3
+    pd = workload(n)
+    params = lbm.make_params(storage=args.storage, kernel=args.kernel, **pd)
+    if args.storage != "f32":
+        params.ref_R, params.ref_B = 0.0, 1.0
+    rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in workload_fields(n))
+    stream = torch.cuda.Stream(dev)
+    lat = lbm.Lattice(params, device=dev, stream=stream)
+    lat.init_fields(rR, rB, u)
+    launches = lbm.lbm_launches_per_step(lat.ctx)
+
+    # --- device-resident throughput -------------------------------------
+    for _ in range(args.warmup):
+        lbm.lbm_step(lat.ctx, 1)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ
+                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        lbm.lbm_step(lat.ctx, 1)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    diag = lat.diagnostics(raise_unstable=False)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N / (ms_per_step * 1e-3) / 1e6
+
+    # --- end to end through the C ABI with host buffers -------------------
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    hR, hB, hu = pin(rR), pin(rB), pin(u)
+    oR = torch.empty(rR.shape, dtype=torch.float32).pin_memory()
+    oB = torch.empty(rB.shape, dtype=torch.float32).pin_memory()
+    ou = torch.empty(u.shape, dtype=torch.float32).pin_memory()
+    e2e_steps = max(args.steps // 4, 10)
+    lbm.lbm_init_fields(lat.ctx, hR, hB, hu)  # warm the staging buffers
+    lbm.lbm_moments(lat.ctx, oR, oB, ou)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lbm.lbm_init_fields(lat.ctx, hR, hB, hu)
+    for _ in range(e2e_steps):
+        lbm.lbm_step(lat.ctx, 1)
+        lbm.lbm_diagnostics(lat.ctx, raise_unstable=False)
+    lbm.lbm_moments(lat.ctx, oR, oB, ou)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * N * e2e_steps / e2e_s / 1e6
+    h2d = 5 * 4 * N / e2e_steps
+    d2h = (5 * 4 * N + e2e_steps * 12 * 8) / e2e_steps
+
+    # --- roofline of the dominant kernel --------------------------------
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 2 * 38 * BYTES_PER_VALUE[args.storage] * N  # read + write per launch
+    if launches == 1:
+        achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    else:
+        # two-pass: the collide kernel carries the same algorithmic bytes;
+        # attribute the whole step (both launches) to it
+        achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.kernel, args.storage, n)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, _, _ = cpu_oracle_sample(args.cpu_n, args.cpu_seconds)
+
+    lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": config_block(args, world),
+                "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "gpu_launches": args.steps * launches,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak,
+                             "traffic": traffic,
+                             "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind
+                             if peak_kind == "measured" else "fallback 6.8 TB/s",
+                             "algorithmic_bytes_per_cell": 2 * 38 * BYTES_PER_VALUE[args.storage],
+                             "kernel_ms": launch_ms},
+                "clocks": clocks,
+                "cpu_baseline": cpu,
+                "check": {"nonfinite_cells": diag[5], "negative_density_cells": diag[6],
+                          "mass_R": diag[0], "mass_B": diag[1]}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--cpu-n", type=int, default=48)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) implementation of the improved
+ * three-dimensional colour-gradient MRT lattice Boltzmann time step of
+ * Wen, Li, Yu & Luo, "Improved three-dimensional color-gradient lattice
+ * Boltzmann model for immiscible multiphase flows" (arXiv:1904.03618).
+ *
+ * The operation behind this interface is one time step of Eq. 1-2 for two
+ * fluids ("red" k = R and "blue" k = B) on the D3Q19 lattice of Eq. 5:
+ *   pull streaming (Sec. II.A, below Eq. 13), moments (Eq. 4), phase field
+ *   rho^N (below Eq. 8), isotropic colour and correction gradients (Eq. 49),
+ *   variable shear relaxation time (Eq. 52), MRT collision in moment space
+ *   with the improved equilibrium (Eq. 18-19, Appendix) and the correction
+ *   term (Eq. 41, 45-48), the surface-tension perturbation applied through
+ *   the collision matrix (Eq. 8, 53), and recolouring (Eq. 10-11).
+ *
+ * Conventions for every entry point:
+ *   - A lattice has nx * ny * nz cells, x fastest: cell = (z * ny + y) * nx + x.
+ *   - Scalar fields are float32 arrays of N = nx*ny*nz values; vector fields
+ *     are three consecutive planes (x, y, z components), 3*N values.
+ *   - Population arrays f_i^k are float32, layout [k][i][cell], k = 0 red,
+ *     1 blue, i = 0..18 in the order of Eq. 5: 38*N values.
+ *   - Pointers marked "host or device" may point to either; the library
+ *     detects which (CUDA unified addressing) and copies accordingly.
+ *     Caller-owned memory is only read or written during the call's stream
+ *     work and never retained.
+ *   - All work is ordered on the stream given to lbm_create.  Calls that
+ *     return data to a host pointer synchronise that stream before
+ *     returning; others return as soon as the work is queued.
+ *   - Every function returns an lbm_status; nothing aborts, traps or exits.
+ *     On failure lbm_last_error() describes the cause.
+ *   - Lattice units throughout: delta_x = delta_t = c = 1.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,      /* invalid argument or parameter                    */
+  LBM_ERR_OOM = -2,      /* device or host allocation failed                 */
+  LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                       */
+  LBM_ERR_UNSTABLE = -4, /* non-finite value or negative density detected    */
+  LBM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up               */
+  LBM_ERR_STATE = -6     /* call out of order (e.g. step before init)        */
+} lbm_status;
+
+typedef enum {
+  LBM_F32 = 0,  /* populations stored as float32                            */
+  LBM_F16 = 1,  /* stored as IEEE half deviations f - ref_k * phi_i^k         */
+  LBM_BF16 = 2  /* stored as bfloat16 deviations f - ref_k * phi_i^k          */
+} lbm_storage;
+
+typedef enum {
+  LBM_KERNEL_FUSED = 0,   /* one kernel per step: z-marching tile, halo moments
+                             recomputed in shared memory                     */
+  LBM_KERNEL_TWO_PASS = 1 /* two kernels per step: phase field and correction
+                             flux written to a scratch field, then collision */
+} lbm_kernel;
+
+/* Model and lattice parameters.  Defaults used by the paper are in
+   brackets; see the cited equations for meaning. */
+typedef struct {
+  int nx, ny, nz;      /* lattice size, each >= 1                            */
+  int wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on
+                          both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D  */
+  int improved;        /* 1: Eq. 18 equilibrium + Eq. 45 correction (the
+                          improved model); 0: Eq. 6, no correction (the
+                          "original model" of Sec. IV.A)                     */
+  int storage;         /* lbm_storage                                        */
+  int kernel;          /* lbm_kernel                                         */
+  int reserved0;       /* must be 0                                          */
+  double rho_in_R, rho_in_B; /* rho_k^in in rho^N, below Eq. 8 (> 0)         */
+  double alpha_R, alpha_B;   /* alpha_k of Eq. 13, in [0, 1)                 */
+  double tau_R, tau_B;       /* tau_v^R, tau_v^B of Eq. 52 (> 1/2)            */
+  double tau_e, tau_q, tau_pi; /* Eq. 44 [1.0] (> 1/2)                       */
+  double A_R, A_B;     /* Eq. 8; surface tension 2 (A_R + A_B) / 9 (Eq. 53)  */
+  double beta;         /* recolouring parameter of Eq. 10-11, in [0, 1]      */
+  double delta;        /* interface half-width of Eq. 52 [0.98], in (0, 1]   */
+  double force[3];     /* uniform body-force density (Sec. IV.B)             */
+  double gravity[3];   /* acceleration g; adds the force density rho * g
+                          (Sec. IV.C)                                        */
+  double ref_R, ref_B; /* reference densities of the FP16/BF16 deviation
+                          storage (ignored for LBM_F32): colour k is stored as
+                          f_i^k - ref_k * phi_i^k                            */
+} lbm_params;
+
+/* Creates a context: validates p, allocates the two population buffers and
+   scratch on the current CUDA device, and binds `cuda_stream` (a
+   cudaStream_t; NULL = the legacy default stream).  *out receives the
+   context; on failure *out is NULL.  Errors: LBM_ERR_ARG for an invalid p
+   (the message names the field), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_params *p, void *cuda_stream, lbm_ctx **out);
+
+/* Sets the populations to the equilibrium of each colour (Eq. 18, or Eq. 6
+   when improved = 0) for the given fields, as in the paper's initialisation
+   "brought to the equilibrium state" (Sec. IV.A).  rho_R, rho_B: N floats;
+   u: 3*N floats; all host or device.  solid must be NULL (walls are the
+   per-axis flags of lbm_params).  Resets the step counter to 0.
+   Errors: LBM_ERR_ARG (NULL field, non-NULL solid), LBM_ERR_CUDA. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, const float *rho_R,
+                           const float *rho_B, const float *u,
+                           const unsigned char *solid);
+
+/* Advances n >= 0 time steps (Eq. 1-2, Eq. 10-13, Eq. 40-53, streaming).
+   Queued on the context stream; returns without waiting.
+   Errors: LBM_ERR_ARG (n < 0), LBM_ERR_STATE (no init yet), LBM_ERR_CUDA. */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Writes the macroscopic fields at the current time level (after
+   streaming): rho_R, rho_B (N floats each) and u (3*N floats), with
+   u = (sum_i sum_k e_i f_i^k + F/2) / rho (Eq. 4, forcing shift), F the
+   total force density.  Any output pointer may be NULL to skip it; each is
+   host or device. */
+lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
+
+/* FP64 whole-lattice diagnostics into the host array out[16]:
+   [0] sum rho_R   [1] sum rho_B   [2..4] sum_i sum_k e_i f_i^k (momentum)
+   [5] count of cells with a non-finite population
+   [6] count of cells with rho_R < 0 or rho_B < 0
+   [7] max |u|     [8] count of cells with rho^N > 0
+   [9..11] red-mass centroid (sum rho_R x / sum rho_R, lattice coordinates,
+           no periodic unwrapping)
+   [12] number of completed steps   [13..15] 0 (reserved).
+   Synchronises the context stream.  Returns LBM_ERR_UNSTABLE if [5] or [6]
+   is non-zero (out is still filled). */
+lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[16]);
+
+/* Copies f_i^k(x, t) -- the populations after streaming at the current
+   time level, the paper's state variable -- as float32 [2][19][N] into f
+   (host or device), converting from the storage format. */
+lbm_status lbm_get_f(lbm_ctx *ctx, float *f);
+
+/* Sets the state from f_i^k(x, t) given as float32 [2][19][N] (host or
+   device), converting to the storage format.  Resets the step counter. */
+lbm_status lbm_set_f(lbm_ctx *ctx, const float *f);
+
+/* Size in bytes of one raw population buffer (the checkpoint unit). */
+size_t lbm_population_bytes(const lbm_ctx *ctx);
+
+/* Raw checkpoint of the current population buffer: dst (host or device)
+   receives lbm_population_bytes() bytes in the library's internal layout
+   (storage format, pull-streaming order).  Restoring it with
+   lbm_set_populations into a context created with the same parameters
+   resumes the run bit-identically.  The step counter is not part of it.
+   Both synchronise the context stream. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
+
+/* Number of kernel launches one lbm_step(ctx, 1) issues (1 for the fused
+   kernel, 2 for the two-pass form). */
+int lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* Releases everything the context owns.  NULL is allowed. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Text of the last error on ctx (never NULL; "" after success).  With
+   ctx == NULL, the last error of a failed lbm_create in this thread. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

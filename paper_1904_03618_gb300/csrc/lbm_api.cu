@@ -1,0 +1,454 @@
+// C ABI of the library (declared in include/lbm.h): parameter validation,
+// device memory, stream ordering, host/device pointer handling and error
+// reporting around the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::StepArgs;
+
+struct lbm_ctx {
+  lbm_params p;
+  StepArgs args;
+  lbm::FusedConfig fused;
+  cudaStream_t stream;
+  int device;
+  size_t elem;          // bytes per stored population value
+  long long N;          // cells
+  void* pop[2];         // ping-pong population buffers
+  int cur;              // buffer holding the current state (pull layout)
+  float4* phase;        // two-pass scratch: (rho^N, Qbar) per cell
+  double* diag_part;    // per-block partial sums of lbm_diagnostics
+  double* diag_out;     // folded sums (device)
+  int diag_blocks;
+  float* staging;       // device staging for host-pointer transfers
+  size_t staging_floats;
+  long long steps;
+  int initialized;
+  char err[512];
+};
+
+static thread_local char g_create_err[512];
+
+static lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
+  char* dst = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call, what)                       \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static lbm_status validate(const lbm_params* p) {
+  if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1)
+    return fail(nullptr, LBM_ERR_ARG, "nx, ny, nz must be >= 1");
+  for (int a = 0; a < 3; ++a)
+    if (p->wall[a] != 0 && p->wall[a] != 1)
+      return fail(nullptr, LBM_ERR_ARG, "wall[%d] must be 0 or 1", a);
+  if (p->improved != 0 && p->improved != 1)
+    return fail(nullptr, LBM_ERR_ARG, "improved must be 0 or 1");
+  if (p->storage < LBM_F32 || p->storage > LBM_BF16)
+    return fail(nullptr, LBM_ERR_ARG, "storage must be LBM_F32, LBM_F16 or LBM_BF16");
+  if (p->kernel != LBM_KERNEL_FUSED && p->kernel != LBM_KERNEL_TWO_PASS)
+    return fail(nullptr, LBM_ERR_ARG, "kernel must be LBM_KERNEL_FUSED or LBM_KERNEL_TWO_PASS");
+  if (p->reserved0 != 0) return fail(nullptr, LBM_ERR_ARG, "reserved0 must be 0");
+  if (!(p->rho_in_R > 0) || !(p->rho_in_B > 0))
+    return fail(nullptr, LBM_ERR_ARG, "rho_in_R and rho_in_B must be > 0");
+  if (!(p->alpha_R >= 0 && p->alpha_R < 1) || !(p->alpha_B >= 0 && p->alpha_B < 1))
+    return fail(nullptr, LBM_ERR_ARG, "alpha_R and alpha_B must lie in [0, 1)");
+  const double taus[5] = {p->tau_R, p->tau_B, p->tau_e, p->tau_q, p->tau_pi};
+  const char* names[5] = {"tau_R", "tau_B", "tau_e", "tau_q", "tau_pi"};
+  for (int i = 0; i < 5; ++i)
+    if (!(taus[i] > 0.5) || !isfinite(taus[i]))
+      return fail(nullptr, LBM_ERR_ARG, "%s must be finite and > 1/2", names[i]);
+  if (!(p->A_R >= 0) || !(p->A_B >= 0) || !isfinite(p->A_R) || !isfinite(p->A_B))
+    return fail(nullptr, LBM_ERR_ARG, "A_R and A_B must be finite and >= 0");
+  if (!(p->beta >= 0 && p->beta <= 1))
+    return fail(nullptr, LBM_ERR_ARG, "beta must lie in [0, 1]");
+  if (!(p->delta > 0 && p->delta <= 1))
+    return fail(nullptr, LBM_ERR_ARG, "delta must lie in (0, 1]");
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->force[a]) || !isfinite(p->gravity[a]))
+      return fail(nullptr, LBM_ERR_ARG, "force and gravity must be finite");
+  if (!isfinite(p->ref_R) || !isfinite(p->ref_B))
+    return fail(nullptr, LBM_ERR_ARG, "ref_R and ref_B must be finite");
+  long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > (1LL << 40)) return fail(nullptr, LBM_ERR_ARG, "lattice too large");
+  return LBM_OK;
+}
+
+static StepArgs derive_args(const lbm_params* p, long long plane) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.wx = p->wall[0];
+  a.wy = p->wall[1];
+  a.wz = p->wall[2];
+  a.plane = plane;
+  a.improved = p->improved;
+  a.inv_rin_R = (float)(1.0 / p->rho_in_R);
+  a.inv_rin_B = (float)(1.0 / p->rho_in_B);
+  double csR = 0.5 * (1.0 - p->alpha_R), csB = 0.5 * (1.0 - p->alpha_B);
+  a.cs2_R = (float)csR;
+  a.cs2_B = (float)csB;
+  a.q_R = (float)(1.0 - 3.0 * csR);
+  a.q_B = (float)(1.0 - 3.0 * csB);
+  a.tau_R = (float)p->tau_R;
+  a.tau_B = (float)p->tau_B;
+  double th = 2.0 * p->tau_R * p->tau_B / (p->tau_R + p->tau_B);
+  a.tau_h = (float)th;
+  a.par_a = (float)(2.0 * (p->tau_R - th) / p->delta);
+  a.par_b = (float)(2.0 * (th - p->tau_B) / p->delta);
+  a.delta = (float)p->delta;
+  a.s_e = (float)(1.0 / p->tau_e);
+  a.s_q = (float)(1.0 / p->tau_q);
+  a.s_pi = (float)(1.0 / p->tau_pi);
+  a.half_A = (float)(0.5 * (p->A_R + p->A_B));
+  a.beta = (float)p->beta;
+  a.fx = (float)p->force[0];
+  a.fy = (float)p->force[1];
+  a.fz = (float)p->force[2];
+  a.gx = (float)p->gravity[0];
+  a.gy = (float)p->gravity[1];
+  a.gz = (float)p->gravity[2];
+  if (p->storage != LBM_F32) {
+    a.offR0 = (float)(p->ref_R * p->alpha_R);
+    a.offR1 = (float)(p->ref_R * (1.0 - p->alpha_R) / 12.0);
+    a.offR2 = (float)(p->ref_R * (1.0 - p->alpha_R) / 24.0);
+    a.offB0 = (float)(p->ref_B * p->alpha_B);
+    a.offB1 = (float)(p->ref_B * (1.0 - p->alpha_B) / 12.0);
+    a.offB2 = (float)(p->ref_B * (1.0 - p->alpha_B) / 24.0);
+  }
+  return a;
+}
+
+static void release(lbm_ctx* c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (c->device >= 0) cudaSetDevice(c->device);
+  cudaFree(c->pop[0]);
+  cudaFree(c->pop[1]);
+  cudaFree(c->phase);
+  cudaFree(c->diag_part);
+  cudaFree(c->diag_out);
+  cudaFree(c->staging);
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+extern "C" lbm_status lbm_create(const lbm_params* p, void* cuda_stream,
+                                 lbm_ctx** out) {
+  g_create_err[0] = 0;
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  lbm_status st = validate(p);
+  if (st != LBM_OK) return st;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx;
+  if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+  memset(c, 0, sizeof(*c));
+  c->p = *p;
+  c->device = -1;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  c->elem = p->storage == LBM_F32 ? 4 : 2;
+  c->N = (long long)p->nx * p->ny * p->nz;
+  // Each (colour, direction) plane starts on a 256-byte boundary.
+  long long per = 256 / (long long)c->elem;
+  long long plane = (c->N + per - 1) / per * per;
+  c->args = derive_args(p, plane);
+  c->fused = lbm::default_fused_config(c->args, p->storage);
+  size_t bytes = (size_t)plane * 38 * c->elem;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&c->pop[b], bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      release(c);
+      delete c;
+      return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+  }
+  if (p->kernel == LBM_KERNEL_TWO_PASS) {
+    e = cudaMalloc(&c->phase, sizeof(float4) * (size_t)c->N);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      release(c);
+      delete c;
+      return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the phase field failed");
+    }
+  }
+  long long nb = (c->N + 255) / 256;
+  c->diag_blocks = (int)(nb < 4 * 152 ? nb : 4 * 152);
+  if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
+      cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess) {
+    cudaGetLastError();
+    release(c);
+    delete c;
+    return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
+  }
+  c->err[0] = 0;
+  *out = c;
+  return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  release(c);
+  delete c;
+}
+
+extern "C" const char* lbm_last_error(const lbm_ctx* c) {
+  return c ? c->err : g_create_err;
+}
+
+static lbm_status ensure_staging(lbm_ctx* c, size_t floats) {
+  if (c->staging_floats >= floats) return LBM_OK;
+  cudaFree(c->staging);
+  c->staging = nullptr;
+  c->staging_floats = 0;
+  if (cudaMalloc(&c->staging, floats * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LBM_ERR_OOM, "cudaMalloc of %zu staging floats failed", floats);
+  }
+  c->staging_floats = floats;
+  return LBM_OK;
+}
+
+// Makes `n` floats at `ptr` (host or device) readable by kernels: returns
+// ptr itself for device memory, else a staging copy at `slot` floats.
+static lbm_status device_input(lbm_ctx* c, const float* ptr, size_t n,
+                               size_t slot, const float** out) {
+  if (is_device_ptr(ptr)) {
+    *out = ptr;
+    return LBM_OK;
+  }
+  LBM_CUDA(c, cudaMemcpyAsync(c->staging + slot, ptr, n * sizeof(float),
+                              cudaMemcpyHostToDevice, c->stream),
+           "cudaMemcpyAsync H2D");
+  *out = c->staging + slot;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init_fields(lbm_ctx* c, const float* rho_R,
+                                      const float* rho_B, const float* u,
+                                      const unsigned char* solid) {
+  if (!c) return LBM_ERR_ARG;
+  if (!rho_R || !rho_B || !u) return fail(c, LBM_ERR_ARG, "NULL field pointer");
+  if (solid) return fail(c, LBM_ERR_ARG, "solid masks are not supported; use wall[]");
+  size_t N = (size_t)c->N;
+  bool all_dev = is_device_ptr(rho_R) && is_device_ptr(rho_B) && is_device_ptr(u);
+  if (!all_dev) {
+    lbm_status st = ensure_staging(c, 5 * N);
+    if (st != LBM_OK) return st;
+  }
+  const float *dR, *dB, *dU;
+  lbm_status st;
+  if ((st = device_input(c, rho_R, N, 0, &dR)) != LBM_OK) return st;
+  if ((st = device_input(c, rho_B, N, N, &dB)) != LBM_OK) return st;
+  if ((st = device_input(c, u, 3 * N, 2 * N, &dU)) != LBM_OK) return st;
+  LBM_CUDA(c, lbm::launch_init_eq(c->p.storage, c->pop[0], c->args,
+                                  (float)c->p.alpha_R, (float)c->p.alpha_B, dR,
+                                  dB, dU, c->stream),
+           "init kernel");
+  c->cur = 0;
+  c->steps = 0;
+  c->initialized = 1;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+static lbm_status step_once(lbm_ctx* c) {
+  const void* src = c->pop[c->cur];
+  void* dst = c->pop[c->cur ^ 1];
+  cudaError_t e;
+  if (c->p.kernel == LBM_KERNEL_TWO_PASS)
+    e = lbm::launch_twopass(c->p.storage, src, dst, c->args, c->phase, c->stream);
+  else
+    e = lbm::launch_fused(c->p.storage, src, dst, c->args, c->fused, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  c->cur ^= 1;
+  c->steps += 1;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
+  if (!c) return LBM_ERR_ARG;
+  if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_f");
+  for (int s = 0; s < n; ++s) {
+    lbm_status st = step_once(c);
+    if (st != LBM_OK) return st;
+  }
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
+                                  float* u) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_moments before init");
+  size_t N = (size_t)c->N;
+  float* outs[3] = {rho_R, rho_B, u};
+  size_t sizes[3] = {N, N, 3 * N};
+  size_t slots[3] = {0, N, 2 * N};
+  bool host[3];
+  bool any_host = false;
+  for (int k = 0; k < 3; ++k) {
+    host[k] = outs[k] && !is_device_ptr(outs[k]);
+    any_host = any_host || host[k];
+  }
+  if (any_host) {
+    lbm_status st = ensure_staging(c, 5 * N);
+    if (st != LBM_OK) return st;
+  }
+  float* k_out[3];
+  for (int k = 0; k < 3; ++k)
+    k_out[k] = !outs[k] ? nullptr : (host[k] ? c->staging + slots[k] : outs[k]);
+  LBM_CUDA(c, lbm::launch_moments(c->p.storage, c->pop[c->cur], c->args,
+                                  k_out[0], k_out[1], k_out[2], c->stream),
+           "moments kernel");
+  for (int k = 0; k < 3; ++k)
+    if (host[k])
+      LBM_CUDA(c, cudaMemcpyAsync(outs[k], k_out[k], sizes[k] * sizeof(float),
+                                  cudaMemcpyDeviceToHost, c->stream),
+               "cudaMemcpyAsync D2H");
+  if (any_host) LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
+  if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_diagnostics before init");
+  LBM_CUDA(c, lbm::launch_diag(c->p.storage, c->pop[c->cur], c->args,
+                               c->diag_part, c->diag_blocks, c->diag_out,
+                               c->stream),
+           "diagnostics kernels");
+  double d[lbm::kDiagSlots];
+  LBM_CUDA(c, cudaMemcpyAsync(d, c->diag_out, sizeof(d), cudaMemcpyDeviceToHost,
+                              c->stream),
+           "cudaMemcpyAsync D2H");
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  for (int i = 0; i < 16; ++i) out[i] = 0.0;
+  for (int i = 0; i < lbm::kDiagSlots; ++i) out[i] = d[i];
+  if (d[0] > 0) {
+    out[9] = d[9] / d[0];
+    out[10] = d[10] / d[0];
+    out[11] = d[11] / d[0];
+  }
+  out[12] = (double)c->steps;
+  c->err[0] = 0;
+  if (d[5] != 0.0 || d[6] != 0.0)
+    return fail(c, LBM_ERR_UNSTABLE,
+                "%.0f cells with non-finite populations, %.0f with negative density",
+                d[5], d[6]);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_f(lbm_ctx* c, float* f) {
+  if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_get_f before init");
+  size_t n = 38 * (size_t)c->N;
+  if (is_device_ptr(f)) {
+    LBM_CUDA(c, lbm::launch_get_f(c->p.storage, c->pop[c->cur], c->args, f, c->stream),
+             "get_f kernel");
+  } else {
+    lbm_status st = ensure_staging(c, n);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(c, lbm::launch_get_f(c->p.storage, c->pop[c->cur], c->args,
+                                  c->staging, c->stream),
+             "get_f kernel");
+    LBM_CUDA(c, cudaMemcpyAsync(f, c->staging, n * sizeof(float),
+                                cudaMemcpyDeviceToHost, c->stream),
+             "cudaMemcpyAsync D2H");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  }
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_f(lbm_ctx* c, const float* f) {
+  if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
+  size_t n = 38 * (size_t)c->N;
+  const float* src = f;
+  if (!is_device_ptr(f)) {
+    lbm_status st = ensure_staging(c, n);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(c, cudaMemcpyAsync(c->staging, f, n * sizeof(float),
+                                cudaMemcpyHostToDevice, c->stream),
+             "cudaMemcpyAsync H2D");
+    src = c->staging;
+  }
+  LBM_CUDA(c, lbm::launch_set_f(c->p.storage, c->pop[0], c->args, src, c->stream),
+           "set_f kernel");
+  c->cur = 0;
+  c->steps = 0;
+  c->initialized = 1;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" size_t lbm_population_bytes(const lbm_ctx* c) {
+  return c ? (size_t)c->args.plane * 38 * c->elem : 0;
+}
+
+extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
+  if (!c || !dst) return c ? fail(c, LBM_ERR_ARG, "dst is NULL") : LBM_ERR_ARG;
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_get_populations before init");
+  LBM_CUDA(c, cudaMemcpyAsync(dst, c->pop[c->cur], lbm_population_bytes(c),
+                              cudaMemcpyDefault, c->stream),
+           "cudaMemcpyAsync");
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
+  if (!c || !src) return c ? fail(c, LBM_ERR_ARG, "src is NULL") : LBM_ERR_ARG;
+  LBM_CUDA(c, cudaMemcpyAsync(c->pop[0], src, lbm_population_bytes(c),
+                              cudaMemcpyDefault, c->stream),
+           "cudaMemcpyAsync");
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  c->cur = 0;
+  c->initialized = 1;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
+  if (!c) return 0;
+  return c->p.kernel == LBM_KERNEL_TWO_PASS ? 2 : 1;
+}

@@ -1,0 +1,485 @@
+// Device-side building blocks of the colour-gradient MRT-LB step
+// (Wen, Li, Yu & Luo, arXiv:1904.03618) for sm_103a.
+//
+// The collision is written for the total population f = f^R + f^B: the
+// relaxation matrix S (Eq. 44) depends only on the cell's phase field, so
+// summing Eq. 41 over the two colours gives one 19-moment update
+//   m* = m - S (m - sum_k m^{k,eq}) + (I - S/2)(sum_k C^k + F_hat) + S P_hat
+// followed by f* = f + M^-1 (m* - m) (Eq. 42, 12, 53).  All moment-space
+// quantities are closed forms of the raw-moment basis of Eq. 43:
+//   m^eq   Appendix rows 0-15; rows 16-18 as M f^eq (the printed rows 16-18
+//          differ from M f^eq at O(u^2); the paper defines m^eq = M f^eq);
+//          third-order rows carry p_k u (Eq. 19), i.e. the Eq. 18 high-order
+//          term with coefficient 3 (the printed 3/2 gives half of Eq. 19);
+//   C      Eq. 45-48, rows 4-6 only;
+//   F_hat  M times the Guo forcing term (force density F, u shifted by F/2);
+//   P_hat  M times the summed perturbation of Eq. 8, executed through S as
+//          Eq. 53 prescribes.
+// M^-1 is applied in its sparse closed form (99 non-zeros).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Step arguments, derived on the host from lbm_params.
+// ---------------------------------------------------------------------------
+struct StepArgs {
+  int nx, ny, nz;
+  int wx, wy, wz;           // wall flags per axis
+  long long plane;          // elements per (colour, direction) plane
+  int improved;
+  int pad0;
+  float inv_rin_R, inv_rin_B;   // 1 / rho_k^in (below Eq. 8)
+  float cs2_R, cs2_B;           // (c_s^k)^2 = (1 - alpha_k) / 2 (Eq. 13)
+  float q_R, q_B;               // 1 - 3 (c_s^k)^2 (below Eq. 49)
+  float tau_R, tau_B;           // Eq. 52 end values
+  float tau_h;                  // 2 tau_R tau_B / (tau_R + tau_B)
+  float par_a, par_b;           // slopes of g^R, g^B at rho^N = 0
+  float delta;                  // Eq. 52
+  float s_e, s_q, s_pi;         // 1/tau_e, 1/tau_q, 1/tau_pi (Eq. 44)
+  float half_A;                 // (A_R + A_B) / 2, Eq. 8 summed over colours
+  float beta;                   // Eq. 10-11
+  float fx, fy, fz;             // uniform force density
+  float gx, gy, gz;             // gravity
+  // deviation storage offsets ref_k * phi_i^k for (rest, axis, diagonal)
+  float offR0, offR1, offR2, offB0, offB1, offB2;
+};
+
+// ---------------------------------------------------------------------------
+// D3Q19 lattice of Eq. 5, as compile-time functions of the direction index.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ex(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+// Opposite pairs are (1,2), (3,4), ..., (17,18).
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+}
+// 0 = rest, 1 = axis (|e| = 1), 2 = diagonal (|e| = sqrt 2)
+__host__ __device__ constexpr int shell(int i) {
+  return i == 0 ? 0 : (i <= 6 ? 1 : 2);
+}
+
+// ---------------------------------------------------------------------------
+// Storage formats.  FP32 stores f itself; FP16 / BF16 store the deviation
+// f - ref_k phi_i^k and are converted to FP32 on load.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Store;
+
+template <>
+struct Store<float> {
+  static constexpr bool kDeviation = false;
+  __device__ __forceinline__ static float load(const float* p) {
+    return __ldg(p);
+  }
+  __device__ __forceinline__ static void store(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool kDeviation = true;
+  __device__ __forceinline__ static float load(const __half* p) {
+    return __half2float(__ldg(p));
+  }
+  __device__ __forceinline__ static void store(__half* p, float v) {
+    *p = __float2half_rn(v);
+  }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr bool kDeviation = true;
+  __device__ __forceinline__ static float load(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  __device__ __forceinline__ static void store(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+};
+
+template <int I>
+__device__ __forceinline__ float dev_offset(const StepArgs& a, int k) {
+  constexpr int s = shell(I);
+  if (k == 0) return s == 0 ? a.offR0 : (s == 1 ? a.offR1 : a.offR2);
+  return s == 0 ? a.offB0 : (s == 1 ? a.offB1 : a.offB2);
+}
+
+// ---------------------------------------------------------------------------
+// Indexing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap1(int v, int n) {
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+__device__ __forceinline__ long long cell_of(const StepArgs& a, int x, int y,
+                                             int z) {
+  return ((long long)z * a.ny + y) * a.nx + x;
+}
+__device__ __forceinline__ long long pidx(const StepArgs& a, int k, int i,
+                                          long long cell) {
+  return ((long long)(k * 19 + i)) * a.plane + cell;
+}
+
+// Pull streaming (Sec. II.A, below Eq. 13): f_i^k(x, t) = f_i^{k,+}(x - e_i,
+// t - 1), periodic wrap; where x - e_i lies beyond a wall, halfway
+// bounce-back gives f_i^k(x, t) = f_{opp(i)}^{k,+}(x, t - 1).
+template <typename T, int I>
+__device__ __forceinline__ void pull_one(const T* __restrict__ src,
+                                         const StepArgs& a, int x, int y,
+                                         int z, long long c, float* fR,
+                                         float* fB) {
+  int xs = x - ex(I), ys = y - ey(I), zs = z - ez(I);
+  bool out = (a.wx && (xs < 0 || xs >= a.nx)) ||
+             (a.wy && (ys < 0 || ys >= a.ny)) ||
+             (a.wz && (zs < 0 || zs >= a.nz));
+  long long cs;
+  int d;
+  if (out) {
+    cs = c;
+    d = opp(I);
+  } else {
+    cs = cell_of(a, wrap1(xs, a.nx), wrap1(ys, a.ny), wrap1(zs, a.nz));
+    d = I;
+  }
+  float r = Store<T>::load(src + pidx(a, 0, d, cs));
+  float b = Store<T>::load(src + pidx(a, 1, d, cs));
+  if (Store<T>::kDeviation) {
+    // the offset belongs to the stored direction, which has the same shell
+    r += dev_offset<I>(a, 0);
+    b += dev_offset<I>(a, 1);
+  }
+  fR[I] = r;
+  fB[I] = b;
+}
+
+template <typename T, int I>
+struct PullAll {
+  __device__ __forceinline__ static void run(const T* __restrict__ src,
+                                             const StepArgs& a, int x, int y,
+                                             int z, long long c, float* fR,
+                                             float* fB) {
+    pull_one<T, I>(src, a, x, y, z, c, fR, fB);
+    PullAll<T, I + 1>::run(src, a, x, y, z, c, fR, fB);
+  }
+};
+template <typename T>
+struct PullAll<T, 19> {
+  __device__ __forceinline__ static void run(const T* __restrict__,
+                                             const StepArgs&, int, int, int,
+                                             long long, float*, float*) {}
+};
+
+template <typename T>
+__device__ __forceinline__ void pull_cell(const T* __restrict__ src,
+                                          const StepArgs& a, int x, int y,
+                                          int z, float* fR, float* fB) {
+  PullAll<T, 0>::run(src, a, x, y, z, cell_of(a, x, y, z), fR, fB);
+}
+
+// Store of the post-recolouring populations at the cell itself (the next
+// step pulls them).
+template <typename T>
+__device__ __forceinline__ void store_cell(T* __restrict__ dst,
+                                           const StepArgs& a, long long c,
+                                           const float* fR, const float* fB) {
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    float r = fR[i], b = fB[i];
+    if (Store<T>::kDeviation) {
+      const int s = shell(i);
+      r -= s == 0 ? a.offR0 : (s == 1 ? a.offR1 : a.offR2);
+      b -= s == 0 ? a.offB0 : (s == 1 ? a.offB1 : a.offB2);
+    }
+    Store<T>::store(dst + pidx(a, 0, i, c), r);
+    Store<T>::store(dst + pidx(a, 1, i, c), b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cell macroscopics (Eq. 4 with the forcing shift; rho^N below Eq. 8).
+// ---------------------------------------------------------------------------
+struct Macro {
+  float rR, rB, rho, inv_rho, ux, uy, uz, Fx, Fy, Fz;
+};
+
+__device__ __forceinline__ Macro macro_of(const StepArgs& a, const float* fR,
+                                          const float* fB) {
+  Macro m;
+  float rR = 0.f, rB = 0.f;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    rR += fR[i];
+    rB += fB[i];
+  }
+  float f[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
+  float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) +
+             (f[13] - f[14]);
+  float jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) +
+             (f[17] - f[18]);
+  float jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) +
+             (f[15] - f[16]) + (f[18] - f[17]);
+  m.rR = rR;
+  m.rB = rB;
+  m.rho = rR + rB;
+  m.inv_rho = 1.0f / m.rho;
+  m.Fx = a.fx + m.rho * a.gx;
+  m.Fy = a.fy + m.rho * a.gy;
+  m.Fz = a.fz + m.rho * a.gz;
+  m.ux = (jx + 0.5f * m.Fx) * m.inv_rho;
+  m.uy = (jy + 0.5f * m.Fy) * m.inv_rho;
+  m.uz = (jz + 0.5f * m.Fz) * m.inv_rho;
+  return m;
+}
+
+__device__ __forceinline__ float phase_field(const StepArgs& a, float rR,
+                                             float rB) {
+  float r = rR * a.inv_rin_R, b = rB * a.inv_rin_B;
+  return (r - b) / (r + b);
+}
+
+// Sum over colours of rho_k (1 - 3 c_s^k^2): Qbar_alpha = u_alpha * this.
+__device__ __forceinline__ float qbar_scale(const StepArgs& a, float rR,
+                                            float rB) {
+  return a.q_R * rR + a.q_B * rB;
+}
+
+// Eq. 52 with the parabolic g^R, g^B (continuous, zero slope at +-delta,
+// harmonic mean at rho^N = 0).
+__device__ __forceinline__ float tau_v_of(const StepArgs& a, float rn) {
+  if (rn > a.delta) return a.tau_R;
+  if (rn > 0.f) return a.tau_h + rn * (a.par_a - a.par_a * rn / (2.f * a.delta));
+  if (rn >= -a.delta)
+    return a.tau_h + rn * (a.par_b + a.par_b * rn / (2.f * a.delta));
+  return a.tau_B;
+}
+
+// ---------------------------------------------------------------------------
+// Collision + perturbation + recolouring of one cell.  On entry fR, fB hold
+// the pulled populations; on exit the post-recolouring f^{k,+}.
+// grad = grad rho^N and Q = (d_x Qbar_x, d_y Qbar_y, d_z Qbar_z), both from
+// the Eq. 49 stencil.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
+                                             float* fB, const Macro& mc,
+                                             float rhoN, float Gx, float Gy,
+                                             float Gz, float Qx, float Qy,
+                                             float Qz) {
+  float f[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
+  const float rho = mc.rho, ux = mc.ux, uy = mc.uy, uz = mc.uz;
+  const float Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
+
+  // raw moments of Eq. 43, rows 4..18
+  const float a12 = f[1] + f[2], a34 = f[3] + f[4], a56 = f[5] + f[6];
+  const float Sxy = (f[7] + f[8]) + (f[9] + f[10]);
+  const float Sxz = (f[11] + f[12]) + (f[13] + f[14]);
+  const float Syz = (f[15] + f[16]) + (f[17] + f[18]);
+  float m[19];
+  m[4] = a12 + a34 + a56 + 2.f * (Sxy + Sxz + Syz);
+  m[5] = 2.f * a12 - a34 - a56 + Sxy + Sxz - 2.f * Syz;
+  m[6] = a34 - a56 + Sxy - Sxz;
+  m[7] = (f[7] + f[8]) - (f[9] + f[10]);
+  m[8] = (f[11] + f[12]) - (f[13] + f[14]);
+  m[9] = (f[15] + f[16]) - (f[17] + f[18]);
+  m[10] = (f[7] - f[8]) - (f[9] - f[10]);
+  m[11] = (f[7] - f[8]) + (f[9] - f[10]);
+  m[12] = (f[11] - f[12]) - (f[13] - f[14]);
+  m[13] = (f[11] - f[12]) + (f[13] - f[14]);
+  m[14] = (f[15] - f[16]) - (f[17] - f[18]);
+  m[15] = (f[15] - f[16]) + (f[17] - f[18]);
+  m[16] = Sxy;
+  m[17] = Sxz;
+  m[18] = Syz;
+
+  // equilibria summed over colours; p = sum_k rho_k (c_s^k)^2
+  const float p = a.cs2_R * mc.rR + a.cs2_B * mc.rB;
+  const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+  const float pc = a.improved ? p : rho * (1.0f / 3.0f);
+  float e[19];
+  e[4] = 3.f * p + rho * (ux2 + uy2 + uz2);
+  e[5] = rho * (2.f * ux2 - uy2 - uz2);
+  e[6] = rho * (uy2 - uz2);
+  e[7] = rho * ux * uy;
+  e[8] = rho * ux * uz;
+  e[9] = rho * uy * uz;
+  e[10] = pc * uy;
+  e[11] = pc * ux;
+  e[12] = pc * uz;
+  e[13] = pc * ux;
+  e[14] = pc * uz;
+  e[15] = pc * uy;
+  const float twop = 2.f * p;
+  e[16] = (twop + rho * (2.f * ux2 + 2.f * uy2 - uz2)) * (1.0f / 6.0f);
+  e[17] = (twop + rho * (2.f * ux2 + 2.f * uz2 - uy2)) * (1.0f / 6.0f);
+  e[18] = (twop + rho * (2.f * uy2 + 2.f * uz2 - ux2)) * (1.0f / 6.0f);
+
+  // source in moment space: correction C (rows 4-6) + Guo force F_hat
+  const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz;
+  float src[19];
+  src[4] = 2.f * (Fux + Fuy + Fuz);
+  src[5] = 2.f * (2.f * Fux - Fuy - Fuz);
+  src[6] = 2.f * (Fuy - Fuz);
+  if (a.improved) {
+    src[4] += Qx + Qy + Qz;
+    src[5] += 2.f * Qx - Qy - Qz;
+    src[6] += Qy - Qz;
+  }
+  src[7] = Fx * uy + Fy * ux;
+  src[8] = Fx * uz + Fz * ux;
+  src[9] = Fy * uz + Fz * uy;
+  const float third = 1.0f / 3.0f;
+  src[10] = Fy * third;
+  src[11] = Fx * third;
+  src[12] = Fz * third;
+  src[13] = Fx * third;
+  src[14] = Fz * third;
+  src[15] = Fy * third;
+  src[16] = (2.f * Fux + 2.f * Fuy - Fuz) * third;
+  src[17] = (2.f * Fux + 2.f * Fuz - Fuy) * third;
+  src[18] = (2.f * Fuy + 2.f * Fuz - Fux) * third;
+
+  // perturbation moments (A/2)|G| pi(n), pi from M applied to Eq. 8
+  const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+  const bool has_g = G2 >= 1e-24f;
+  const float ig = has_g ? rsqrtf(G2) : 0.f;
+  const float hA = a.half_A;
+  float P4 = 0.f, P5 = 0.f, P6 = 0.f, P7 = 0.f, P8 = 0.f, P9 = 0.f, P16 = 0.f,
+        P17 = 0.f, P18 = 0.f;
+  if (has_g) {
+    const float k29 = hA * ig * (2.0f / 9.0f);
+    const float k19 = hA * ig * (1.0f / 9.0f);
+    const float Gx2 = Gx * Gx, Gy2 = Gy * Gy, Gz2 = Gz * Gz;
+    P4 = -(4.0f / 9.0f) * hA * (G2 * ig);
+    P5 = k29 * (2.f * Gx2 - Gy2 - Gz2);
+    P6 = k29 * (Gy2 - Gz2);
+    P7 = k29 * Gx * Gy;
+    P8 = k29 * Gx * Gz;
+    P9 = k29 * Gy * Gz;
+    P16 = -k19 * Gz2;
+    P17 = -k19 * Gy2;
+    P18 = -k19 * Gx2;
+  }
+
+  // relaxation rates (Eq. 44) with the variable tau_v of Eq. 52
+  const float s_v = 1.0f / tau_v_of(a, rhoN);
+  const float s_e = a.s_e, s_q = a.s_q, s_pi = a.s_pi;
+
+  // change of moments dm = m* - m (rows 1-3: F; row 0: 0)
+  float d[19];
+  d[4] = -s_e * (m[4] - e[4]) + (1.f - 0.5f * s_e) * src[4] + s_e * P4;
+#pragma unroll
+  for (int r = 5; r <= 9; ++r)
+    d[r] = -s_v * (m[r] - e[r]) + (1.f - 0.5f * s_v) * src[r];
+  d[5] += s_v * P5;
+  d[6] += s_v * P6;
+  d[7] += s_v * P7;
+  d[8] += s_v * P8;
+  d[9] += s_v * P9;
+#pragma unroll
+  for (int r = 10; r <= 15; ++r)
+    d[r] = -s_q * (m[r] - e[r]) + (1.f - 0.5f * s_q) * src[r];
+#pragma unroll
+  for (int r = 16; r <= 18; ++r)
+    d[r] = -s_pi * (m[r] - e[r]) + (1.f - 0.5f * s_pi) * src[r];
+  d[16] += s_pi * P16;
+  d[17] += s_pi * P17;
+  d[18] += s_pi * P18;
+  d[1] = Fx;
+  d[2] = Fy;
+  d[3] = Fz;
+
+  // f* = f + M^-1 dm (sparse closed form of the inverse of Eq. 43)
+  const float h = 0.5f, q = 0.25f;
+  const float c46 = d[4] * (1.0f / 6.0f);
+  const float c5a = d[5] * (1.0f / 6.0f), c5b = d[5] * (1.0f / 12.0f);
+  const float c6 = d[6] * 0.25f;
+  float fs[19];
+  fs[0] = f[0] - d[4] + d[16] + d[17] + d[18];
+  {
+    const float base = c46 + c5a - h * (d[16] + d[17]);
+    const float odd = h * (d[1] - d[11] - d[13]);
+    fs[1] = f[1] + base + odd;
+    fs[2] = f[2] + base - odd;
+  }
+  {
+    const float base = c46 - c5b + c6 - h * (d[16] + d[18]);
+    const float odd = h * (d[2] - d[10] - d[15]);
+    fs[3] = f[3] + base + odd;
+    fs[4] = f[4] + base - odd;
+  }
+  {
+    const float base = c46 - c5b - c6 - h * (d[17] + d[18]);
+    const float odd = h * (d[3] - d[12] - d[14]);
+    fs[5] = f[5] + base + odd;
+    fs[6] = f[6] + base - odd;
+  }
+  fs[7] = f[7] + q * (d[7] + d[10] + d[11] + d[16]);
+  fs[8] = f[8] + q * (d[7] - d[10] - d[11] + d[16]);
+  fs[9] = f[9] + q * (-d[7] - d[10] + d[11] + d[16]);
+  fs[10] = f[10] + q * (-d[7] + d[10] - d[11] + d[16]);
+  fs[11] = f[11] + q * (d[8] + d[12] + d[13] + d[17]);
+  fs[12] = f[12] + q * (d[8] - d[12] - d[13] + d[17]);
+  fs[13] = f[13] + q * (-d[8] - d[12] + d[13] + d[17]);
+  fs[14] = f[14] + q * (-d[8] + d[12] - d[13] + d[17]);
+  fs[15] = f[15] + q * (d[9] + d[14] + d[15] + d[18]);
+  fs[16] = f[16] + q * (d[9] - d[14] - d[15] + d[18]);
+  fs[17] = f[17] + q * (-d[9] - d[14] + d[15] + d[18]);
+  fs[18] = f[18] + q * (-d[9] + d[14] - d[15] + d[18]);
+
+  // recolouring, Eq. 10-11: f^{R,+} = (rho_R/rho) f* + seg_i,
+  // f^{B,+} = (rho_B/rho) f* - seg_i, seg_i = beta rho_R rho_B / rho^2
+  // cos(phi_i) sum_k rho_k phi_i^k; sum_k rho_k phi_i^k = p/6 on the axes and
+  // p/12 on the diagonals, cos(phi_i) = e_i.n / |e_i|.
+  const float wr = mc.rR * mc.inv_rho, wb = mc.rB * mc.inv_rho;
+  float nx = 0.f, ny = 0.f, nz = 0.f, cax = 0.f, cdg = 0.f;
+  if (has_g) {
+    nx = Gx * ig;
+    ny = Gy * ig;
+    nz = Gz * ig;
+    const float cb = a.beta * wr * wb * p;
+    cax = cb * (1.0f / 6.0f);
+    cdg = cb * (1.0f / (12.0f * 1.41421356237309515f));
+  }
+  float sg[19];
+  sg[0] = 0.f;
+  sg[1] = cax * nx;
+  sg[2] = -sg[1];
+  sg[3] = cax * ny;
+  sg[4] = -sg[3];
+  sg[5] = cax * nz;
+  sg[6] = -sg[5];
+  sg[7] = cdg * (nx + ny);
+  sg[8] = -sg[7];
+  sg[9] = cdg * (nx - ny);
+  sg[10] = -sg[9];
+  sg[11] = cdg * (nx + nz);
+  sg[12] = -sg[11];
+  sg[13] = cdg * (nx - nz);
+  sg[14] = -sg[13];
+  sg[15] = cdg * (ny + nz);
+  sg[16] = -sg[15];
+  sg[17] = cdg * (ny - nz);
+  sg[18] = -sg[17];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    fR[i] = wr * fs[i] + sg[i];
+    fB[i] = wb * fs[i] - sg[i];
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,269 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_lib/liblbm.so`` built by ``__graft_entry__.build()``.  If that
+library is missing this module raises on import -- there is no CPU fallback.
+
+Functions carry the C names (``lbm_create``, ``lbm_init_fields``,
+``lbm_step``, ``lbm_moments``, ``lbm_diagnostics``, ``lbm_get_f``,
+``lbm_set_f``, ``lbm_get_populations``, ``lbm_set_populations``,
+``lbm_destroy``, ``lbm_last_error``); :class:`Lattice` is a small
+convenience wrapper holding a context, its torch stream and output tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise RuntimeError(
+        "CUDA library %s is missing: run __graft_entry__.build() first "
+        "(there is no CPU fallback)" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA = 0, -1, -2, -3
+LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6
+LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2
+LBM_KERNEL_FUSED, LBM_KERNEL_TWO_PASS = 0, 1
+STORAGE = {"f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+
+
+class LbmParams(ctypes.Structure):
+    """Mirror of ``lbm_params``."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("wall", ctypes.c_int * 3),
+        ("improved", ctypes.c_int), ("storage", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("reserved0", ctypes.c_int),
+        ("rho_in_R", ctypes.c_double), ("rho_in_B", ctypes.c_double),
+        ("alpha_R", ctypes.c_double), ("alpha_B", ctypes.c_double),
+        ("tau_R", ctypes.c_double), ("tau_B", ctypes.c_double),
+        ("tau_e", ctypes.c_double), ("tau_q", ctypes.c_double),
+        ("tau_pi", ctypes.c_double),
+        ("A_R", ctypes.c_double), ("A_B", ctypes.c_double),
+        ("beta", ctypes.c_double), ("delta", ctypes.c_double),
+        ("force", ctypes.c_double * 3), ("gravity", ctypes.c_double * 3),
+        ("ref_R", ctypes.c_double), ("ref_B", ctypes.c_double),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("lbm status %d: %s" % (status, message))
+        self.status = status
+
+
+_ctx_p = ctypes.c_void_p
+_fp = ctypes.c_void_p
+
+_lib.lbm_create.argtypes = [ctypes.POINTER(LbmParams), ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_void_p)]
+_lib.lbm_create.restype = ctypes.c_int
+_lib.lbm_init_fields.argtypes = [_ctx_p, _fp, _fp, _fp, _fp]
+_lib.lbm_init_fields.restype = ctypes.c_int
+_lib.lbm_step.argtypes = [_ctx_p, ctypes.c_int]
+_lib.lbm_step.restype = ctypes.c_int
+_lib.lbm_moments.argtypes = [_ctx_p, _fp, _fp, _fp]
+_lib.lbm_moments.restype = ctypes.c_int
+_lib.lbm_diagnostics.argtypes = [_ctx_p, ctypes.POINTER(ctypes.c_double)]
+_lib.lbm_diagnostics.restype = ctypes.c_int
+_lib.lbm_get_f.argtypes = [_ctx_p, _fp]
+_lib.lbm_get_f.restype = ctypes.c_int
+_lib.lbm_set_f.argtypes = [_ctx_p, _fp]
+_lib.lbm_set_f.restype = ctypes.c_int
+_lib.lbm_population_bytes.argtypes = [_ctx_p]
+_lib.lbm_population_bytes.restype = ctypes.c_size_t
+_lib.lbm_get_populations.argtypes = [_ctx_p, _fp]
+_lib.lbm_get_populations.restype = ctypes.c_int
+_lib.lbm_set_populations.argtypes = [_ctx_p, _fp]
+_lib.lbm_set_populations.restype = ctypes.c_int
+_lib.lbm_launches_per_step.argtypes = [_ctx_p]
+_lib.lbm_launches_per_step.restype = ctypes.c_int
+_lib.lbm_destroy.argtypes = [_ctx_p]
+_lib.lbm_destroy.restype = None
+_lib.lbm_last_error.argtypes = [_ctx_p]
+_lib.lbm_last_error.restype = ctypes.c_char_p
+
+EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
+            "lbm_diagnostics", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
+            "lbm_get_populations", "lbm_set_populations",
+            "lbm_launches_per_step", "lbm_destroy", "lbm_last_error")
+
+
+def lbm_last_error(ctx) -> str:
+    msg = _lib.lbm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def _check(ctx, status):
+    if status != LBM_OK:
+        raise LbmError(status, lbm_last_error(ctx))
+
+
+def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
+                kernel="fused", rho_in_R=1.0, rho_in_B=1.0, alpha_R=1.0 / 3.0,
+                alpha_B=1.0 / 3.0, tau_R=1.0, tau_B=1.0, tau_e=1.0, tau_q=1.0,
+                tau_pi=1.0, A_R=0.0, A_B=0.0, beta=0.7, delta=0.98,
+                force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), ref_R=0.0,
+                ref_B=0.0, **_ignored) -> LbmParams:
+    p = LbmParams()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    for a in range(3):
+        p.wall[a] = int(wall[a])
+        p.force[a] = float(force[a])
+        p.gravity[a] = float(gravity[a])
+    p.improved = 1 if improved else 0
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.kernel = {"fused": LBM_KERNEL_FUSED, "two_pass": LBM_KERNEL_TWO_PASS}[kernel] \
+        if isinstance(kernel, str) else int(kernel)
+    p.reserved0 = 0
+    p.rho_in_R, p.rho_in_B = float(rho_in_R), float(rho_in_B)
+    p.alpha_R, p.alpha_B = float(alpha_R), float(alpha_B)
+    p.tau_R, p.tau_B = float(tau_R), float(tau_B)
+    p.tau_e, p.tau_q, p.tau_pi = float(tau_e), float(tau_q), float(tau_pi)
+    p.A_R, p.A_B = float(A_R), float(A_B)
+    p.beta, p.delta = float(beta), float(delta)
+    p.ref_R, p.ref_B = float(ref_R), float(ref_B)
+    return p
+
+
+def _addr(x):
+    """Address of a torch tensor, numpy array or raw integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array arguments must be C-contiguous")
+        return x.ctypes.data
+    return int(x)
+
+
+def lbm_create(params: LbmParams, stream=None):
+    ctx = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream) if stream else None
+    st = _lib.lbm_create(ctypes.byref(params), s, ctypes.byref(ctx))
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
+    return ctx
+
+
+def lbm_init_fields(ctx, rho_R, rho_B, u, solid=None):
+    _check(ctx, _lib.lbm_init_fields(ctx, _addr(rho_R), _addr(rho_B), _addr(u),
+                                     _addr(solid)))
+
+
+def lbm_step(ctx, n=1):
+    _check(ctx, _lib.lbm_step(ctx, int(n)))
+
+
+def lbm_moments(ctx, rho_R, rho_B, u):
+    _check(ctx, _lib.lbm_moments(ctx, _addr(rho_R), _addr(rho_B), _addr(u)))
+
+
+def lbm_diagnostics(ctx, raise_unstable=True):
+    out = (ctypes.c_double * 16)()
+    st = _lib.lbm_diagnostics(ctx, out)
+    if st != LBM_OK and (raise_unstable or st != LBM_ERR_UNSTABLE):
+        raise LbmError(st, lbm_last_error(ctx))
+    return np.array(out[:], dtype=np.float64)
+
+
+def lbm_get_f(ctx, f):
+    _check(ctx, _lib.lbm_get_f(ctx, _addr(f)))
+
+
+def lbm_set_f(ctx, f):
+    _check(ctx, _lib.lbm_set_f(ctx, _addr(f)))
+
+
+def lbm_population_bytes(ctx) -> int:
+    return int(_lib.lbm_population_bytes(ctx))
+
+
+def lbm_get_populations(ctx, dst):
+    _check(ctx, _lib.lbm_get_populations(ctx, _addr(dst)))
+
+
+def lbm_set_populations(ctx, src):
+    _check(ctx, _lib.lbm_set_populations(ctx, _addr(src)))
+
+
+def lbm_launches_per_step(ctx) -> int:
+    return int(_lib.lbm_launches_per_step(ctx))
+
+
+def lbm_destroy(ctx):
+    _lib.lbm_destroy(ctx)
+
+
+class Lattice:
+    """One lattice on one device, bound to the current torch stream of that
+    device at construction."""
+
+    def __init__(self, params: LbmParams, device=None, stream=None):
+        self.device = torch.device(device or "cuda")
+        self.params = params
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            self.ctx = lbm_create(params, self.stream.cuda_stream)
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+
+    def _t(self, x):
+        if isinstance(x, torch.Tensor):
+            return x.to(device=self.device, dtype=torch.float32).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
+                               device=self.device)
+
+    def init_fields(self, rho_R, rho_B, u):
+        rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        lbm_init_fields(self.ctx, rR, rB, uu)
+        self._keep = (rR, rB, uu)  # alive until the queued kernel has read them
+        self.stream.synchronize()
+
+    def set_f(self, f):
+        ft = self._t(f)
+        lbm_set_f(self.ctx, ft)
+        self.stream.synchronize()
+
+    def get_f(self):
+        out = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
+        lbm_get_f(self.ctx, out)
+        self.stream.synchronize()
+        return out
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def moments(self):
+        rR = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        rB = torch.empty_like(rR)
+        u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        lbm_moments(self.ctx, rR, rB, u)
+        self.stream.synchronize()
+        return rR, rB, u
+
+    def diagnostics(self, raise_unstable=True):
+        return lbm_diagnostics(self.ctx, raise_unstable)
+
+    def close(self):
+        if self.ctx is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

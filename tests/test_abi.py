@@ -1,0 +1,77 @@
+"""The C ABI library loads and exports every entry point include/*.h
+declares; host-side parameter validation runs without a GPU."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1904_03618_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(lbm_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
+                 "lbm_diagnostics", "lbm_destroy", "lbm_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(lbm.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """Compile a probe against include/lbm.h with the host C compiler and
+    compare sizeof and every field offset with the ctypes mirror."""
+    fields = [f[0] for f in lbm.LbmParams._fields_]
+    src = tmp_path / "probe.c"
+    body = "".join('printf("%%s %%zu\\n", "%s", offsetof(lbm_params, %s));' % (f, f)
+                   for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
+                   'int main(void){printf("sizeof %%zu\\n", sizeof(lbm_params));%s'
+                   'return 0;}\n' % body)
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    out = dict(line.split() for line in
+               subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(out["sizeof"]) == ctypes.sizeof(lbm.LbmParams)
+    for f in fields:
+        assert int(out[f]) == getattr(lbm.LbmParams, f).offset, f
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("tau_R", 0.5, "tau_R"), ("tau_q", 0.2, "tau_q"), ("beta", 1.5, "beta"),
+    ("delta", 0.0, "delta"), ("alpha_B", 1.0, "alpha"), ("rho_in_R", 0.0, "rho_in"),
+    ("nx", 0, "nx"), ("storage", 7, "storage"), ("kernel", 5, "kernel"),
+])
+def test_invalid_parameters_are_rejected_on_the_host(field, value, msg):
+    p = lbm.make_params(8, 8, 8)
+    setattr(p, field, value)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(p)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    assert msg in str(ei.value)
+
+
+def test_null_context_calls_do_not_crash():
+    assert lbm._lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lbm._lib.lbm_moments(None, None, None, None) == lbm.LBM_ERR_ARG
+    assert lbm._lib.lbm_population_bytes(None) == 0
+    lbm.lbm_destroy(None)

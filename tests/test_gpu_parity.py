@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are seeded, rounded to float32 once, and given to both sides, so the
+only difference is the arithmetic.  Bars (stated by the target, checked
+here): per-step relative L-infinity error of the populations <= 1e-5 in
+FP32; density and velocity relative L2 error <= 1e-4 after 1000 steps, the
+velocity error being normalised by max(||u_oracle||_2, U_ref sqrt(N)) with
+U_ref = 1e-3 for the static droplet, whose only velocities are the spurious
+currents.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_03618_gb300 import lbm, workloads as wl
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+KERNELS = ["fused", "two_pass"]
+
+
+def base(nx, ny, nz, **kw):
+    d = dict(nx=nx, ny=ny, nz=nz, wall=(0, 0, 0), improved=True, rho_in_R=3.0,
+             rho_in_B=1.0, alpha_R=0.9, alpha_B=0.7, tau_R=0.8, tau_B=1.1,
+             tau_e=1.0, tau_q=0.95, tau_pi=1.05, A_R=0.01, A_B=0.01, beta=0.7,
+             delta=0.98, force=(2e-5, 0.0, 0.0), gravity=(0.0, 0.0, -1e-5))
+    d.update(kw)
+    return d
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def gpu_run(pd, f0, nsteps, kernel="fused"):
+    lat = lbm.Lattice(lbm.make_params(kernel=kernel, **pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    lat.step(nsteps)
+    out = lat.get_f().double().cpu().numpy()
+    lat.close()
+    return out
+
+
+def rel_linf(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def droplet_state(pd, radius, velocity=(0.0, 0.0, 0.0), noise=1e-3, seed=0):
+    rR, rB, u = wl.droplet(pd["nx"], pd["ny"], pd["nz"], radius, pd["rho_in_R"],
+                           pd["rho_in_B"], velocity=velocity, noise=noise, seed=seed)
+    return f32(oracle.init(oracle.params_from(pd), rR, rB, u))
+
+
+CASES = {
+    # several 30 x 6 fused tiles with ragged tails in x and y, z walls
+    "droplet_zwalls": (base(67, 23, 11, wall=(0, 0, 1)), 5.0, (0.02, 0.01, 0.0)),
+    # every axis periodic, moving droplet across the periodic seam
+    "droplet_periodic": (base(40, 13, 9, tau_R=0.6, tau_B=1.3), 4.0, (0.03, 0.0, 0.01)),
+    # walls everywhere, original model
+    "original_all_walls": (base(35, 17, 8, wall=(1, 1, 1), improved=False), 5.0, (0.0, 0.0, 0.0)),
+    # walls in x only, odd sizes
+    "xwalls_odd": (base(31, 8, 7, wall=(1, 0, 0)), 3.0, (0.0, 0.02, 0.0)),
+}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_one_step_parity(case, kernel):
+    pd, R, vel = CASES[case]
+    f0 = droplet_state(pd, R, vel)
+    ref = oracle.step(oracle.params_from(pd), f0, 1)
+    got = gpu_run(pd, f0, 1, kernel)
+    assert rel_linf(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_every_cell_at_an_interface(kernel):
+    pd = base(37, 14, 6, wall=(0, 1, 0))
+    rR, rB, u = wl.random_fields(37, 14, 6, seed=3)
+    f0 = f32(oracle.init(oracle.params_from(pd), rR, rB, u))
+    ref = oracle.step(oracle.params_from(pd), f0, 3)
+    assert rel_linf(gpu_run(pd, f0, 3, kernel), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_far_from_equilibrium_populations(kernel):
+    pd = base(33, 9, 5, wall=(0, 0, 1))
+    f0 = f32(wl.random_populations(33, 9, 5, seed=4))
+    ref = oracle.step(oracle.params_from(pd), f0, 1)
+    assert rel_linf(gpu_run(pd, f0, 1, kernel), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("shape,wall", [((1, 1, 1), (0, 0, 0)), ((3, 2, 1), (0, 0, 0)),
+                                        ((2, 5, 3), (1, 0, 0)), ((5, 7, 3), (1, 1, 1)),
+                                        ((1, 6, 1), (0, 1, 0))])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_tiny_and_degenerate_lattices(shape, wall, kernel):
+    nx, ny, nz = shape
+    pd = base(nx, ny, nz, wall=wall)
+    rR, rB, u = wl.random_fields(nx, ny, nz, seed=5)
+    f0 = f32(oracle.init(oracle.params_from(pd), rR, rB, u))
+    ref = oracle.step(oracle.params_from(pd), f0, 2)
+    assert rel_linf(gpu_run(pd, f0, 2, kernel), ref) <= 1e-5
+
+
+def test_zero_steps_and_initial_equilibrium():
+    pd = base(20, 12, 7)
+    rR, rB, u = wl.droplet(20, 12, 7, 4.0, 3.0, 1.0, velocity=(0.03, -0.02, 0.01))
+    rR, rB, u = f32(rR), f32(rB), f32(u)
+    ref = oracle.init(oracle.params_from(pd), rR, rB, u)
+    lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+    lat.init_fields(rR, rB, u)
+    lat.step(0)
+    got = lat.get_f().double().cpu().numpy()
+    lat.close()
+    assert rel_linf(got, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_moments_match_oracle(kernel):
+    pd = base(26, 11, 9, wall=(0, 0, 1))
+    f0 = droplet_state(pd, 4.0, (0.02, 0.0, 0.0))
+    p = oracle.params_from(pd)
+    f1 = oracle.step(p, f0, 2)
+    rR, rB, u = oracle.moments(p, f1)
+    lat = lbm.Lattice(lbm.make_params(kernel=kernel, **pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    lat.step(2)
+    gR, gB, gu = (t.double().cpu().numpy() for t in lat.moments())
+    lat.close()
+    assert rel_linf(gR, rR) <= 1e-5 and rel_linf(gB, rB) <= 1e-5
+    assert np.abs(gu - u).max() <= 1e-5 * max(np.abs(u).max(), 1e-2)
+
+
+def test_fused_and_two_pass_agree_over_many_steps():
+    pd = base(45, 20, 16, wall=(0, 1, 0))
+    f0 = droplet_state(pd, 6.0, (0.02, 0.0, 0.0))
+    a = gpu_run(pd, f0, 50, "fused")
+    b = gpu_run(pd, f0, 50, "two_pass")
+    assert rel_linf(a, b) <= 1e-5
+
+
+def test_thousand_steps_static_droplet():
+    """32^3 periodic static droplet (R = 8, ratio 1, sigma = 0.01, beta =
+    0.7), with +-1e-3 density noise: 1000 steps against the oracle."""
+    n = 32
+    pd = base(n, n, n, rho_in_R=1.0, rho_in_B=1.0, alpha_R=1 / 3, alpha_B=1 / 3,
+              tau_R=1.0, tau_B=1.0, tau_q=1.0, tau_pi=1.0, A_R=0.0225, A_B=0.0225,
+              beta=0.7, force=(0, 0, 0), gravity=(0, 0, 0))
+    f0 = droplet_state(pd, 8.0, noise=1e-3, seed=0)
+    p = oracle.params_from(pd)
+    ref = oracle.step(p, f0, 1000)
+    rR, rB, u = oracle.moments(p, ref)
+    lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    lat.step(1000)
+    gR, gB, gu = (t.double().cpu().numpy() for t in lat.moments())
+    lat.close()
+    rho, grho = rR + rB, gR + gB
+    assert np.linalg.norm(grho - rho) / np.linalg.norm(rho) <= 1e-4
+    assert np.linalg.norm(gR - rR) / np.linalg.norm(rR) <= 1e-4
+    scale = max(np.linalg.norm(u), 1e-3 * np.sqrt(3 * n ** 3))
+    assert np.linalg.norm(gu - u) / scale <= 1e-4
+
+
+def test_full_size_moving_droplet_one_step():
+    """128^3 periodic, R = 20, u = (0.05, 0, 0), density ratio 10, sigma =
+    0.005: one fused step in the benchmark's launch configuration, compared
+    with the oracle over the whole lattice."""
+    n = 128
+    pd = base(n, n, n, rho_in_R=10.0, rho_in_B=1.0, alpha_R=0.97, alpha_B=0.7,
+              tau_R=1.0, tau_B=1.0, tau_q=1.0, tau_pi=1.0, A_R=0.01125,
+              A_B=0.01125, beta=0.7, force=(0, 0, 0), gravity=(0, 0, 0))
+    f0 = droplet_state(pd, 20.0, (0.05, 0.0, 0.0), noise=0.0)
+    ref = oracle.step(oracle.params_from(pd), f0, 1)
+    got = gpu_run(pd, f0, 1, "fused")
+    assert rel_linf(got, ref) <= 1e-5
+
+
+def test_checkpoint_resume_is_bit_identical():
+    pd = base(30, 14, 10)
+    f0 = droplet_state(pd, 4.0, (0.02, 0.0, 0.0))
+    params = lbm.make_params(**pd)
+    a = lbm.Lattice(params, device=DEV)
+    a.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    a.step(7)
+    ck = torch.empty(lbm.lbm_population_bytes(a.ctx), dtype=torch.uint8)
+    lbm.lbm_get_populations(a.ctx, ck)
+    a.step(9)
+    fa = a.get_f()
+    b = lbm.Lattice(params, device=DEV)
+    lbm.lbm_set_populations(b.ctx, ck)
+    b.step(9)
+    fb = b.get_f()
+    a.close()
+    b.close()
+    assert torch.equal(fa, fb)
+
+
+def test_host_and_device_pointers_agree():
+    pd = base(24, 10, 6)
+    rR, rB, u = (np.ascontiguousarray(x, dtype=np.float32)
+                 for x in wl.droplet(24, 10, 6, 3.0, 3.0, 1.0, velocity=(0.01, 0, 0)))
+    params = lbm.make_params(**pd)
+    a = lbm.Lattice(params, device=DEV)
+    lbm.lbm_init_fields(a.ctx, rR, rB, u)          # host pointers
+    b = lbm.Lattice(params, device=DEV)
+    b.init_fields(rR, rB, u)                        # device tensors
+    a.step(3)
+    b.step(3)
+    hR = np.empty(rR.shape, np.float32)
+    hB = np.empty(rR.shape, np.float32)
+    hu = np.empty(u.shape, np.float32)
+    lbm.lbm_moments(a.ctx, hR, hB, hu)              # host outputs
+    dR, dB, du = b.moments()
+    assert np.array_equal(hR, dR.cpu().numpy()) and np.array_equal(hu, du.cpu().numpy())
+    fh = np.empty((2, 19, 6, 10, 24), np.float32)
+    lbm.lbm_get_f(a.ctx, fh)
+    assert np.array_equal(fh, b.get_f().cpu().numpy())
+    a.close()
+    b.close()
+
+
+def test_diagnostics_and_mass_conservation():
+    pd = base(40, 24, 16, force=(0, 0, 0), gravity=(0, 0, 0))
+    f0 = droplet_state(pd, 6.0, (0.02, 0.0, 0.0))
+    lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    d0 = lat.diagnostics()
+    assert d0[0] == pytest.approx(f0[0].sum(), rel=1e-12)
+    assert d0[1] == pytest.approx(f0[1].sum(), rel=1e-12)
+    lat.step(300)
+    d1 = lat.diagnostics()
+    f1 = lat.get_f().double().cpu().numpy()
+    lat.close()
+    assert d1[12] == 300 and d1[5] == 0 and d1[6] == 0
+    assert d1[0] == pytest.approx(f1[0].sum(), rel=1e-12)
+    # FP32 storage: each colour's mass drifts only by accumulated rounding
+    assert abs(d1[0] - d0[0]) / d0[0] < 1e-5 and abs(d1[1] - d0[1]) / d0[1] < 1e-5
+    e = oracle.params_from(pd)
+    mom = np.einsum("ia,kizyx->a", np.array(
+        [[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+         [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1],
+         [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]], float), f1)
+    assert np.allclose(d1[2:5], mom, rtol=1e-9, atol=1e-9)
+    assert e.nx == 40
+
+
+def test_non_finite_state_is_reported_not_faulted():
+    pd = base(16, 8, 4)
+    f0 = droplet_state(pd, 3.0)
+    f0[0, 3, 2, 4, 5] = np.nan
+    lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.diagnostics()
+    assert ei.value.status == lbm.LBM_ERR_UNSTABLE
+    lat.step(1)  # the context stays usable
+    d = lat.diagnostics(raise_unstable=False)
+    assert d[5] >= 1
+    lat.close()
+
+
+def test_step_before_init_is_a_state_error():
+    lat = lbm.Lattice(lbm.make_params(8, 8, 8), device=DEV)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)
+    assert ei.value.status == lbm.LBM_ERR_STATE
+    lat.close()
