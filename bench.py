@@ -212,7 +212,8 @@ def config_block(args, world):
                         "R=%g, u=(0.05,0,0), density ratio 10, viscosity ratio 1, "
                         "sigma=0.005, beta=0.7" % (args.n, 20.0 * args.n / 128.0),
             "lattice": [args.n, args.n, args.n], "storage": args.storage,
-            "kernel": args.kernel, "model": "improved (Eq. 18 + Eq. 45 correction)",
+            "kernel": args.kernel, "fused_config": args.fused_config or "library default",
+            "model": "improved (Eq. 18 + Eq. 45 correction)",
             "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
             "l2_policy": "inputs larger than L2 (%.0f MB populations)" % (
                 args.n ** 3 * 38 * BYTES_PER_VALUE[args.storage] / 1e6)}
@@ -245,6 +246,9 @@ def run_ours(args, rank, world, local_rank):
     rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in workload_fields(n))
     stream = torch.cuda.Stream(dev)
     lat = lbm.Lattice(params, device=dev, stream=stream)
+    if args.kernel == "fused" and args.fused_config:
+        ty, zc, hold = (int(v) for v in args.fused_config.split(","))
+        lbm.lbm_set_fused_config(lat.ctx, ty, zc, hold)
     lat.init_fields(rR, rB, u)
     launches = lbm.lbm_launches_per_step(lat.ctx)
 
@@ -357,6 +361,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--fused-config", default="",
+                    help="tile_y,zchunk,hold of the fused kernel (default: library choice)")
     ap.add_argument("--cpu-n", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")

@@ -67,7 +67,7 @@ typedef enum {
 /* Model and lattice parameters.  Defaults used by the paper are in
    brackets; see the cited equations for meaning. */
 typedef struct {
-  int nx, ny, nz;      /* lattice size, each >= 1                            */
+  int nx, ny, nz;      /* lattice size, each >= 1, nx*ny*nz < 226 million    */
   int wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on
                           both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D  */
   int improved;        /* 1: Eq. 18 equilibrium + Eq. 45 correction (the
@@ -141,7 +141,9 @@ lbm_status lbm_get_f(lbm_ctx *ctx, float *f);
    device), converting to the storage format.  Resets the step counter. */
 lbm_status lbm_set_f(lbm_ctx *ctx, const float *f);
 
-/* Size in bytes of one raw population buffer (the checkpoint unit). */
+/* Size in bytes of one raw population buffer (the checkpoint unit).  The
+   internal layout is [direction][cell][colour]: the red and blue values of
+   one direction and cell are adjacent; each direction plane is padded. */
 size_t lbm_population_bytes(const lbm_ctx *ctx);
 
 /* Raw checkpoint of the current population buffer: dst (host or device)
@@ -152,6 +154,21 @@ size_t lbm_population_bytes(const lbm_ctx *ctx);
    Both synchronise the context stream. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
+
+/* Launch configuration of the fused kernel (LBM_KERNEL_FUSED), the knob the
+   autotuner turns; results are identical for every valid configuration.
+   tile_y: CTA rows including the one-cell ring, 8 or 16 (the interior tile
+   is 30 x (tile_y - 2) cells).  zchunk: planes marched per CTA, 0 = the
+   library's default for this lattice.  hold: where the populations of a
+   plane wait between the moment pass and the collision: 0 pulled again, 1
+   registers, 2 shared memory (tile_y = 8 only), 3 shared memory filled by
+   asynchronous copies issued two planes ahead (tile_y = 8 only), 4 shared
+   memory with each thread handling two tile rows (tile_y = 16 only), 5 and
+   6 as 2 with registers capped for three and four CTAs per SM.
+   Errors: LBM_ERR_ARG. */
+lbm_status lbm_set_fused_config(lbm_ctx *ctx, int tile_y, int zchunk, int hold);
+lbm_status lbm_get_fused_config(const lbm_ctx *ctx, int *tile_y, int *zchunk,
+                                int *hold);
 
 /* Number of kernel launches one lbm_step(ctx, 1) issues (1 for the fused
    kernel, 2 for the two-pass form). */

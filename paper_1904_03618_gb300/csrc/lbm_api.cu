@@ -99,7 +99,9 @@ static lbm_status validate(const lbm_params* p) {
   if (!isfinite(p->ref_R) || !isfinite(p->ref_B))
     return fail(nullptr, LBM_ERR_ARG, "ref_R and ref_B must be finite");
   long long N = (long long)p->nx * p->ny * p->nz;
-  if (N > (1LL << 40)) return fail(nullptr, LBM_ERR_ARG, "lattice too large");
+  // pair offsets (direction * padded plane + cell) are 32-bit
+  if ((N + 64) * 19 >= (1LL << 32))
+    return fail(nullptr, LBM_ERR_ARG, "lattice too large: nx*ny*nz must be below 226,000,000");
   return LBM_OK;
 }
 
@@ -127,6 +129,8 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
   a.tau_h = (float)th;
   a.par_a = (float)(2.0 * (p->tau_R - th) / p->delta);
   a.par_b = (float)(2.0 * (th - p->tau_B) / p->delta);
+  a.par_a2 = (float)(2.0 * (p->tau_R - th) / p->delta / (2.0 * p->delta));
+  a.par_b2 = (float)(2.0 * (th - p->tau_B) / p->delta / (2.0 * p->delta));
   a.delta = (float)p->delta;
   a.s_e = (float)(1.0 / p->tau_e);
   a.s_q = (float)(1.0 / p->tau_q);
@@ -139,6 +143,8 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
   a.gx = (float)p->gravity[0];
   a.gy = (float)p->gravity[1];
   a.gz = (float)p->gravity[2];
+  a.has_force = (p->force[0] != 0 || p->force[1] != 0 || p->force[2] != 0 ||
+                 p->gravity[0] != 0 || p->gravity[1] != 0 || p->gravity[2] != 0);
   if (p->storage != LBM_F32) {
     a.offR0 = (float)(p->ref_R * p->alpha_R);
     a.offR1 = (float)(p->ref_R * (1.0 - p->alpha_R) / 12.0);
@@ -445,6 +451,32 @@ extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
   c->cur = 0;
   c->initialized = 1;
   c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
+                                           int hold) {
+  if (!c) return LBM_ERR_ARG;
+  lbm::FusedConfig f;
+  f.tile_y = tile_y;
+  f.hold = hold;
+  f.zchunk = zchunk == 0 ? lbm::default_fused_config(c->args, c->p.storage).zchunk
+                         : zchunk;
+  if (zchunk < 0 || !lbm::valid_fused_config(f, c->p.storage))
+    return fail(c, LBM_ERR_ARG,
+                "invalid fused configuration (tile_y 8 or 16, zchunk >= 0, hold 0..4, "
+                "hold 2-3 need tile_y 8, hold 4 needs tile_y 16)");
+  c->fused = f;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fused_config(const lbm_ctx* c, int* tile_y,
+                                           int* zchunk, int* hold) {
+  if (!c || !tile_y || !zchunk || !hold) return LBM_ERR_ARG;
+  *tile_y = c->fused.tile_y;
+  *zchunk = c->fused.zchunk;
+  *hold = c->fused.hold;
   return LBM_OK;
 }
 

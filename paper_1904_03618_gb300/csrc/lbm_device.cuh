@@ -40,7 +40,9 @@ struct StepArgs {
   float tau_R, tau_B;           // Eq. 52 end values
   float tau_h;                  // 2 tau_R tau_B / (tau_R + tau_B)
   float par_a, par_b;           // slopes of g^R, g^B at rho^N = 0
+  float par_a2, par_b2;         // par_a / (2 delta), par_b / (2 delta)
   float delta;                  // Eq. 52
+  int has_force;                // any non-zero force or gravity component
   float s_e, s_q, s_pi;         // 1/tau_e, 1/tau_q, 1/tau_pi (Eq. 44)
   float half_A;                 // (A_R + A_B) / 2, Eq. 8 summed over colours
   float beta;                   // Eq. 10-11
@@ -75,7 +77,9 @@ __host__ __device__ constexpr int shell(int i) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage formats.  FP32 stores f itself; FP16 / BF16 store the deviation
+// Storage formats.  The red and blue values of one direction and cell are
+// adjacent (one 8-byte FP32 pair or one 4-byte half pair), so one access
+// moves both colours.  FP32 stores f itself; FP16 / BF16 store the deviation
 // f - ref_k phi_i^k and are converted to FP32 on load.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -84,29 +88,42 @@ struct Store;
 template <>
 struct Store<float> {
   static constexpr bool kDeviation = false;
-  __device__ __forceinline__ static float load(const float* p) {
-    return __ldg(p);
+  using Pair = float2;
+  __device__ __forceinline__ static float2 load2(const float* p) {
+    return __ldg(reinterpret_cast<const float2*>(p));
   }
-  __device__ __forceinline__ static void store(float* p, float v) { *p = v; }
+  __device__ __forceinline__ static void store2(float* p, float r, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(r, b);
+  }
+  __device__ __forceinline__ static float2 to_float2(float2 v) { return v; }
 };
 template <>
 struct Store<__half> {
   static constexpr bool kDeviation = true;
-  __device__ __forceinline__ static float load(const __half* p) {
-    return __half2float(__ldg(p));
+  using Pair = __half2;
+  __device__ __forceinline__ static float2 load2(const __half* p) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
   }
-  __device__ __forceinline__ static void store(__half* p, float v) {
-    *p = __float2half_rn(v);
+  __device__ __forceinline__ static void store2(__half* p, float r, float b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(r, b);
+  }
+  __device__ __forceinline__ static float2 to_float2(__half2 v) {
+    return __half22float2(v);
   }
 };
 template <>
 struct Store<__nv_bfloat16> {
   static constexpr bool kDeviation = true;
-  __device__ __forceinline__ static float load(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
+  using Pair = __nv_bfloat162;
+  __device__ __forceinline__ static float2 load2(const __nv_bfloat16* p) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
   }
-  __device__ __forceinline__ static void store(__nv_bfloat16* p, float v) {
-    *p = __float2bfloat16_rn(v);
+  __device__ __forceinline__ static void store2(__nv_bfloat16* p, float r,
+                                                float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(r, b);
+  }
+  __device__ __forceinline__ static float2 to_float2(__nv_bfloat162 v) {
+    return __bfloat1622float2(v);
   }
 };
 
@@ -116,6 +133,11 @@ __device__ __forceinline__ float dev_offset(const StepArgs& a, int k) {
   if (k == 0) return s == 0 ? a.offR0 : (s == 1 ? a.offR1 : a.offR2);
   return s == 0 ? a.offB0 : (s == 1 ? a.offB1 : a.offB2);
 }
+
+// Reciprocal through the special-function unit (relative error of a few ulp,
+// far below the FP32 parity bar); the IEEE-exact division is a multi-
+// instruction sequence on the critical path of every cell.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 
 // ---------------------------------------------------------------------------
 // Indexing.
@@ -127,9 +149,11 @@ __device__ __forceinline__ long long cell_of(const StepArgs& a, int x, int y,
                                              int z) {
   return ((long long)z * a.ny + y) * a.nx + x;
 }
-__device__ __forceinline__ long long pidx(const StepArgs& a, int k, int i,
-                                          long long cell) {
-  return ((long long)(k * 19 + i)) * a.plane + cell;
+// Element index of the (red, blue) pair of direction i at a cell: layout
+// [i][cell][colour], each direction plane padded to `plane` cells.
+__device__ __forceinline__ long long pidx2(const StepArgs& a, int i,
+                                           long long cell) {
+  return ((long long)i * a.plane + cell) * 2;
 }
 
 // Pull streaming (Sec. II.A, below Eq. 13): f_i^k(x, t) = f_i^{k,+}(x - e_i,
@@ -153,8 +177,8 @@ __device__ __forceinline__ void pull_one(const T* __restrict__ src,
     cs = cell_of(a, wrap1(xs, a.nx), wrap1(ys, a.ny), wrap1(zs, a.nz));
     d = I;
   }
-  float r = Store<T>::load(src + pidx(a, 0, d, cs));
-  float b = Store<T>::load(src + pidx(a, 1, d, cs));
+  const float2 v = Store<T>::load2(src + pidx2(a, d, cs));
+  float r = v.x, b = v.y;
   if (Store<T>::kDeviation) {
     // the offset belongs to the stored direction, which has the same shell
     r += dev_offset<I>(a, 0);
@@ -202,8 +226,7 @@ __device__ __forceinline__ void store_cell(T* __restrict__ dst,
       r -= s == 0 ? a.offR0 : (s == 1 ? a.offR1 : a.offR2);
       b -= s == 0 ? a.offB0 : (s == 1 ? a.offB1 : a.offB2);
     }
-    Store<T>::store(dst + pidx(a, 0, i, c), r);
-    Store<T>::store(dst + pidx(a, 1, i, c), b);
+    Store<T>::store2(dst + pidx2(a, i, c), r, b);
   }
 }
 
@@ -214,28 +237,20 @@ struct Macro {
   float rR, rB, rho, inv_rho, ux, uy, uz, Fx, Fy, Fz;
 };
 
-__device__ __forceinline__ Macro macro_of(const StepArgs& a, const float* fR,
-                                          const float* fB) {
+// From the total populations f_i = f_i^R + f_i^B and the colour densities.
+__device__ __forceinline__ Macro macro_total(const StepArgs& a, const float* f,
+                                             float rR, float rB) {
   Macro m;
-  float rR = 0.f, rB = 0.f;
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    rR += fR[i];
-    rB += fB[i];
-  }
-  float f[19];
-#pragma unroll
-  for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
-  float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) +
-             (f[13] - f[14]);
-  float jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) +
-             (f[17] - f[18]);
-  float jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) +
-             (f[15] - f[16]) + (f[18] - f[17]);
+  const float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) +
+                   (f[11] - f[12]) + (f[13] - f[14]);
+  const float jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) +
+                   (f[15] - f[16]) + (f[17] - f[18]);
+  const float jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) +
+                   (f[15] - f[16]) + (f[18] - f[17]);
   m.rR = rR;
   m.rB = rB;
   m.rho = rR + rB;
-  m.inv_rho = 1.0f / m.rho;
+  m.inv_rho = fast_rcp(m.rho);
   m.Fx = a.fx + m.rho * a.gx;
   m.Fy = a.fy + m.rho * a.gy;
   m.Fz = a.fz + m.rho * a.gz;
@@ -245,10 +260,49 @@ __device__ __forceinline__ Macro macro_of(const StepArgs& a, const float* fR,
   return m;
 }
 
+// Macroscopics from held values (colour densities and velocity).
+__device__ __forceinline__ Macro macro_held(const StepArgs& a, float rR,
+                                            float rB, float ux, float uy,
+                                            float uz) {
+  Macro m;
+  m.rR = rR;
+  m.rB = rB;
+  m.rho = rR + rB;
+  m.inv_rho = fast_rcp(m.rho);
+  m.Fx = a.fx + m.rho * a.gx;
+  m.Fy = a.fy + m.rho * a.gy;
+  m.Fz = a.fz + m.rho * a.gz;
+  m.ux = ux;
+  m.uy = uy;
+  m.uz = uz;
+  return m;
+}
+
+// Reduces the pulled colour populations to (f = fR + fB, rho_R, rho_B), all
+// that the collision and recolouring of the cell need.
+__device__ __forceinline__ void reduce_colours(const float* fR, const float* fB,
+                                               float* f, float& rR, float& rB) {
+  rR = 0.f;
+  rB = 0.f;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    rR += fR[i];
+    rB += fB[i];
+    f[i] = fR[i] + fB[i];
+  }
+}
+
+__device__ __forceinline__ Macro macro_of(const StepArgs& a, const float* fR,
+                                          const float* fB) {
+  float f[19], rR, rB;
+  reduce_colours(fR, fB, f, rR, rB);
+  return macro_total(a, f, rR, rB);
+}
+
 __device__ __forceinline__ float phase_field(const StepArgs& a, float rR,
                                              float rB) {
   float r = rR * a.inv_rin_R, b = rB * a.inv_rin_B;
-  return (r - b) / (r + b);
+  return (r - b) * fast_rcp(r + b);
 }
 
 // Sum over colours of rho_k (1 - 3 c_s^k^2): Qbar_alpha = u_alpha * this.
@@ -257,30 +311,54 @@ __device__ __forceinline__ float qbar_scale(const StepArgs& a, float rR,
   return a.q_R * rR + a.q_B * rB;
 }
 
+// Window entry of the Eq. 49 stencils: (rho^N, Qbar_x, Qbar_y, Qbar_z).
+__device__ __forceinline__ float4 stencil_entry(const StepArgs& a,
+                                                const Macro& m) {
+  const float q = qbar_scale(a, m.rR, m.rB);
+  return make_float4(phase_field(a, m.rR, m.rB), m.ux * q, m.uy * q, m.uz * q);
+}
+
 // Eq. 52 with the parabolic g^R, g^B (continuous, zero slope at +-delta,
 // harmonic mean at rho^N = 0).
 __device__ __forceinline__ float tau_v_of(const StepArgs& a, float rn) {
   if (rn > a.delta) return a.tau_R;
-  if (rn > 0.f) return a.tau_h + rn * (a.par_a - a.par_a * rn / (2.f * a.delta));
+  if (rn > 0.f) return a.tau_h + rn * (a.par_a - a.par_a2 * rn);
   if (rn >= -a.delta)
-    return a.tau_h + rn * (a.par_b + a.par_b * rn / (2.f * a.delta));
+    return a.tau_h + rn * (a.par_b + a.par_b2 * rn);
   return a.tau_B;
 }
 
 // ---------------------------------------------------------------------------
-// Collision + perturbation + recolouring of one cell.  On entry fR, fB hold
-// the pulled populations; on exit the post-recolouring f^{k,+}.
+// Recolouring coefficients of Eq. 10-11 for one cell:
+//   f_i^{R,+} = wr f*_i + seg_i,  f_i^{B,+} = wb f*_i - seg_i,
+//   seg_i = beta rho_R rho_B / rho^2 cos(phi_i) sum_k rho_k phi_i^k
+//         = c_shell(i) * (e_i . n),
+// since sum_k rho_k phi_i^k = p/6 on the axes and p/12 on the diagonals and
+// cos(phi_i) = e_i . n / |e_i| (|e_i| = 1 or sqrt 2).
+// ---------------------------------------------------------------------------
+struct Recolour {
+  float wr, wb, nx, ny, nz, cax, cdg;
+};
+
+template <int I>
+__device__ __forceinline__ float recolour_seg(const Recolour& rc) {
+  if (I == 0) return 0.f;
+  const float en = ex(I) * rc.nx + ey(I) * rc.ny + ez(I) * rc.nz;
+  return (shell(I) == 1 ? rc.cax : rc.cdg) * en;
+}
+
+// ---------------------------------------------------------------------------
+// Collision + perturbation of the total population of one cell.  On entry
+// f holds the pulled f_i = f_i^R + f_i^B; on exit the post-perturbation
+// f*_i (Eq. 12 summed over colours).  Returns the recolouring coefficients.
 // grad = grad rho^N and Q = (d_x Qbar_x, d_y Qbar_y, d_z Qbar_z), both from
 // the Eq. 49 stencil.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
-                                             float* fB, const Macro& mc,
-                                             float rhoN, float Gx, float Gy,
-                                             float Gz, float Qx, float Qy,
-                                             float Qz) {
-  float f[19];
-#pragma unroll
-  for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
+__device__ __forceinline__ Recolour collide_total(const StepArgs& a, float* f,
+                                                  const Macro& mc, float rhoN,
+                                                  float Gx, float Gy, float Gz,
+                                                  float Qx, float Qy,
+                                                  float Qz) {
   const float rho = mc.rho, ux = mc.ux, uy = mc.uy, uz = mc.uz;
   const float Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
 
@@ -329,29 +407,33 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
   e[18] = (twop + rho * (2.f * uy2 + 2.f * uz2 - ux2)) * (1.0f / 6.0f);
 
   // source in moment space: correction C (rows 4-6) + Guo force F_hat
-  const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz;
   float src[19];
-  src[4] = 2.f * (Fux + Fuy + Fuz);
-  src[5] = 2.f * (2.f * Fux - Fuy - Fuz);
-  src[6] = 2.f * (Fuy - Fuz);
+#pragma unroll
+  for (int r = 4; r < 19; ++r) src[r] = 0.f;
+  if (a.has_force) {
+    const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz;
+    src[4] = 2.f * (Fux + Fuy + Fuz);
+    src[5] = 2.f * (2.f * Fux - Fuy - Fuz);
+    src[6] = 2.f * (Fuy - Fuz);
+    src[7] = Fx * uy + Fy * ux;
+    src[8] = Fx * uz + Fz * ux;
+    src[9] = Fy * uz + Fz * uy;
+    const float third = 1.0f / 3.0f;
+    src[10] = Fy * third;
+    src[11] = Fx * third;
+    src[12] = Fz * third;
+    src[13] = Fx * third;
+    src[14] = Fz * third;
+    src[15] = Fy * third;
+    src[16] = (2.f * Fux + 2.f * Fuy - Fuz) * third;
+    src[17] = (2.f * Fux + 2.f * Fuz - Fuy) * third;
+    src[18] = (2.f * Fuy + 2.f * Fuz - Fux) * third;
+  }
   if (a.improved) {
     src[4] += Qx + Qy + Qz;
     src[5] += 2.f * Qx - Qy - Qz;
     src[6] += Qy - Qz;
   }
-  src[7] = Fx * uy + Fy * ux;
-  src[8] = Fx * uz + Fz * ux;
-  src[9] = Fy * uz + Fz * uy;
-  const float third = 1.0f / 3.0f;
-  src[10] = Fy * third;
-  src[11] = Fx * third;
-  src[12] = Fz * third;
-  src[13] = Fx * third;
-  src[14] = Fz * third;
-  src[15] = Fy * third;
-  src[16] = (2.f * Fux + 2.f * Fuy - Fuz) * third;
-  src[17] = (2.f * Fux + 2.f * Fuz - Fuy) * third;
-  src[18] = (2.f * Fuy + 2.f * Fuz - Fux) * third;
 
   // perturbation moments (A/2)|G| pi(n), pi from M applied to Eq. 8
   const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
@@ -376,7 +458,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
   }
 
   // relaxation rates (Eq. 44) with the variable tau_v of Eq. 52
-  const float s_v = 1.0f / tau_v_of(a, rhoN);
+  const float s_v = fast_rcp(tau_v_of(a, rhoN));
   const float s_e = a.s_e, s_q = a.s_q, s_pi = a.s_pi;
 
   // change of moments dm = m* - m (rows 1-3: F; row 0: 0)
@@ -408,78 +490,83 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
   const float c46 = d[4] * (1.0f / 6.0f);
   const float c5a = d[5] * (1.0f / 6.0f), c5b = d[5] * (1.0f / 12.0f);
   const float c6 = d[6] * 0.25f;
-  float fs[19];
-  fs[0] = f[0] - d[4] + d[16] + d[17] + d[18];
+  f[0] += -d[4] + d[16] + d[17] + d[18];
   {
     const float base = c46 + c5a - h * (d[16] + d[17]);
     const float odd = h * (d[1] - d[11] - d[13]);
-    fs[1] = f[1] + base + odd;
-    fs[2] = f[2] + base - odd;
+    f[1] += base + odd;
+    f[2] += base - odd;
   }
   {
     const float base = c46 - c5b + c6 - h * (d[16] + d[18]);
     const float odd = h * (d[2] - d[10] - d[15]);
-    fs[3] = f[3] + base + odd;
-    fs[4] = f[4] + base - odd;
+    f[3] += base + odd;
+    f[4] += base - odd;
   }
   {
     const float base = c46 - c5b - c6 - h * (d[17] + d[18]);
     const float odd = h * (d[3] - d[12] - d[14]);
-    fs[5] = f[5] + base + odd;
-    fs[6] = f[6] + base - odd;
+    f[5] += base + odd;
+    f[6] += base - odd;
   }
-  fs[7] = f[7] + q * (d[7] + d[10] + d[11] + d[16]);
-  fs[8] = f[8] + q * (d[7] - d[10] - d[11] + d[16]);
-  fs[9] = f[9] + q * (-d[7] - d[10] + d[11] + d[16]);
-  fs[10] = f[10] + q * (-d[7] + d[10] - d[11] + d[16]);
-  fs[11] = f[11] + q * (d[8] + d[12] + d[13] + d[17]);
-  fs[12] = f[12] + q * (d[8] - d[12] - d[13] + d[17]);
-  fs[13] = f[13] + q * (-d[8] - d[12] + d[13] + d[17]);
-  fs[14] = f[14] + q * (-d[8] + d[12] - d[13] + d[17]);
-  fs[15] = f[15] + q * (d[9] + d[14] + d[15] + d[18]);
-  fs[16] = f[16] + q * (d[9] - d[14] - d[15] + d[18]);
-  fs[17] = f[17] + q * (-d[9] - d[14] + d[15] + d[18]);
-  fs[18] = f[18] + q * (-d[9] + d[14] - d[15] + d[18]);
+  f[7] += q * (d[7] + d[10] + d[11] + d[16]);
+  f[8] += q * (d[7] - d[10] - d[11] + d[16]);
+  f[9] += q * (-d[7] - d[10] + d[11] + d[16]);
+  f[10] += q * (-d[7] + d[10] - d[11] + d[16]);
+  f[11] += q * (d[8] + d[12] + d[13] + d[17]);
+  f[12] += q * (d[8] - d[12] - d[13] + d[17]);
+  f[13] += q * (-d[8] - d[12] + d[13] + d[17]);
+  f[14] += q * (-d[8] + d[12] - d[13] + d[17]);
+  f[15] += q * (d[9] + d[14] + d[15] + d[18]);
+  f[16] += q * (d[9] - d[14] - d[15] + d[18]);
+  f[17] += q * (-d[9] - d[14] + d[15] + d[18]);
+  f[18] += q * (-d[9] + d[14] - d[15] + d[18]);
 
-  // recolouring, Eq. 10-11: f^{R,+} = (rho_R/rho) f* + seg_i,
-  // f^{B,+} = (rho_B/rho) f* - seg_i, seg_i = beta rho_R rho_B / rho^2
-  // cos(phi_i) sum_k rho_k phi_i^k; sum_k rho_k phi_i^k = p/6 on the axes and
-  // p/12 on the diagonals, cos(phi_i) = e_i.n / |e_i|.
-  const float wr = mc.rR * mc.inv_rho, wb = mc.rB * mc.inv_rho;
-  float nx = 0.f, ny = 0.f, nz = 0.f, cax = 0.f, cdg = 0.f;
+  Recolour rc;
+  rc.wr = mc.rR * mc.inv_rho;
+  rc.wb = mc.rB * mc.inv_rho;
+  rc.nx = rc.ny = rc.nz = rc.cax = rc.cdg = 0.f;
   if (has_g) {
-    nx = Gx * ig;
-    ny = Gy * ig;
-    nz = Gz * ig;
-    const float cb = a.beta * wr * wb * p;
-    cax = cb * (1.0f / 6.0f);
-    cdg = cb * (1.0f / (12.0f * 1.41421356237309515f));
+    rc.nx = Gx * ig;
+    rc.ny = Gy * ig;
+    rc.nz = Gz * ig;
+    const float cb = a.beta * rc.wr * rc.wb * p;
+    rc.cax = cb * (1.0f / 6.0f);
+    rc.cdg = cb * (1.0f / (12.0f * 1.41421356237309515f));
   }
-  float sg[19];
-  sg[0] = 0.f;
-  sg[1] = cax * nx;
-  sg[2] = -sg[1];
-  sg[3] = cax * ny;
-  sg[4] = -sg[3];
-  sg[5] = cax * nz;
-  sg[6] = -sg[5];
-  sg[7] = cdg * (nx + ny);
-  sg[8] = -sg[7];
-  sg[9] = cdg * (nx - ny);
-  sg[10] = -sg[9];
-  sg[11] = cdg * (nx + nz);
-  sg[12] = -sg[11];
-  sg[13] = cdg * (nx - nz);
-  sg[14] = -sg[13];
-  sg[15] = cdg * (ny + nz);
-  sg[16] = -sg[15];
-  sg[17] = cdg * (ny - nz);
-  sg[18] = -sg[17];
+  return rc;
+}
+
+template <int I>
+struct RecolourAll {
+  __device__ __forceinline__ static void run(const Recolour& rc,
+                                             const float* fs, float* fR,
+                                             float* fB) {
+    const float sg = recolour_seg<I>(rc);
+    fR[I] = rc.wr * fs[I] + sg;
+    fB[I] = rc.wb * fs[I] - sg;
+    RecolourAll<I + 1>::run(rc, fs, fR, fB);
+  }
+};
+template <>
+struct RecolourAll<19> {
+  __device__ __forceinline__ static void run(const Recolour&, const float*,
+                                             float*, float*) {}
+};
+
+// Collision + perturbation + recolouring of one cell given both colours.  On
+// entry fR, fB hold the pulled populations; on exit the post-recolouring
+// f^{k,+}.
+__device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
+                                             float* fB, const Macro& mc,
+                                             float rhoN, float Gx, float Gy,
+                                             float Gz, float Qx, float Qy,
+                                             float Qz) {
+  float f[19];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    fR[i] = wr * fs[i] + sg[i];
-    fB[i] = wb * fs[i] - sg[i];
-  }
+  for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
+  const Recolour rc = collide_total(a, f, mc, rhoN, Gx, Gy, Gz, Qx, Qy, Qz);
+  RecolourAll<0>::run(rc, f, fR, fB);
 }
 
 }  // namespace lbm

@@ -25,14 +25,24 @@ cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
 cudaError_t launch_twopass(int storage, const void* src, void* dst,
                            const StepArgs& a, float4* mom, cudaStream_t s);
 
-// Fused z-marching step.  `err` is a device word the kernel may set.
+// Fused z-marching step.
 struct FusedConfig {
-  int tile_x, tile_y;   // interior cells per CTA (x, y)
-  int zchunk;           // planes marched per CTA
+  int tile_y;  // CTA rows including the ring: 8 or 16 (interior 30 x (tile_y - 2))
+  int zchunk;  // planes marched per CTA (> 0)
+  int hold;    // where plane z waits between its two uses: 0 re-pulled from
+               // L1/L2, 1 registers, 2 shared memory (tile_y = 8 only),
+               // 3 shared memory with cp.async prefetch of plane z + 2
+               // (tile_y = 8), 4 shared memory with two tile rows per
+               // thread (tile_y = 16), 5 / 6 as 2 with registers capped
+               // for 3 / 4 CTAs per SM
 };
+template <typename T>
+cudaError_t launch_fused_storage(const void* src, void* dst, const StepArgs& a,
+                                 const FusedConfig& cfg, cudaStream_t s);
 cudaError_t launch_fused(int storage, const void* src, void* dst,
                          const StepArgs& a, const FusedConfig& cfg,
                          cudaStream_t s);
 FusedConfig default_fused_config(const StepArgs& a, int storage);
+bool valid_fused_config(const FusedConfig& c, int storage);
 
 }  // namespace lbm

@@ -33,8 +33,7 @@ __device__ __forceinline__ void scatter_one(T* __restrict__ dst,
     vr -= dev_offset<I>(a, 0);
     vb -= dev_offset<I>(a, 1);
   }
-  Store<T>::store(dst + pidx(a, 0, d, cs), vr);
-  Store<T>::store(dst + pidx(a, 1, d, cs), vb);
+  Store<T>::store2(dst + pidx2(a, d, cs), vr, vb);
 }
 
 template <typename T, int I>
@@ -193,10 +192,11 @@ __global__ void __launch_bounds__(kDiagBlock)
     for (int i = 0; i < 19; ++i)
       finite = finite && isfinite(fR[i]) && isfinite(fB[i]);
     Macro m = macro_of(a, fR, fB);
-    double rR = m.rR, rB = m.rB;
-    double jx = 0, jy = 0, jz = 0;
+    double rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
+      rR += (double)fR[i];
+      rB += (double)fB[i];
       double fi = (double)fR[i] + (double)fB[i];
       jx += ex(i) * fi;
       jy += ey(i) * fi;
@@ -291,23 +291,25 @@ __global__ void __launch_bounds__(256)
   pull_cell<T>(src, a, x, y, z, fR, fB);
   Macro m = macro_of(a, fR, fB);
   // Eq. 49: d_a psi = 3 sum_i w_i psi(x + e_i) e_ia = (1/6) axis differences
-  // + (1/12) diagonal differences.
+  // + (1/12) diagonal differences, accumulated as differences of opposite
+  // neighbours so that a uniform field gives an exactly zero gradient.
   float Gx = 0.f, Gy = 0.f, Gz = 0.f, Qx = 0.f, Qy = 0.f, Qz = 0.f;
 #pragma unroll
-  for (int i = 1; i < 19; ++i) {
+  for (int i = 1; i < 19; i += 2) {
     const float w = (i <= 6) ? (1.0f / 6.0f) : (1.0f / 12.0f);
-    float4 v = __ldg(&mom[stencil_cell(a, x, y, z, ex(i), ey(i), ez(i), c)]);
+    const float4 vp = __ldg(&mom[stencil_cell(a, x, y, z, ex(i), ey(i), ez(i), c)]);
+    const float4 vm = __ldg(&mom[stencil_cell(a, x, y, z, -ex(i), -ey(i), -ez(i), c)]);
     if (ex(i)) {
-      Gx += (ex(i) * w) * v.x;
-      Qx += (ex(i) * w) * v.y;
+      Gx += (ex(i) * w) * (vp.x - vm.x);
+      Qx += (ex(i) * w) * (vp.y - vm.y);
     }
     if (ey(i)) {
-      Gy += (ey(i) * w) * v.x;
-      Qy += (ey(i) * w) * v.z;
+      Gy += (ey(i) * w) * (vp.x - vm.x);
+      Qy += (ey(i) * w) * (vp.z - vm.z);
     }
     if (ez(i)) {
-      Gz += (ez(i) * w) * v.x;
-      Qz += (ez(i) * w) * v.w;
+      Gz += (ez(i) * w) * (vp.x - vm.x);
+      Qz += (ez(i) * w) * (vp.w - vm.w);
     }
   }
   float rn = __ldg(&mom[c]).x;

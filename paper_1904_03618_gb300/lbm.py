@@ -84,6 +84,10 @@ _lib.lbm_get_populations.argtypes = [_ctx_p, _fp]
 _lib.lbm_get_populations.restype = ctypes.c_int
 _lib.lbm_set_populations.argtypes = [_ctx_p, _fp]
 _lib.lbm_set_populations.restype = ctypes.c_int
+_lib.lbm_set_fused_config.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+_lib.lbm_set_fused_config.restype = ctypes.c_int
+_lib.lbm_get_fused_config.argtypes = [_ctx_p] + [ctypes.POINTER(ctypes.c_int)] * 3
+_lib.lbm_get_fused_config.restype = ctypes.c_int
 _lib.lbm_launches_per_step.argtypes = [_ctx_p]
 _lib.lbm_launches_per_step.restype = ctypes.c_int
 _lib.lbm_destroy.argtypes = [_ctx_p]
@@ -94,6 +98,7 @@ _lib.lbm_last_error.restype = ctypes.c_char_p
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
+            "lbm_set_fused_config", "lbm_get_fused_config",
             "lbm_launches_per_step", "lbm_destroy", "lbm_last_error")
 
 
@@ -197,6 +202,16 @@ def lbm_get_populations(ctx, dst):
 
 def lbm_set_populations(ctx, src):
     _check(ctx, _lib.lbm_set_populations(ctx, _addr(src)))
+
+
+def lbm_set_fused_config(ctx, tile_y, zchunk, hold):
+    _check(ctx, _lib.lbm_set_fused_config(ctx, int(tile_y), int(zchunk), int(hold)))
+
+
+def lbm_get_fused_config(ctx):
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(ctx, _lib.lbm_get_fused_config(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def lbm_launches_per_step(ctx) -> int:

@@ -268,3 +268,21 @@ def test_step_before_init_is_a_state_error():
         lat.step(1)
     assert ei.value.status == lbm.LBM_ERR_STATE
     lat.close()
+
+
+@pytest.mark.parametrize("tile_y,hold", [(8, 0), (8, 1), (8, 2), (8, 3), (16, 0), (16, 1), (16, 4),
+                                          (8, 5), (8, 6)])
+@pytest.mark.parametrize("wall", [(0, 0, 0), (1, 0, 1)])
+def test_every_fused_configuration(tile_y, hold, wall):
+    """Results do not depend on the fused launch configuration."""
+    pd = base(71, 37, 19, wall=wall)
+    f0 = droplet_state(pd, 6.0, (0.02, 0.01, 0.0))
+    ref = oracle.step(oracle.params_from(pd), f0, 2)
+    for zchunk in (0, 5):
+        lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+        lbm.lbm_set_fused_config(lat.ctx, tile_y, zchunk, hold)
+        lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+        lat.step(2)
+        got = lat.get_f().double().cpu().numpy()
+        lat.close()
+        assert rel_linf(got, ref) <= 1e-5, (tile_y, hold, zchunk)
