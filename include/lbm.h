@@ -174,6 +174,29 @@ lbm_status lbm_get_fused_config(const lbm_ctx *ctx, int *tile_y, int *zchunk,
    kernel, 2 for the two-pass form). */
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
+/* One time step that allocates no device memory, for callers that cannot
+   call cudaMalloc (code that runs while a stream is being captured into a
+   CUDA graph, services whose device memory is fixed at start-up, embedders
+   that own every device buffer).  The paper has no counterpart: it is a
+   deployment variant of the two-pass step above, with the same result.
+   f_in: f_i^k(x, t) after streaming, float32 [2][19][N], device memory;
+   f_out: receives f_i^k(x, t + 1) in the same layout, device memory, must
+   not overlap f_in.  p->storage and p->kernel are ignored (FP32).  Work is
+   queued on cuda_stream (a cudaStream_t, NULL = legacy default stream); the
+   call returns without waiting.  The scratch (16 bytes per cell) is a fixed
+   device array of 262,144 cells (4 MiB) inside the library, held by every
+   GPU that loads the library until the process exits: lattices with
+   nx*ny*nz > 262,144 are rejected with LBM_ERR_ARG.  The first call on each
+   device looks up that array's device address (once, with the device
+   current); make that first call before any stream capture.  All calls on
+   a device share the array and it keeps the last call's contents (every
+   entry a call reads is written by that call first), so calls that overlap
+   on the GPU -- e.g. on two streams at once -- race.  Errors (LBM_ERR_ARG,
+   LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the calling
+   thread. */
+lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
+                            float *f_out, void *cuda_stream);
+
 /* Releases everything the context owns.  NULL is allowed. */
 void lbm_destroy(lbm_ctx *ctx);
 

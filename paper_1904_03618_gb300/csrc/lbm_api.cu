@@ -170,6 +170,19 @@ static void release(lbm_ctx* c) {
   if (prev >= 0) cudaSetDevice(prev);
 }
 
+// Shared with the other host translation units (declared in lbm_internal.h).
+namespace lbm {
+lbm_status validate_params(const lbm_params* p) { return validate(p); }
+StepArgs derive_step_args(const lbm_params* p, long long plane) {
+  return derive_args(p, plane);
+}
+lbm_status fail_without_context(lbm_status s, const char* msg) {
+  return fail(nullptr, s, "%s", msg);
+}
+bool is_device_pointer(const void* ptr) { return is_device_ptr(ptr); }
+void clear_thread_error() { g_create_err[0] = 0; }
+}  // namespace lbm
+
 extern "C" lbm_status lbm_create(const lbm_params* p, void* cuda_stream,
                                  lbm_ctx** out) {
   g_create_err[0] = 0;

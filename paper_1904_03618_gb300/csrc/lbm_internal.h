@@ -4,11 +4,20 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
 
 constexpr int kDiagSlots = 12;  // accumulated slots of lbm_diagnostics
+
+// Host helpers of the C-ABI layer.  Errors without a context are recorded
+// for lbm_last_error(NULL) of the calling thread.
+lbm_status validate_params(const lbm_params* p);
+StepArgs derive_step_args(const lbm_params* p, long long plane);
+lbm_status fail_without_context(lbm_status s, const char* msg);
+bool is_device_pointer(const void* ptr);
+void clear_thread_error();
 
 cudaError_t launch_init_eq(int storage, void* dst, const StepArgs& a,
                            float alpha_R, float alpha_B, const float* rR,

@@ -88,6 +88,8 @@ _lib.lbm_set_fused_config.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes
 _lib.lbm_set_fused_config.restype = ctypes.c_int
 _lib.lbm_get_fused_config.argtypes = [_ctx_p] + [ctypes.POINTER(ctypes.c_int)] * 3
 _lib.lbm_get_fused_config.restype = ctypes.c_int
+_lib.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
+_lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_launches_per_step.argtypes = [_ctx_p]
 _lib.lbm_launches_per_step.restype = ctypes.c_int
 _lib.lbm_destroy.argtypes = [_ctx_p]
@@ -98,7 +100,7 @@ _lib.lbm_last_error.restype = ctypes.c_char_p
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
-            "lbm_set_fused_config", "lbm_get_fused_config",
+            "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
             "lbm_launches_per_step", "lbm_destroy", "lbm_last_error")
 
 
@@ -212,6 +214,15 @@ def lbm_get_fused_config(ctx):
     v = [ctypes.c_int() for _ in range(3)]
     _check(ctx, _lib.lbm_get_fused_config(ctx, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def lbm_step_noalloc(params: LbmParams, f_in, f_out, stream=None):
+    """One step on caller-owned device arrays (float32 [2][19][N] each)
+    without any device allocation; see include/lbm.h for its limits."""
+    s = ctypes.c_void_p(stream) if stream else None
+    st = _lib.lbm_step_noalloc(ctypes.byref(params), _addr(f_in), _addr(f_out), s)
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
 
 
 def lbm_launches_per_step(ctx) -> int:
