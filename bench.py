@@ -46,6 +46,15 @@ def workload(n):
                 force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0))
 
 
+def storage_references(storage, rho_in_R, rho_in_B, rho_R, rho_B):
+    """Deviation references for FP16/BF16 storage: the colour with more mass
+    (the background phase) is stored as f - rho_in phi, the other as is, so
+    that the absent colour stays exactly zero."""
+    if storage == "f32":
+        return 0.0, 0.0
+    return (rho_in_R, 0.0) if rho_R.sum() >= rho_B.sum() else (0.0, rho_in_B)
+
+
 def workload_fields(n):
     from paper_1904_03618_gb300 import workloads
     return workloads.droplet(n, n, n, 20.0 * n / 128.0, 10.0, 1.0,
@@ -128,7 +137,7 @@ def profiled_traffic(kernel, storage, n):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("lbm_fused.cu", "lbm_device.cuh"):
+    for f in ("lbm_fused.cuh", "lbm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
     key = "%s_%s" % (kernel, storage)
     if vals.get("source_sha256") != h.hexdigest()[:16] or key + "_bytes_per_cell" not in vals:
@@ -240,10 +249,10 @@ def run_ours(args, rank, world, local_rank):
     n = args.n
     N = n ** 3
     pd = workload(n)
-    params = lbm.make_params(storage=args.storage, kernel=args.kernel, **pd)
-    if args.storage != "f32":
-        params.ref_R, params.ref_B = 0.0, 1.0
     rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in workload_fields(n))
+    params = lbm.make_params(storage=args.storage, kernel=args.kernel, **pd)
+    params.ref_R, params.ref_B = storage_references(args.storage, pd["rho_in_R"],
+                                                    pd["rho_in_B"], rR, rB)
     stream = torch.cuda.Stream(dev)
     lat = lbm.Lattice(params, device=dev, stream=stream)
     if args.kernel == "fused" and args.fused_config:
@@ -323,6 +332,10 @@ def run_ours(args, rank, world, local_rank):
         achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.kernel, args.storage, n)
 
+    variants = None
+    if rank == 0 and world == 1 and args.storage == "f32" and not args.no_variants:
+        variants = storage_variants(lbm, dev, pd, rR, rB, u, n, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _, _ = cpu_oracle_sample(args.cpu_n, args.cpu_seconds)
@@ -344,12 +357,67 @@ def run_ours(args, rank, world, local_rank):
                              "algorithmic_bytes_per_cell": 2 * 38 * BYTES_PER_VALUE[args.storage],
                              "kernel_ms": launch_ms},
                 "clocks": clocks,
+                "storage_variants": variants,
                 "cpu_baseline": cpu,
                 "check": {"nonfinite_cells": diag[5], "negative_density_cells": diag[6],
                           "mass_R": diag[0], "mass_B": diag[1]}}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def storage_variants(lbm, dev, pd, rR, rB, u, n, args):
+    """FP16 / BF16 deviation storage on the same workload: device-resident
+    MLUPS (same timing as the FP32 line, fewer steps) and the error after
+    `variant_steps` steps against the FP32 run from the same initial state:
+    relative L2 of the total density and of the velocity (velocity
+    normalised by its FP32 L2 norm)."""
+    import torch
+    out = {}
+    steps = args.variant_steps
+
+    def run(storage, nsteps, timed):
+        p = lbm.make_params(storage=storage, kernel=args.kernel, **pd)
+        p.ref_R, p.ref_B = storage_references(storage, pd["rho_in_R"], pd["rho_in_B"], rR, rB)
+        s = torch.cuda.Stream(dev)
+        lat = lbm.Lattice(p, device=dev, stream=s)
+        lat.init_fields(rR, rB, u)
+        ms = None
+        if timed:
+            for _ in range(args.warmup):
+                lbm.lbm_step(lat.ctx, 1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(timed):
+                lbm.lbm_step(lat.ctx, 1)
+            e1.record(s)
+            s.synchronize()
+            ms = e0.elapsed_time(e1) / timed
+            lat.init_fields(rR, rB, u)
+        lat.step(nsteps)
+        mom = lat.moments()
+        lat.close()
+        return ms, mom
+
+    _, ref = run("f32", steps, 0)
+    rho_ref = (ref[0] + ref[1]).double()
+    u_ref = ref[2].double()
+    peak, _ = measured_peaks()
+    for storage in ("f16", "bf16"):
+        ms, got = run(storage, steps, max(args.steps // 4, 50))
+        rho = (got[0] + got[1]).double()
+        uu = got[2].double()
+        mlups = n ** 3 / (ms * 1e-3) / 1e6
+        out[storage] = {
+            "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
+            "roofline_frac": mlups * 1e6 * 152 / (peak * 1e9),
+            "algorithmic_bytes_per_cell": 152,
+            "err_vs_f32_after_steps": steps,
+            "rho_rel_l2": float((rho - rho_ref).norm() / rho_ref.norm()),
+            "u_rel_l2": float((uu - u_ref).norm() / u_ref.norm()),
+        }
+    return out
 
 
 def main():
@@ -366,6 +434,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

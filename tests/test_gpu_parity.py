@@ -286,3 +286,29 @@ def test_every_fused_configuration(tile_y, hold, wall):
         got = lat.get_f().double().cpu().numpy()
         lat.close()
         assert rel_linf(got, ref) <= 1e-5, (tile_y, hold, zchunk)
+
+
+@pytest.mark.parametrize("storage,ulp", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_reduced_precision_storage_one_step(storage, ulp, kernel):
+    """FP16 / BF16 deviation storage.  The oracle is given exactly the state
+    the GPU holds (read back after lbm_set_f, i.e. already rounded), so one
+    step differs from it only by the rounding of the stored result: at most
+    half an ulp of the stored deviation f - ref_k phi_i^k, bounded here by
+    ulp * (max|f| + max ref_k phi_i^k) relative to max|f|, plus FP32
+    arithmetic."""
+    pd = base(45, 19, 11, wall=(0, 0, 1))
+    f0 = droplet_state(pd, 5.0, (0.02, 0.01, 0.0))
+    params = lbm.make_params(storage=storage, kernel=kernel, **pd)
+    params.ref_R, params.ref_B = 0.0, pd["rho_in_B"]  # blue is the background
+    lat = lbm.Lattice(params, device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    held = lat.get_f().double().cpu().numpy()
+    lat.step(1)
+    got = lat.get_f().double().cpu().numpy()
+    lat.close()
+    ref = oracle.step(oracle.params_from(pd), held, 1)
+    bound = ulp * (1.0 + pd["rho_in_B"] * pd["alpha_B"] / np.abs(ref).max()) + 1e-5
+    assert rel_linf(got, ref) <= bound
+    # rounding of the input alone stays within the same bound
+    assert rel_linf(held, f0) <= bound
