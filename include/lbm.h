@@ -67,7 +67,8 @@ typedef enum {
 /* Model and lattice parameters.  Defaults used by the paper are in
    brackets; see the cited equations for meaning. */
 typedef struct {
-  int nx, ny, nz;      /* lattice size, each >= 1, nx*ny*nz < 226 million    */
+  int nx, ny, nz;      /* lattice size, each >= 1, ny and nz <= 65535,
+                          nx*ny*nz < 226 million                            */
   int wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on
                           both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D  */
   int improved;        /* 1: Eq. 18 equilibrium + Eq. 45 correction (the

@@ -68,6 +68,8 @@ static lbm_status validate(const lbm_params* p) {
   if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1)
     return fail(nullptr, LBM_ERR_ARG, "nx, ny, nz must be >= 1");
+  if (p->ny > 65535 || p->nz > 65535)
+    return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
   for (int a = 0; a < 3; ++a)
     if (p->wall[a] != 0 && p->wall[a] != 1)
       return fail(nullptr, LBM_ERR_ARG, "wall[%d] must be 0 or 1", a);

@@ -145,78 +145,100 @@ __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x);
 __device__ __forceinline__ int wrap1(int v, int n) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
-__device__ __forceinline__ long long cell_of(const StepArgs& a, int x, int y,
-                                             int z) {
-  return ((long long)z * a.ny + y) * a.nx + x;
-}
-// Element index of the (red, blue) pair of direction i at a cell: layout
-// [i][cell][colour], each direction plane padded to `plane` cells.
-__device__ __forceinline__ long long pidx2(const StepArgs& a, int i,
-                                           long long cell) {
-  return ((long long)i * a.plane + cell) * 2;
+// Wrapped neighbour offsets of one column / plane (index d + 1 for x + d).
+struct ColOff {
+  unsigned xo[3], yo[3];
+  bool bxl, bxh, byl, byh;  // pull source beyond a wall (x-1 < 0, x+1 >= n)
+};
+struct PlaneOff {
+  unsigned zo[3];
+  bool bzl, bzh;
+};
+
+__device__ __forceinline__ int wrapn(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
 }
 
-// Pull streaming (Sec. II.A, below Eq. 13): f_i^k(x, t) = f_i^{k,+}(x - e_i,
-// t - 1), periodic wrap; where x - e_i lies beyond a wall, halfway
-// bounce-back gives f_i^k(x, t) = f_{opp(i)}^{k,+}(x, t - 1).
-template <typename T, int I>
-__device__ __forceinline__ void pull_one(const T* __restrict__ src,
-                                         const StepArgs& a, int x, int y,
-                                         int z, long long c, float* fR,
-                                         float* fB) {
-  int xs = x - ex(I), ys = y - ey(I), zs = z - ez(I);
-  bool out = (a.wx && (xs < 0 || xs >= a.nx)) ||
-             (a.wy && (ys < 0 || ys >= a.ny)) ||
-             (a.wz && (zs < 0 || zs >= a.nz));
-  long long cs;
-  int d;
-  if (out) {
-    cs = c;
-    d = opp(I);
-  } else {
-    cs = cell_of(a, wrap1(xs, a.nx), wrap1(ys, a.ny), wrap1(zs, a.nz));
-    d = I;
+// Pair index of the pulled value of direction I: f_I(x) comes from x - e_I,
+// or, beyond a wall, from direction opp(I) of x itself (halfway bounce-back).
+template <bool WALLS, int I>
+__device__ __forceinline__ unsigned pull_index(unsigned plane, const ColOff& c,
+                                               const PlaneOff& p) {
+  unsigned cs = p.zo[1 - ez(I)] + c.yo[1 - ey(I)] + c.xo[1 - ex(I)];
+  unsigned q = I;
+  if (WALLS) {
+    const bool out = (ex(I) > 0 && c.bxl) || (ex(I) < 0 && c.bxh) ||
+                     (ey(I) > 0 && c.byl) || (ey(I) < 0 && c.byh) ||
+                     (ez(I) > 0 && p.bzl) || (ez(I) < 0 && p.bzh);
+    if (out) {
+      cs = p.zo[1] + c.yo[1] + c.xo[1];
+      q = opp(I);
+    }
   }
-  const float2 v = Store<T>::load2(src + pidx2(a, d, cs));
-  float r = v.x, b = v.y;
-  if (Store<T>::kDeviation) {
-    // the offset belongs to the stored direction, which has the same shell
-    r += dev_offset<I>(a, 0);
-    b += dev_offset<I>(a, 1);
-  }
-  fR[I] = r;
-  fB[I] = b;
+  return q * plane + cs;
 }
 
+// Offsets of the cell (x, y, z), all in range, for pull_index.
+__device__ __forceinline__ ColOff col_off(const StepArgs& a, int x, int y) {
+  ColOff c;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    c.xo[d] = (unsigned)wrap1(x + d - 1, a.nx);
+    c.yo[d] = (unsigned)wrap1(y + d - 1, a.ny) * (unsigned)a.nx;
+  }
+  c.bxl = a.wx && x == 0;
+  c.bxh = a.wx && x == a.nx - 1;
+  c.byl = a.wy && y == 0;
+  c.byh = a.wy && y == a.ny - 1;
+  return c;
+}
+__device__ __forceinline__ PlaneOff plane_off(const StepArgs& a, int z) {
+  PlaneOff p;
+  const unsigned pc = (unsigned)a.nx * (unsigned)a.ny;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p.zo[d] = (unsigned)wrap1(z + d - 1, a.nz) * pc;
+  p.bzl = a.wz && z == 0;
+  p.bzh = a.wz && z == a.nz - 1;
+  return p;
+}
+
+// Pull of both colours of all 19 directions of one cell (walls handled at
+// run time), converted to FP32 with the deviation offsets added back.
 template <typename T, int I>
-struct PullAll {
-  __device__ __forceinline__ static void run(const T* __restrict__ src,
-                                             const StepArgs& a, int x, int y,
-                                             int z, long long c, float* fR,
+struct PullPairs {
+  __device__ __forceinline__ static void run(const typename Store<T>::Pair* src,
+                                             const StepArgs& a, const ColOff& c,
+                                             const PlaneOff& p, float* fR,
                                              float* fB) {
-    pull_one<T, I>(src, a, x, y, z, c, fR, fB);
-    PullAll<T, I + 1>::run(src, a, x, y, z, c, fR, fB);
+    float2 v = Store<T>::to_float2(__ldg(src + pull_index<true, I>((unsigned)a.plane, c, p)));
+    if (Store<T>::kDeviation) {
+      v.x += dev_offset<I>(a, 0);
+      v.y += dev_offset<I>(a, 1);
+    }
+    fR[I] = v.x;
+    fB[I] = v.y;
+    PullPairs<T, I + 1>::run(src, a, c, p, fR, fB);
   }
 };
 template <typename T>
-struct PullAll<T, 19> {
-  __device__ __forceinline__ static void run(const T* __restrict__,
-                                             const StepArgs&, int, int, int,
-                                             long long, float*, float*) {}
+struct PullPairs<T, 19> {
+  __device__ __forceinline__ static void run(const typename Store<T>::Pair*,
+                                             const StepArgs&, const ColOff&,
+                                             const PlaneOff&, float*, float*) {}
 };
-
 template <typename T>
-__device__ __forceinline__ void pull_cell(const T* __restrict__ src,
-                                          const StepArgs& a, int x, int y,
-                                          int z, float* fR, float* fB) {
-  PullAll<T, 0>::run(src, a, x, y, z, cell_of(a, x, y, z), fR, fB);
+__device__ __forceinline__ void pull_pairs(const T* src, const StepArgs& a, int x,
+                                           int y, int z, float* fR, float* fB) {
+  PullPairs<T, 0>::run(reinterpret_cast<const typename Store<T>::Pair*>(src), a,
+                       col_off(a, x, y), plane_off(a, z), fR, fB);
 }
 
 // Store of the post-recolouring populations at the cell itself (the next
 // step pulls them).
 template <typename T>
 __device__ __forceinline__ void store_cell(T* __restrict__ dst,
-                                           const StepArgs& a, long long c,
+                                           const StepArgs& a, unsigned c,
                                            const float* fR, const float* fB) {
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
@@ -226,7 +248,7 @@ __device__ __forceinline__ void store_cell(T* __restrict__ dst,
       r -= s == 0 ? a.offR0 : (s == 1 ? a.offR1 : a.offR2);
       b -= s == 0 ? a.offB0 : (s == 1 ? a.offB1 : a.offB2);
     }
-    Store<T>::store2(dst + pidx2(a, i, c), r, b);
+    Store<T>::store2(dst + 2 * ((size_t)i * (unsigned)a.plane + c), r, b);
   }
 }
 

@@ -36,40 +36,6 @@ namespace lbm {
 
 constexpr int kTileW = 32;  // threads along x per CTA (one warp)
 
-// Wrapped neighbour offsets of one column / plane (index d + 1 for x + d).
-struct ColOff {
-  unsigned xo[3], yo[3];
-  bool bxl, bxh, byl, byh;  // pull source beyond a wall (x-1 < 0, x+1 >= n)
-};
-struct PlaneOff {
-  unsigned zo[3];
-  bool bzl, bzh;
-};
-
-__device__ __forceinline__ int wrapn(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
-// Pair index of the pulled value of direction I: f_I(x) comes from x - e_I,
-// or, beyond a wall, from direction opp(I) of x itself (halfway bounce-back).
-template <bool WALLS, int I>
-__device__ __forceinline__ unsigned pull_index(unsigned plane, const ColOff& c,
-                                               const PlaneOff& p) {
-  unsigned cs = p.zo[1 - ez(I)] + c.yo[1 - ey(I)] + c.xo[1 - ex(I)];
-  unsigned q = I;
-  if (WALLS) {
-    const bool out = (ex(I) > 0 && c.bxl) || (ex(I) < 0 && c.bxh) ||
-                     (ey(I) > 0 && c.byl) || (ey(I) < 0 && c.byh) ||
-                     (ez(I) > 0 && p.bzl) || (ez(I) < 0 && p.bzh);
-    if (out) {
-      cs = p.zo[1] + c.yo[1] + c.xo[1];
-      q = opp(I);
-    }
-  }
-  return q * plane + cs;
-}
-
 template <typename T, int I>
 __device__ __forceinline__ void add_offsets(const StepArgs& a, float2& v) {
   if (Store<T>::kDeviation) {

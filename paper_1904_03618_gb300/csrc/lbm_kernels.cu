@@ -1,57 +1,53 @@
 // Auxiliary kernels (initialisation, state access, moments, FP64
 // diagnostics) and the two-pass form of the step, for sm_103a.
+//
+// Every kernel here maps threads to cells with a 3-D grid (x from the
+// thread index, y and z from the block index) and 32-bit cell indices, and
+// pulls through the same index function as the fused step (pull_index).
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
 
-// ---------------------------------------------------------------------------
-// Scatter of a full state f_i^k(x, t) into the pull-streaming buffer: the
-// value f_i(x) is stored where the next pull looks for it, i.e. at
-// x - e_i (wrapped), or, when x - e_i lies beyond a wall, at x in direction
-// opp(i) (halfway bounce-back).  The map is one-to-one.
-// ---------------------------------------------------------------------------
-template <typename T, int I>
-__device__ __forceinline__ void scatter_one(T* __restrict__ dst,
-                                            const StepArgs& a, int x, int y,
-                                            int z, long long c, float vr,
-                                            float vb) {
-  int xs = x - ex(I), ys = y - ey(I), zs = z - ez(I);
-  bool out = (a.wx && (xs < 0 || xs >= a.nx)) ||
-             (a.wy && (ys < 0 || ys >= a.ny)) ||
-             (a.wz && (zs < 0 || zs >= a.nz));
-  long long cs;
-  int d;
-  if (out) {
-    cs = c;
-    d = opp(I);
-  } else {
-    cs = cell_of(a, wrap1(xs, a.nx), wrap1(ys, a.ny), wrap1(zs, a.nz));
-    d = I;
-  }
-  if (Store<T>::kDeviation) {
-    vr -= dev_offset<I>(a, 0);
-    vb -= dev_offset<I>(a, 1);
-  }
-  Store<T>::store2(dst + pidx2(a, d, cs), vr, vb);
+constexpr int kAuxBlock = 128;
+
+struct CellPos {
+  int x, y, z;
+  unsigned c;
+};
+__device__ __forceinline__ bool cell_pos(const StepArgs& a, CellPos& p) {
+  p.x = blockIdx.x * blockDim.x + threadIdx.x;
+  p.y = blockIdx.y;
+  p.z = blockIdx.z;
+  if (p.x >= a.nx) return false;
+  p.c = ((unsigned)p.z * (unsigned)a.ny + (unsigned)p.y) * (unsigned)a.nx + (unsigned)p.x;
+  return true;
 }
 
+// ---------------------------------------------------------------------------
+// Scatter of a full state f_i^k(x, t) into the pull-streaming buffer: the
+// value f_i(x) is stored exactly where the next pull looks for it
+// (pull_index: x - e_i, or, beyond a wall, x itself in direction opp(i)).
+// The map is one-to-one.
+// ---------------------------------------------------------------------------
 template <typename T, int I>
 struct ScatterAll {
-  __device__ __forceinline__ static void run(T* __restrict__ dst,
-                                             const StepArgs& a, int x, int y,
-                                             int z, long long c,
-                                             const float* fR,
-                                             const float* fB) {
-    scatter_one<T, I>(dst, a, x, y, z, c, fR[I], fB[I]);
-    ScatterAll<T, I + 1>::run(dst, a, x, y, z, c, fR, fB);
+  __device__ __forceinline__ static void run(T* dst, const StepArgs& a,
+                                             const ColOff& co, const PlaneOff& po,
+                                             const float* fR, const float* fB) {
+    float r = fR[I], b = fB[I];
+    if (Store<T>::kDeviation) {
+      r -= dev_offset<I>(a, 0);
+      b -= dev_offset<I>(a, 1);
+    }
+    Store<T>::store2(dst + 2 * (size_t)pull_index<true, I>((unsigned)a.plane, co, po), r, b);
+    ScatterAll<T, I + 1>::run(dst, a, co, po, fR, fB);
   }
 };
 template <typename T>
 struct ScatterAll<T, 19> {
-  __device__ __forceinline__ static void run(T* __restrict__,
-                                             const StepArgs&, int, int, int,
-                                             long long, const float*,
+  __device__ __forceinline__ static void run(T*, const StepArgs&, const ColOff&,
+                                             const PlaneOff&, const float*,
                                              const float*) {}
 };
 
@@ -76,62 +72,48 @@ __device__ __forceinline__ void equilibrium(float rho, float alpha, float ux,
   }
 }
 
-__device__ __forceinline__ bool cell_coords(const StepArgs& a, long long c,
-                                            int& x, int& y, int& z) {
-  long long N = (long long)a.nx * a.ny * a.nz;
-  if (c >= N) return false;
-  x = (int)(c % a.nx);
-  long long r = c / a.nx;
-  y = (int)(r % a.ny);
-  z = (int)(r / a.ny);
-  return true;
-}
-
 template <typename T>
 __global__ void k_init_eq(T* __restrict__ dst, StepArgs a, float alpha_R,
                           float alpha_B, const float* __restrict__ rho_R,
                           const float* __restrict__ rho_B,
                           const float* __restrict__ u) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int x, y, z;
-  if (!cell_coords(a, c, x, y, z)) return;
-  long long N = (long long)a.nx * a.ny * a.nz;
-  float ux = u[c], uy = u[N + c], uz = u[2 * N + c];
+  CellPos p;
+  if (!cell_pos(a, p)) return;
+  const unsigned N = (unsigned)a.nx * (unsigned)a.ny * (unsigned)a.nz;
+  const float ux = u[p.c], uy = u[N + p.c], uz = u[2 * (size_t)N + p.c];
   float fR[19], fB[19];
-  equilibrium(rho_R[c], alpha_R, ux, uy, uz, a.improved, fR);
-  equilibrium(rho_B[c], alpha_B, ux, uy, uz, a.improved, fB);
-  ScatterAll<T, 0>::run(dst, a, x, y, z, c, fR, fB);
+  equilibrium(rho_R[p.c], alpha_R, ux, uy, uz, a.improved, fR);
+  equilibrium(rho_B[p.c], alpha_B, ux, uy, uz, a.improved, fB);
+  ScatterAll<T, 0>::run(dst, a, col_off(a, p.x, p.y), plane_off(a, p.z), fR, fB);
 }
 
 template <typename T>
 __global__ void k_set_f(T* __restrict__ dst, StepArgs a,
                         const float* __restrict__ f) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int x, y, z;
-  if (!cell_coords(a, c, x, y, z)) return;
-  long long N = (long long)a.nx * a.ny * a.nz;
+  CellPos p;
+  if (!cell_pos(a, p)) return;
+  const size_t N = (size_t)a.nx * a.ny * a.nz;
   float fR[19], fB[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    fR[i] = f[(long long)i * N + c];
-    fB[i] = f[(long long)(19 + i) * N + c];
+    fR[i] = f[i * N + p.c];
+    fB[i] = f[(19 + i) * N + p.c];
   }
-  ScatterAll<T, 0>::run(dst, a, x, y, z, c, fR, fB);
+  ScatterAll<T, 0>::run(dst, a, col_off(a, p.x, p.y), plane_off(a, p.z), fR, fB);
 }
 
 template <typename T>
 __global__ void k_get_f(const T* __restrict__ src, StepArgs a,
                         float* __restrict__ f) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int x, y, z;
-  if (!cell_coords(a, c, x, y, z)) return;
-  long long N = (long long)a.nx * a.ny * a.nz;
+  CellPos p;
+  if (!cell_pos(a, p)) return;
+  const size_t N = (size_t)a.nx * a.ny * a.nz;
   float fR[19], fB[19];
-  pull_cell<T>(src, a, x, y, z, fR, fB);
+  pull_pairs<T>(src, a, p.x, p.y, p.z, fR, fB);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    f[(long long)i * N + c] = fR[i];
-    f[(long long)(19 + i) * N + c] = fB[i];
+    f[i * N + p.c] = fR[i];
+    f[(19 + i) * N + p.c] = fB[i];
   }
 }
 
@@ -139,26 +121,30 @@ template <typename T>
 __global__ void k_moments(const T* __restrict__ src, StepArgs a,
                           float* __restrict__ rho_R, float* __restrict__ rho_B,
                           float* __restrict__ u) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int x, y, z;
-  if (!cell_coords(a, c, x, y, z)) return;
-  long long N = (long long)a.nx * a.ny * a.nz;
+  CellPos p;
+  if (!cell_pos(a, p)) return;
+  const size_t N = (size_t)a.nx * a.ny * a.nz;
   float fR[19], fB[19];
-  pull_cell<T>(src, a, x, y, z, fR, fB);
-  Macro m = macro_of(a, fR, fB);
-  if (rho_R) rho_R[c] = m.rR;
-  if (rho_B) rho_B[c] = m.rB;
+  pull_pairs<T>(src, a, p.x, p.y, p.z, fR, fB);
+  const Macro m = macro_of(a, fR, fB);
+  if (rho_R) rho_R[p.c] = m.rR;
+  if (rho_B) rho_B[p.c] = m.rB;
   if (u) {
-    u[c] = m.ux;
-    u[N + c] = m.uy;
-    u[2 * N + c] = m.uz;
+    u[p.c] = m.ux;
+    u[N + p.c] = m.uy;
+    u[2 * N + p.c] = m.uz;
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 diagnostics: per-block partial sums (warp shuffles, then shared
-// memory) into a scratch array, then one block folds the partials in a
-// fixed order, so the result is deterministic.
+// Diagnostics with FP64 results.  Each thread accumulates its cells' colour
+// masses, momentum and red-mass moments in FP32 with Neumaier compensation
+// (running sum plus running error), which keeps the sums to about FP64
+// accuracy at FP32 cost -- the part's FP64 rate is far below its FP32 rate.
+// The per-thread sums are converted to FP64 once, reduced per block (warp
+// shuffles, then shared memory) into a scratch array, and one warp per slot
+// folds the block partials in a fixed order, so the result is
+// deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kDiagBlock = 256;
 
@@ -173,77 +159,98 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kDiagBlock)
     k_diag_partial(const T* __restrict__ src, StepArgs a,
                    double* __restrict__ part) {
-  double acc[kDiagSlots];
-#pragma unroll
-  for (int s = 0; s < kDiagSlots; ++s) acc[s] = 0.0;
-  long long N = (long long)a.nx * a.ny * a.nz;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
-       c += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_coords(a, c, x, y, z);
+  // slots 0..4, 9..11 compensated sums; 5, 6, 8 counts; 7 max
+  CSum mR, mB, jx, jy, jz, cx, cy, cz;
+  unsigned n_nonfinite = 0, n_negative = 0, n_red = 0;
+  float umax = 0.f;
+  const unsigned nx = (unsigned)a.nx, ny = (unsigned)a.ny;
+  const unsigned N = nx * ny * (unsigned)a.nz;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += gridDim.x * blockDim.x) {
+    const unsigned x = c % nx, t = c / nx;
+    const unsigned y = t % ny, z = t / ny;
     float fR[19], fB[19];
-    pull_cell<T>(src, a, x, y, z, fR, fB);
+    pull_pairs<T>(src, a, (int)x, (int)y, (int)z, fR, fB);
     bool finite = true;
-#pragma unroll
-    for (int i = 0; i < 19; ++i)
-      finite = finite && isfinite(fR[i]) && isfinite(fB[i]);
-    Macro m = macro_of(a, fR, fB);
-    double rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+    CSum cR;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-      rR += (double)fR[i];
-      rB += (double)fB[i];
-      double fi = (double)fR[i] + (double)fB[i];
-      jx += ex(i) * fi;
-      jy += ey(i) * fi;
-      jz += ez(i) * fi;
+      finite = finite && isfinite(fR[i]) && isfinite(fB[i]);
+      cR.add(fR[i]);
+      mR.add(fR[i]);
+      mB.add(fB[i]);
+      if (ex(i)) {
+        jx.add(ex(i) * fR[i]);
+        jx.add(ex(i) * fB[i]);
+      }
+      if (ey(i)) {
+        jy.add(ey(i) * fR[i]);
+        jy.add(ey(i) * fB[i]);
+      }
+      if (ez(i)) {
+        jz.add(ez(i) * fR[i]);
+        jz.add(ez(i) * fB[i]);
+      }
     }
-    acc[0] += rR;
-    acc[1] += rB;
-    acc[2] += jx;
-    acc[3] += jy;
-    acc[4] += jz;
-    acc[5] += finite ? 0.0 : 1.0;
-    acc[6] += (m.rR < 0.f || m.rB < 0.f) ? 1.0 : 0.0;
-    double um = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy +
-                     (double)m.uz * m.uz);
-    if (finite && um > acc[7]) acc[7] = um;
-    acc[8] += phase_field(a, m.rR, m.rB) > 0.f ? 1.0 : 0.0;
-    acc[9] += rR * x;
-    acc[10] += rR * y;
-    acc[11] += rR * z;
+    const float rRc = cR.s + cR.c;
+    cx.add(rRc * (float)x);
+    cy.add(rRc * (float)y);
+    cz.add(rRc * (float)z);
+    const Macro m = macro_of(a, fR, fB);
+    n_nonfinite += finite ? 0u : 1u;
+    n_negative += (m.rR < 0.f || m.rB < 0.f) ? 1u : 0u;
+    const float um = sqrtf(m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    if (finite && um > umax) umax = um;
+    n_red += phase_field(a, m.rR, m.rB) > 0.f ? 1u : 0u;
   }
+  double acc[kDiagSlots] = {mR.value(), mB.value(), jx.value(), jy.value(),
+                            jz.value(), (double)n_nonfinite, (double)n_negative,
+                            (double)umax, (double)n_red, cx.value(), cy.value(),
+                            cz.value()};
   __shared__ double sh[kDiagBlock / 32][kDiagSlots];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < kDiagSlots; ++s) {
-    double v = (s == 7) ? warp_max(acc[s]) : warp_sum(acc[s]);
+    const double v = (s == 7) ? warp_max(acc[s]) : warp_sum(acc[s]);
     if (lane == 0) sh[wid][s] = v;
   }
   __syncthreads();
   if (threadIdx.x < kDiagSlots) {
-    int s = threadIdx.x;
+    const int s = threadIdx.x;
     double v = 0.0;
     for (int w = 0; w < kDiagBlock / 32; ++w)
       v = (s == 7) ? fmax(v, sh[w][s]) : v + sh[w][s];
-    part[(long long)blockIdx.x * kDiagSlots + s] = v;
+    part[(size_t)blockIdx.x * kDiagSlots + s] = v;
   }
 }
 
+// One warp per slot: lanes stride over the block partials, then a fixed
+// shuffle tree.
 __global__ void k_diag_final(const double* __restrict__ part, int nblocks,
                              double* __restrict__ out) {
-  int s = threadIdx.x;
+  const int s = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (s >= kDiagSlots) return;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    double p = part[(long long)b * kDiagSlots + s];
+  for (int b = lane; b < nblocks; b += 32) {
+    const double p = part[(size_t)b * kDiagSlots + s];
     v = (s == 7) ? fmax(v, p) : v + p;
   }
-  out[s] = v;
+  v = (s == 7) ? warp_max(v) : warp_sum(v);
+  if (lane == 0) out[s] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,41 +262,42 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_twopass_phase(const T* __restrict__ src, StepArgs a,
                     float4* __restrict__ mom) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int y = blockIdx.y * blockDim.y + threadIdx.y;
-  int z = blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
   float fR[19], fB[19];
-  pull_cell<T>(src, a, x, y, z, fR, fB);
-  Macro m = macro_of(a, fR, fB);
-  float q = qbar_scale(a, m.rR, m.rB);
-  mom[cell_of(a, x, y, z)] =
-      make_float4(phase_field(a, m.rR, m.rB), m.ux * q, m.uy * q, m.uz * q);
+  pull_pairs<T>(src, a, x, y, z, fR, fB);
+  const Macro m = macro_of(a, fR, fB);
+  mom[((unsigned)z * (unsigned)a.ny + (unsigned)y) * (unsigned)a.nx + (unsigned)x] =
+      stencil_entry(a, m);
 }
 
 // Neighbour x + e of the Eq. 49 stencil; beyond a wall the centre cell.
-__device__ __forceinline__ long long stencil_cell(const StepArgs& a, int x,
-                                                  int y, int z, int dx, int dy,
-                                                  int dz, long long c) {
-  int xn = x + dx, yn = y + dy, zn = z + dz;
+__device__ __forceinline__ unsigned stencil_cell(const StepArgs& a, int x,
+                                                 int y, int z, int dx, int dy,
+                                                 int dz, unsigned c) {
+  const int xn = x + dx, yn = y + dy, zn = z + dz;
   if ((a.wx && (xn < 0 || xn >= a.nx)) || (a.wy && (yn < 0 || yn >= a.ny)) ||
       (a.wz && (zn < 0 || zn >= a.nz)))
     return c;
-  return cell_of(a, wrap1(xn, a.nx), wrap1(yn, a.ny), wrap1(zn, a.nz));
+  return ((unsigned)wrap1(zn, a.nz) * (unsigned)a.ny + (unsigned)wrap1(yn, a.ny)) *
+             (unsigned)a.nx +
+         (unsigned)wrap1(xn, a.nx);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_twopass_collide(const T* __restrict__ src, T* __restrict__ dst,
                       StepArgs a, const float4* __restrict__ mom) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int y = blockIdx.y * blockDim.y + threadIdx.y;
-  int z = blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
   if (x >= a.nx || y >= a.ny) return;
-  long long c = cell_of(a, x, y, z);
+  const unsigned c = ((unsigned)z * (unsigned)a.ny + (unsigned)y) * (unsigned)a.nx + (unsigned)x;
   float fR[19], fB[19];
-  pull_cell<T>(src, a, x, y, z, fR, fB);
-  Macro m = macro_of(a, fR, fB);
+  pull_pairs<T>(src, a, x, y, z, fR, fB);
+  const Macro m = macro_of(a, fR, fB);
   // Eq. 49: d_a psi = 3 sum_i w_i psi(x + e_i) e_ia = (1/6) axis differences
   // + (1/12) diagonal differences, accumulated as differences of opposite
   // neighbours so that a uniform field gives an exactly zero gradient.
@@ -312,7 +320,7 @@ __global__ void __launch_bounds__(256)
       Qz += (ez(i) * w) * (vp.w - vm.w);
     }
   }
-  float rn = __ldg(&mom[c]).x;
+  const float rn = __ldg(&mom[c]).x;
   collide_cell(a, fR, fB, m, rn, Gx, Gy, Gz, Qx, Qy, Qz);
   store_cell<T>(dst, a, c, fR, fB);
 }
@@ -320,38 +328,33 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // Launchers (host side).
 // ---------------------------------------------------------------------------
-static inline unsigned blocks_for(long long n, int b) {
-  return (unsigned)((n + b - 1) / b);
+static inline dim3 aux_grid(const StepArgs& a) {
+  return dim3((a.nx + kAuxBlock - 1) / kAuxBlock, a.ny, a.nz);
 }
 
 template <typename T>
 cudaError_t launch_init_eq_t(void* dst, const StepArgs& a, float alpha_R,
                              float alpha_B, const float* rR, const float* rB,
                              const float* u, cudaStream_t s) {
-  long long N = (long long)a.nx * a.ny * a.nz;
-  k_init_eq<T><<<blocks_for(N, 128), 128, 0, s>>>((T*)dst, a, alpha_R, alpha_B,
-                                                   rR, rB, u);
+  k_init_eq<T><<<aux_grid(a), kAuxBlock, 0, s>>>((T*)dst, a, alpha_R, alpha_B, rR, rB, u);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_set_f_t(void* dst, const StepArgs& a, const float* f,
                            cudaStream_t s) {
-  long long N = (long long)a.nx * a.ny * a.nz;
-  k_set_f<T><<<blocks_for(N, 128), 128, 0, s>>>((T*)dst, a, f);
+  k_set_f<T><<<aux_grid(a), kAuxBlock, 0, s>>>((T*)dst, a, f);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_get_f_t(const void* src, const StepArgs& a, float* f,
                            cudaStream_t s) {
-  long long N = (long long)a.nx * a.ny * a.nz;
-  k_get_f<T><<<blocks_for(N, 128), 128, 0, s>>>((const T*)src, a, f);
+  k_get_f<T><<<aux_grid(a), kAuxBlock, 0, s>>>((const T*)src, a, f);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_moments_t(const void* src, const StepArgs& a, float* rR,
                              float* rB, float* u, cudaStream_t s) {
-  long long N = (long long)a.nx * a.ny * a.nz;
-  k_moments<T><<<blocks_for(N, 128), 128, 0, s>>>((const T*)src, a, rR, rB, u);
+  k_moments<T><<<aux_grid(a), kAuxBlock, 0, s>>>((const T*)src, a, rR, rB, u);
   return cudaGetLastError();
 }
 template <typename T>
@@ -360,7 +363,7 @@ cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
   k_diag_partial<T><<<nblocks, kDiagBlock, 0, s>>>((const T*)src, a, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_diag_final<<<1, 32, 0, s>>>(part, nblocks, out);
+  k_diag_final<<<1, 32 * kDiagSlots, 0, s>>>(part, nblocks, out);
   return cudaGetLastError();
 }
 template <typename T>
