@@ -324,23 +324,21 @@ def run_ours(args, rank, world, local_rank):
     # --- roofline of the dominant kernel --------------------------------
     peak, peak_kind = measured_peaks()
     alg_bytes = 2 * 38 * BYTES_PER_VALUE[args.storage] * N  # read + write per launch
-    if launches == 1:
-        achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    else:
-        # two-pass: the collide kernel carries the same algorithmic bytes;
-        # attribute the whole step (both launches) to it
-        achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    # launch_ms brackets one lbm_step call: the fused kernel's launch, or both
+    # launches of the two-pass form (charged together to the step's bytes)
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.kernel, args.storage, n)
 
     variants = None
     if rank == 0 and world == 1 and args.storage == "f32" and not args.no_variants:
         variants = storage_variants(lbm, dev, pd, rR, rB, u, n, args)
+    lat.close()
+    batch = batch_measure(args, dev) if (rank == 0 and args.batch > 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _, _ = cpu_oracle_sample(args.cpu_n, args.cpu_seconds)
 
-    lat.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -358,6 +356,7 @@ def run_ours(args, rank, world, local_rank):
                              "kernel_ms": launch_ms},
                 "clocks": clocks,
                 "storage_variants": variants,
+                "batch": batch,
                 "cpu_baseline": cpu,
                 "check": {"nonfinite_cells": diag[5], "negative_density_cells": diag[6],
                           "mass_R": diag[0], "mass_B": diag[1]}}
@@ -420,6 +419,62 @@ def storage_variants(lbm, dev, pd, rR, rB, u, n, args):
     return out
 
 
+def batch_measure(args, dev):
+    """Batched sweep: `args.batch` independent droplet cases of uneven cubic
+    sizes advanced together (one persistent launch per step, CUDA-graph
+    replay).  MLUPS over all cases, FP32 and FP16 storage."""
+    import numpy as np
+    import torch
+
+    from paper_1904_03618_gb300 import lbm, params as P, workloads
+    samples = workloads.droplet_sweep(args.batch, seed=1234)
+    cases = [P.droplet_case(s) for s in samples]
+    cells = sum(c["nx"] ** 3 for c in cases)
+    out = {"cases": len(cases), "cells": cells,
+           "edges": sorted({c["nx"] for c in cases}),
+           "workload": "droplet sweep: cubic boxes of edge 32/48/64/96, radius edge/4, "
+                       "density ratio U[1,20], sigma U[0.001,0.02], speed U[0,0.05] "
+                       "(half static), seed 1234"}
+    peak, _ = measured_peaks()
+    for storage in ("f32", "f16"):
+        plist = []
+        fields = []
+        for c, s in zip(cases, samples):
+            n = c["nx"]
+            f = workloads.droplet(n, n, n, 0.25 * n, c["rho_in_R"], 1.0,
+                                  velocity=(s["speed"], 0.0, 0.0))
+            p = lbm.make_params(storage=storage, **c)
+            p.ref_R, p.ref_B = storage_references(storage, c["rho_in_R"], 1.0, f[0], f[1])
+            plist.append(p)
+            fields.append(f)
+        stream = torch.cuda.Stream(dev)
+        b = lbm.Batch(plist, device=dev, stream=stream)
+        for k, f in enumerate(fields):
+            rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in f)
+            lbm.lbm_batch_init_fields(b.ctx, k, rR, rB, u)
+        stream.synchronize()
+        del fields
+        b.step(max(args.warmup, 4))
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(args.batch_steps)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / args.batch_steps
+        bad = sum(b.diagnostics(k, raise_unstable=False)[5] for k in range(0, len(cases), 64))
+        b.close()
+        mlups = cells / (ms * 1e-3) / 1e6
+        bpc = 304 if storage == "f32" else 152
+        out[storage] = {"value": mlups, "unit": "MLUPS", "ms_per_step": ms,
+                        "roofline_frac": mlups * 1e6 * bpc / (peak * 1e9),
+                        "steps": args.batch_steps, "gpu_launches_per_step": 1,
+                        "nonfinite_cells_sampled": bad}
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,6 +491,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=200)
+    ap.add_argument("--batch", type=int, default=512,
+                    help="number of cases of the batched droplet sweep (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=30)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -124,13 +124,17 @@ lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
 /* FP64 whole-lattice diagnostics into the host array out[16]:
    [0] sum rho_R   [1] sum rho_B   [2..4] sum_i sum_k e_i f_i^k (momentum)
    [5] count of cells with a non-finite population
-   [6] count of cells with rho_R < 0 or rho_B < 0
+   [6] count of cells with total density rho <= 0
    [7] max |u|     [8] count of cells with rho^N > 0
    [9..11] red-mass centroid (sum rho_R x / sum rho_R, lattice coordinates,
            no periodic unwrapping)
-   [12] number of completed steps   [13..15] 0 (reserved).
-   Synchronises the context stream.  Returns LBM_ERR_UNSTABLE if [5] or [6]
-   is non-zero (out is still filled). */
+   [12] number of completed steps
+   [13] count of cells with rho_R < 0 or rho_B < 0 (small negative colour
+        densities in the minority phase are a normal effect of the
+        recolouring, Eq. 10-11; informational)   [14..15] 0 (reserved).
+   Sums are accumulated in compensated FP32 per thread and FP64 across
+   threads.  Synchronises the context stream.  Returns LBM_ERR_UNSTABLE if
+   [5] or [6] is non-zero (out is still filled). */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[16]);
 
 /* Copies f_i^k(x, t) -- the populations after streaming at the current
@@ -158,6 +162,7 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
 
 /* Launch configuration of the fused kernel (LBM_KERNEL_FUSED), the knob the
    autotuner turns; results are identical for every valid configuration.
+   Batch contexts accept (tile_y, hold) = (8, 2), (8, 0) or (16, 1).
    tile_y: CTA rows including the one-cell ring, 8 or 16 (the interior tile
    is 30 x (tile_y - 2) cells).  zchunk: planes marched per CTA, 0 = the
    library's default for this lattice.  hold: where the populations of a
@@ -174,6 +179,35 @@ lbm_status lbm_get_fused_config(const lbm_ctx *ctx, int *tile_y, int *zchunk,
 /* Number of kernel launches one lbm_step(ctx, 1) issues (1 for the fused
    kernel, 2 for the two-pass form). */
 int lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* ---- Batches: many independent lattices advanced together --------------
+   A batch context holds `ncases` lattices ("cases"), each with its own
+   lbm_params (size, walls, densities, alpha, relaxation times, surface
+   tension, beta, forces); all cases share storage (p->storage) and run the
+   fused kernel.  lbm_step advances every case by n steps with one kernel
+   launch per step: persistent CTAs take (case, tile, z-chunk) work items in
+   turn, so cases of uneven sizes share the GPU without idle tails.  Cases
+   must be initialised (lbm_batch_init_fields or lbm_batch_set_f) before
+   lbm_step.  The single-lattice calls (lbm_init_fields, lbm_moments,
+   lbm_diagnostics, lbm_get_f, lbm_set_f) act on case 0 of a batch. */
+lbm_status lbm_create_batch(const lbm_params *cases, int ncases,
+                            void *cuda_stream, lbm_ctx **out);
+int lbm_num_cases(const lbm_ctx *ctx);
+lbm_status lbm_batch_init_fields(lbm_ctx *ctx, int case_index,
+                                 const float *rho_R, const float *rho_B,
+                                 const float *u);
+lbm_status lbm_batch_moments(lbm_ctx *ctx, int case_index, float *rho_R,
+                             float *rho_B, float *u);
+lbm_status lbm_batch_diagnostics(lbm_ctx *ctx, int case_index,
+                                 double out[16]);
+lbm_status lbm_batch_get_f(lbm_ctx *ctx, int case_index, float *f);
+lbm_status lbm_batch_set_f(lbm_ctx *ctx, int case_index, const float *f);
+
+/* lbm_step(ctx, n) with n >= 4 on a non-default stream replays two steps
+   captured once into a CUDA graph (the first such call also runs two plain
+   steps before capturing).  enable = 0 launches every step directly.  The
+   result does not depend on it. */
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* One time step that allocates no device memory, for callers that cannot
    call cudaMalloc (code that runs while a stream is being captured into a

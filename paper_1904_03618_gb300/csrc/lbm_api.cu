@@ -13,24 +13,39 @@
 
 using lbm::StepArgs;
 
-struct lbm_ctx {
+// One lattice of a context.  A single-lattice context has one case.
+struct CaseRec {
   lbm_params p;
-  StepArgs args;
+  StepArgs args;        // args.plane = the case's padded cell count
+  long long N;          // cells
+  long long pair_base;  // offset of the case within each buffer, in pairs
+  int initialized;
+};
+
+struct lbm_ctx {
+  CaseRec* cases;
+  int ncases;
+  int storage, kernel;
   lbm::FusedConfig fused;
   cudaStream_t stream;
-  int device;
-  size_t elem;          // bytes per stored population value
-  long long N;          // cells
-  void* pop[2];         // ping-pong population buffers
-  int cur;              // buffer holding the current state (pull layout)
-  float4* phase;        // two-pass scratch: (rho^N, Qbar) per cell
-  double* diag_part;    // per-block partial sums of lbm_diagnostics
-  double* diag_out;     // folded sums (device)
+  int device, sms;
+  size_t elem;              // bytes per stored population value
+  long long total_pairs;    // pairs per buffer over all cases
+  long long max_cells;      // largest case
+  bool any_walls;
+  void* pop[2];             // ping-pong population buffers
+  int cur;                  // buffer holding the current state (pull layout)
+  float4* phase;            // two-pass scratch: (rho^N, Qbar) per cell
+  double* diag_part;        // per-block partial sums of the diagnostics
+  double* diag_out;         // folded sums (device)
   int diag_blocks;
-  float* staging;       // device staging for host-pointer transfers
+  float* staging;           // device staging for host-pointer transfers
   size_t staging_floats;
+  lbm::BatchCase* d_cases;  // device case table of the batched kernel
+  int total_items;
+  cudaGraphExec_t graph;    // two captured steps (buffer 0 -> 1 -> 0)
+  int use_graph;
   long long steps;
-  int initialized;
   char err[512];
 };
 
@@ -158,20 +173,6 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
   return a;
 }
 
-static void release(lbm_ctx* c) {
-  if (!c) return;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (c->device >= 0) cudaSetDevice(c->device);
-  cudaFree(c->pop[0]);
-  cudaFree(c->pop[1]);
-  cudaFree(c->phase);
-  cudaFree(c->diag_part);
-  cudaFree(c->diag_out);
-  cudaFree(c->staging);
-  if (prev >= 0) cudaSetDevice(prev);
-}
-
 // Shared with the other host translation units (declared in lbm_internal.h).
 namespace lbm {
 lbm_status validate_params(const lbm_params* p) { return validate(p); }
@@ -185,62 +186,165 @@ bool is_device_pointer(const void* ptr) { return is_device_ptr(ptr); }
 void clear_thread_error() { g_create_err[0] = 0; }
 }  // namespace lbm
 
-extern "C" lbm_status lbm_create(const lbm_params* p, void* cuda_stream,
-                                 lbm_ctx** out) {
+static void release(lbm_ctx* c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (c->device >= 0) cudaSetDevice(c->device);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  cudaFree(c->pop[0]);
+  cudaFree(c->pop[1]);
+  cudaFree(c->phase);
+  cudaFree(c->diag_part);
+  cudaFree(c->diag_out);
+  cudaFree(c->staging);
+  cudaFree(c->d_cases);
+  delete[] c->cases;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+static void drop_graph(lbm_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+// Rebuilds the batched kernel's device case table for the current fused
+// configuration (tile counts and item numbering depend on it).
+static lbm_status upload_case_table(lbm_ctx* c) {
+  if (c->ncases <= 1) return LBM_OK;
+  lbm::BatchCase* h = new (std::nothrow) lbm::BatchCase[c->ncases];
+  if (!h) return fail(c, LBM_ERR_OOM, "host allocation failed");
+  const int ty = c->fused.tile_y, zc = c->fused.zchunk;
+  long long items = 0;
+  for (int k = 0; k < c->ncases; ++k) {
+    const CaseRec& r = c->cases[k];
+    h[k].args = r.args;
+    h[k].pair_base = r.pair_base;
+    h[k].item_start = (int)items;
+    h[k].tiles_x = (r.p.nx + 29) / 30;
+    h[k].tiles_y = (r.p.ny + ty - 3) / (ty - 2);
+    h[k].pad_ = 0;
+    items += (long long)h[k].tiles_x * h[k].tiles_y * ((r.p.nz + zc - 1) / zc);
+  }
+  if (items >= (1LL << 31)) {
+    delete[] h;
+    return fail(c, LBM_ERR_ARG, "batch too large: more than 2^31 work items");
+  }
+  cudaError_t e = cudaMemcpyAsync(c->d_cases, h, sizeof(lbm::BatchCase) * c->ncases,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  delete[] h;
+  if (e != cudaSuccess) return cuda_fail(c, e, "upload of the case table");
+  c->total_items = (int)items;
+  drop_graph(c);
+  return LBM_OK;
+}
+
+static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream,
+                             lbm_ctx** out) {
   g_create_err[0] = 0;
   if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
   *out = nullptr;
-  lbm_status st = validate(p);
-  if (st != LBM_OK) return st;
+  if (!ps || ncases < 1) return fail(nullptr, LBM_ERR_ARG, "need at least one case");
+  for (int k = 0; k < ncases; ++k) {
+    lbm_status st = validate(&ps[k]);
+    if (st != LBM_OK) {
+      if (ncases > 1) {
+        char buf[512];
+        snprintf(buf, sizeof(buf), "case %d: %s", k, g_create_err);
+        return fail(nullptr, st, "%s", buf);
+      }
+      return st;
+    }
+    if (ps[k].storage != ps[0].storage || ps[k].kernel != ps[0].kernel)
+      return fail(nullptr, LBM_ERR_ARG, "all cases of a batch need the same storage and kernel");
+  }
+  if (ncases > 1 && ps[0].kernel != LBM_KERNEL_FUSED)
+    return fail(nullptr, LBM_ERR_ARG, "batches run the fused kernel only");
   lbm_ctx* c = new (std::nothrow) lbm_ctx;
   if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
   memset(c, 0, sizeof(*c));
-  c->p = *p;
+  c->cases = new (std::nothrow) CaseRec[ncases];
+  if (!c->cases) {
+    delete c;
+    return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+  }
+  c->ncases = ncases;
+  c->storage = ps[0].storage;
+  c->kernel = ps[0].kernel;
   c->device = -1;
   c->stream = (cudaStream_t)cuda_stream;
+  c->use_graph = 1;
   cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
+    delete[] c->cases;
     delete c;
-    return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    return fail(nullptr, LBM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
   }
-  c->elem = p->storage == LBM_F32 ? 4 : 2;
-  c->N = (long long)p->nx * p->ny * p->nz;
-  // Each (colour, direction) plane starts on a 256-byte boundary.
-  long long per = 256 / (long long)c->elem;
-  long long plane = (c->N + per - 1) / per * per;
-  c->args = derive_args(p, plane);
-  c->fused = lbm::default_fused_config(c->args, p->storage);
-  size_t bytes = (size_t)plane * 38 * c->elem;
-  for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&c->pop[b], bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      release(c);
-      delete c;
-      return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+  c->elem = c->storage == LBM_F32 ? 4 : 2;
+  long long pairs = 0;
+  for (int k = 0; k < ncases; ++k) {
+    CaseRec& r = c->cases[k];
+    r.p = ps[k];
+    r.N = (long long)r.p.nx * r.p.ny * r.p.nz;
+    const long long plane = (r.N + 63) / 64 * 64;  // 256-byte aligned planes
+    r.args = derive_args(&r.p, plane);
+    r.pair_base = pairs;
+    r.initialized = 0;
+    pairs += 19 * plane;
+    if (r.N > c->max_cells) c->max_cells = r.N;
+    c->any_walls = c->any_walls || r.p.wall[0] || r.p.wall[1] || r.p.wall[2];
+  }
+  c->total_pairs = pairs;
+  c->fused = lbm::default_fused_config(c->cases[0].args, c->storage);
+  if (ncases > 1) c->fused.zchunk = 12;
+  const size_t bytes = (size_t)pairs * 2 * c->elem;
+  lbm_status st = LBM_OK;
+  for (int b = 0; b < 2 && st == LBM_OK; ++b)
+    if (cudaMalloc(&c->pop[b], bytes) != cudaSuccess)
+      st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+  if (st == LBM_OK && c->kernel == LBM_KERNEL_TWO_PASS &&
+      cudaMalloc(&c->phase, sizeof(float4) * (size_t)c->max_cells) != cudaSuccess)
+    st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the phase field failed");
+  if (st == LBM_OK) {
+    long long nb = (c->max_cells + 255) / 256;
+    c->diag_blocks = (int)(nb < 4 * c->sms ? nb : 4 * c->sms);
+    if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
+        cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess)
+      st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
+  }
+  if (st == LBM_OK && ncases > 1 &&
+      cudaMalloc(&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
+    st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the case table failed");
+  if (st == LBM_OK) {
+    st = upload_case_table(c);
+    if (st != LBM_OK) {
+      char buf[512];
+      snprintf(buf, sizeof(buf), "%s", c->err);
+      st = fail(nullptr, st, "%s", buf);
     }
   }
-  if (p->kernel == LBM_KERNEL_TWO_PASS) {
-    e = cudaMalloc(&c->phase, sizeof(float4) * (size_t)c->N);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      release(c);
-      delete c;
-      return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the phase field failed");
-    }
-  }
-  long long nb = (c->N + 255) / 256;
-  c->diag_blocks = (int)(nb < 4 * 152 ? nb : 4 * 152);
-  if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
-      cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess) {
+  if (st != LBM_OK) {
     cudaGetLastError();
     release(c);
     delete c;
-    return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
+    return st;
   }
   c->err[0] = 0;
   *out = c;
   return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(const lbm_params* p, void* cuda_stream,
+                                 lbm_ctx** out) {
+  return create_ctx(p, 1, cuda_stream, out);
+}
+
+extern "C" lbm_status lbm_create_batch(const lbm_params* cases, int ncases,
+                                       void* cuda_stream, lbm_ctx** out) {
+  return create_ctx(cases, ncases, cuda_stream, out);
 }
 
 extern "C" void lbm_destroy(lbm_ctx* c) {
@@ -255,11 +359,14 @@ extern "C" const char* lbm_last_error(const lbm_ctx* c) {
   return c ? c->err : g_create_err;
 }
 
+extern "C" int lbm_num_cases(const lbm_ctx* c) { return c ? c->ncases : 0; }
+
 static lbm_status ensure_staging(lbm_ctx* c, size_t floats) {
   if (c->staging_floats >= floats) return LBM_OK;
   cudaFree(c->staging);
   c->staging = nullptr;
   c->staging_floats = 0;
+  drop_graph(c);
   if (cudaMalloc(&c->staging, floats * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, LBM_ERR_OOM, "cudaMalloc of %zu staging floats failed", floats);
@@ -283,87 +390,159 @@ static lbm_status device_input(lbm_ctx* c, const float* ptr, size_t n,
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_init_fields(lbm_ctx* c, const float* rho_R,
-                                      const float* rho_B, const float* u,
-                                      const unsigned char* solid) {
+// Buffer b of case k, as a byte pointer.
+static char* case_buffer(lbm_ctx* c, int b, int k) {
+  return (char*)c->pop[b] + (size_t)c->cases[k].pair_base * 2 * c->elem;
+}
+
+static lbm_status check_case(lbm_ctx* c, int k) {
+  if (k < 0 || k >= c->ncases)
+    return fail(c, LBM_ERR_ARG, "case index %d out of range [0, %d)", k, c->ncases);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_R,
+                                            const float* rho_B, const float* u) {
   if (!c) return LBM_ERR_ARG;
+  lbm_status st = check_case(c, k);
+  if (st != LBM_OK) return st;
   if (!rho_R || !rho_B || !u) return fail(c, LBM_ERR_ARG, "NULL field pointer");
-  if (solid) return fail(c, LBM_ERR_ARG, "solid masks are not supported; use wall[]");
-  size_t N = (size_t)c->N;
-  bool all_dev = is_device_ptr(rho_R) && is_device_ptr(rho_B) && is_device_ptr(u);
-  if (!all_dev) {
-    lbm_status st = ensure_staging(c, 5 * N);
-    if (st != LBM_OK) return st;
-  }
+  CaseRec& r = c->cases[k];
+  const size_t N = (size_t)r.N;
+  const bool all_dev = is_device_ptr(rho_R) && is_device_ptr(rho_B) && is_device_ptr(u);
+  if (!all_dev && (st = ensure_staging(c, 5 * N)) != LBM_OK) return st;
   const float *dR, *dB, *dU;
-  lbm_status st;
   if ((st = device_input(c, rho_R, N, 0, &dR)) != LBM_OK) return st;
   if ((st = device_input(c, rho_B, N, N, &dB)) != LBM_OK) return st;
   if ((st = device_input(c, u, 3 * N, 2 * N, &dU)) != LBM_OK) return st;
-  LBM_CUDA(c, lbm::launch_init_eq(c->p.storage, c->pop[0], c->args,
-                                  (float)c->p.alpha_R, (float)c->p.alpha_B, dR,
-                                  dB, dU, c->stream),
+  LBM_CUDA(c, lbm::launch_init_eq(c->storage, case_buffer(c, c->cur, k), r.args,
+                                  (float)r.p.alpha_R, (float)r.p.alpha_B, dR, dB, dU,
+                                  c->stream),
            "init kernel");
-  c->cur = 0;
+  r.initialized = 1;
   c->steps = 0;
-  c->initialized = 1;
   c->err[0] = 0;
   return LBM_OK;
 }
 
-static lbm_status step_once(lbm_ctx* c) {
-  const void* src = c->pop[c->cur];
-  void* dst = c->pop[c->cur ^ 1];
+extern "C" lbm_status lbm_init_fields(lbm_ctx* c, const float* rho_R,
+                                      const float* rho_B, const float* u,
+                                      const unsigned char* solid) {
+  if (!c) return LBM_ERR_ARG;
+  if (solid) return fail(c, LBM_ERR_ARG, "solid masks are not supported; use wall[]");
+  return lbm_batch_init_fields(c, 0, rho_R, rho_B, u);
+}
+
+static lbm_status launch_step(lbm_ctx* c, int from) {
+  const void* src = c->pop[from];
+  void* dst = c->pop[from ^ 1];
   cudaError_t e;
-  if (c->p.kernel == LBM_KERNEL_TWO_PASS)
-    e = lbm::launch_twopass(c->p.storage, src, dst, c->args, c->phase, c->stream);
+  if (c->ncases > 1)
+    e = lbm::launch_fused_batch(c->storage, src, dst, c->d_cases, c->ncases,
+                                c->total_items, c->any_walls, c->fused, c->sms,
+                                c->stream);
+  else if (c->kernel == LBM_KERNEL_TWO_PASS)
+    e = lbm::launch_twopass(c->storage, src, dst, c->cases[0].args, c->phase, c->stream);
   else
-    e = lbm::launch_fused(c->p.storage, src, dst, c->args, c->fused, c->stream);
+    e = lbm::launch_fused(c->storage, src, dst, c->cases[0].args, c->fused, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-  c->cur ^= 1;
-  c->steps += 1;
+  return LBM_OK;
+}
+
+// Two steps (buffer 0 -> 1 -> 0) captured once into a CUDA graph.
+static lbm_status ensure_graph(lbm_ctx* c) {
+  if (c->graph) return LBM_OK;
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal),
+           "cudaStreamBeginCapture");
+  lbm_status st = launch_step(c, 0);
+  if (st == LBM_OK) st = launch_step(c, 1);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (st != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
   return LBM_OK;
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
-  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_f");
-  for (int s = 0; s < n; ++s) {
-    lbm_status st = step_once(c);
-    if (st != LBM_OK) return st;
+  for (int k = 0; k < c->ncases; ++k)
+    if (!c->cases[k].initialized)
+      return fail(c, LBM_ERR_STATE, "lbm_step before every case was initialised (case %d)", k);
+  // CUDA graphs need a capturable stream (not the legacy default stream).
+  const bool graphs = c->use_graph && c->stream != nullptr && n >= 4;
+  lbm_status st;
+  if (graphs) {
+    // Bring the state to buffer 0; before the first capture also run two
+    // plain steps, so that one-time kernel attribute and occupancy queries
+    // happen outside stream capture.
+    const int plain = (c->cur == 1 ? 1 : 0) + (c->graph ? 0 : 2);
+    for (int q = 0; q < plain; ++q) {
+      if ((st = launch_step(c, c->cur)) != LBM_OK) return st;
+      c->cur ^= 1;
+      c->steps += 1;
+      n -= 1;
+    }
+    if ((st = ensure_graph(c)) != LBM_OK) return st;
+    for (; n >= 2; n -= 2) {
+      LBM_CUDA(c, cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch");
+      c->steps += 2;
+    }
+  }
+  for (; n > 0; --n) {
+    if ((st = launch_step(c, c->cur)) != LBM_OK) return st;
+    c->cur ^= 1;
+    c->steps += 1;
   }
   c->err[0] = 0;
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
-                                  float* u) {
+extern "C" lbm_status lbm_set_graphs(lbm_ctx* c, int enable) {
   if (!c) return LBM_ERR_ARG;
-  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_moments before init");
-  size_t N = (size_t)c->N;
+  c->use_graph = enable ? 1 : 0;
+  if (!enable) drop_graph(c);
+  return LBM_OK;
+}
+
+static bool case_ready(lbm_ctx* c, int k) { return c->cases[k].initialized != 0; }
+
+extern "C" lbm_status lbm_batch_moments(lbm_ctx* c, int k, float* rho_R,
+                                        float* rho_B, float* u) {
+  if (!c) return LBM_ERR_ARG;
+  lbm_status st = check_case(c, k);
+  if (st != LBM_OK) return st;
+  if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "moments before init");
+  const CaseRec& r = c->cases[k];
+  const size_t N = (size_t)r.N;
   float* outs[3] = {rho_R, rho_B, u};
-  size_t sizes[3] = {N, N, 3 * N};
-  size_t slots[3] = {0, N, 2 * N};
+  const size_t sizes[3] = {N, N, 3 * N};
+  const size_t slots[3] = {0, N, 2 * N};
   bool host[3];
   bool any_host = false;
-  for (int k = 0; k < 3; ++k) {
-    host[k] = outs[k] && !is_device_ptr(outs[k]);
-    any_host = any_host || host[k];
+  for (int q = 0; q < 3; ++q) {
+    host[q] = outs[q] && !is_device_ptr(outs[q]);
+    any_host = any_host || host[q];
   }
-  if (any_host) {
-    lbm_status st = ensure_staging(c, 5 * N);
-    if (st != LBM_OK) return st;
-  }
+  if (any_host && (st = ensure_staging(c, 5 * N)) != LBM_OK) return st;
   float* k_out[3];
-  for (int k = 0; k < 3; ++k)
-    k_out[k] = !outs[k] ? nullptr : (host[k] ? c->staging + slots[k] : outs[k]);
-  LBM_CUDA(c, lbm::launch_moments(c->p.storage, c->pop[c->cur], c->args,
+  for (int q = 0; q < 3; ++q)
+    k_out[q] = !outs[q] ? nullptr : (host[q] ? c->staging + slots[q] : outs[q]);
+  LBM_CUDA(c, lbm::launch_moments(c->storage, case_buffer(c, c->cur, k), r.args,
                                   k_out[0], k_out[1], k_out[2], c->stream),
            "moments kernel");
-  for (int k = 0; k < 3; ++k)
-    if (host[k])
-      LBM_CUDA(c, cudaMemcpyAsync(outs[k], k_out[k], sizes[k] * sizeof(float),
+  for (int q = 0; q < 3; ++q)
+    if (host[q])
+      LBM_CUDA(c, cudaMemcpyAsync(outs[q], k_out[q], sizes[q] * sizeof(float),
                                   cudaMemcpyDeviceToHost, c->stream),
                "cudaMemcpyAsync D2H");
   if (any_host) LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
@@ -371,12 +550,21 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
+extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
+                                  float* u) {
+  return lbm_batch_moments(c, 0, rho_R, rho_B, u);
+}
+
+extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
-  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_diagnostics before init");
-  LBM_CUDA(c, lbm::launch_diag(c->p.storage, c->pop[c->cur], c->args,
-                               c->diag_part, c->diag_blocks, c->diag_out,
-                               c->stream),
+  lbm_status st = check_case(c, k);
+  if (st != LBM_OK) return st;
+  if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "diagnostics before init");
+  const CaseRec& r = c->cases[k];
+  long long nb = (r.N + 255) / 256;
+  const int blocks = (int)(nb < c->diag_blocks ? nb : c->diag_blocks);
+  LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
+                               c->diag_part, blocks, c->diag_out, c->stream),
            "diagnostics kernels");
   double d[lbm::kDiagSlots];
   LBM_CUDA(c, cudaMemcpyAsync(d, c->diag_out, sizeof(d), cudaMemcpyDeviceToHost,
@@ -384,32 +572,40 @@ extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
            "cudaMemcpyAsync D2H");
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   for (int i = 0; i < 16; ++i) out[i] = 0.0;
-  for (int i = 0; i < lbm::kDiagSlots; ++i) out[i] = d[i];
+  for (int i = 0; i < 12; ++i) out[i] = d[i];
   if (d[0] > 0) {
     out[9] = d[9] / d[0];
     out[10] = d[10] / d[0];
     out[11] = d[11] / d[0];
   }
   out[12] = (double)c->steps;
+  out[13] = d[12];
   c->err[0] = 0;
   if (d[5] != 0.0 || d[6] != 0.0)
     return fail(c, LBM_ERR_UNSTABLE,
-                "%.0f cells with non-finite populations, %.0f with negative density",
+                "%.0f cells with non-finite populations, %.0f with total density <= 0",
                 d[5], d[6]);
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_get_f(lbm_ctx* c, float* f) {
+extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
+  return lbm_batch_diagnostics(c, 0, out);
+}
+
+extern "C" lbm_status lbm_batch_get_f(lbm_ctx* c, int k, float* f) {
   if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
-  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_get_f before init");
-  size_t n = 38 * (size_t)c->N;
+  lbm_status st = check_case(c, k);
+  if (st != LBM_OK) return st;
+  if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "get_f before init");
+  const CaseRec& r = c->cases[k];
+  const size_t n = 38 * (size_t)r.N;
   if (is_device_ptr(f)) {
-    LBM_CUDA(c, lbm::launch_get_f(c->p.storage, c->pop[c->cur], c->args, f, c->stream),
+    LBM_CUDA(c, lbm::launch_get_f(c->storage, case_buffer(c, c->cur, k), r.args, f,
+                                  c->stream),
              "get_f kernel");
   } else {
-    lbm_status st = ensure_staging(c, n);
-    if (st != LBM_OK) return st;
-    LBM_CUDA(c, lbm::launch_get_f(c->p.storage, c->pop[c->cur], c->args,
+    if ((st = ensure_staging(c, n)) != LBM_OK) return st;
+    LBM_CUDA(c, lbm::launch_get_f(c->storage, case_buffer(c, c->cur, k), r.args,
                                   c->staging, c->stream),
              "get_f kernel");
     LBM_CUDA(c, cudaMemcpyAsync(f, c->staging, n * sizeof(float),
@@ -421,34 +617,41 @@ extern "C" lbm_status lbm_get_f(lbm_ctx* c, float* f) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_set_f(lbm_ctx* c, const float* f) {
+extern "C" lbm_status lbm_get_f(lbm_ctx* c, float* f) { return lbm_batch_get_f(c, 0, f); }
+
+extern "C" lbm_status lbm_batch_set_f(lbm_ctx* c, int k, const float* f) {
   if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
-  size_t n = 38 * (size_t)c->N;
+  lbm_status st = check_case(c, k);
+  if (st != LBM_OK) return st;
+  CaseRec& r = c->cases[k];
+  const size_t n = 38 * (size_t)r.N;
   const float* src = f;
   if (!is_device_ptr(f)) {
-    lbm_status st = ensure_staging(c, n);
-    if (st != LBM_OK) return st;
+    if ((st = ensure_staging(c, n)) != LBM_OK) return st;
     LBM_CUDA(c, cudaMemcpyAsync(c->staging, f, n * sizeof(float),
                                 cudaMemcpyHostToDevice, c->stream),
              "cudaMemcpyAsync H2D");
     src = c->staging;
   }
-  LBM_CUDA(c, lbm::launch_set_f(c->p.storage, c->pop[0], c->args, src, c->stream),
+  LBM_CUDA(c, lbm::launch_set_f(c->storage, case_buffer(c, c->cur, k), r.args, src,
+                                c->stream),
            "set_f kernel");
-  c->cur = 0;
+  r.initialized = 1;
   c->steps = 0;
-  c->initialized = 1;
   c->err[0] = 0;
   return LBM_OK;
 }
 
+extern "C" lbm_status lbm_set_f(lbm_ctx* c, const float* f) { return lbm_batch_set_f(c, 0, f); }
+
 extern "C" size_t lbm_population_bytes(const lbm_ctx* c) {
-  return c ? (size_t)c->args.plane * 38 * c->elem : 0;
+  return c ? (size_t)c->total_pairs * 2 * c->elem : 0;
 }
 
 extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
   if (!c || !dst) return c ? fail(c, LBM_ERR_ARG, "dst is NULL") : LBM_ERR_ARG;
-  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_get_populations before init");
+  for (int k = 0; k < c->ncases; ++k)
+    if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "lbm_get_populations before init");
   LBM_CUDA(c, cudaMemcpyAsync(dst, c->pop[c->cur], lbm_population_bytes(c),
                               cudaMemcpyDefault, c->stream),
            "cudaMemcpyAsync");
@@ -459,12 +662,11 @@ extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
 
 extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
   if (!c || !src) return c ? fail(c, LBM_ERR_ARG, "src is NULL") : LBM_ERR_ARG;
-  LBM_CUDA(c, cudaMemcpyAsync(c->pop[0], src, lbm_population_bytes(c),
+  LBM_CUDA(c, cudaMemcpyAsync(c->pop[c->cur], src, lbm_population_bytes(c),
                               cudaMemcpyDefault, c->stream),
            "cudaMemcpyAsync");
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
-  c->cur = 0;
-  c->initialized = 1;
+  for (int k = 0; k < c->ncases; ++k) c->cases[k].initialized = 1;
   c->err[0] = 0;
   return LBM_OK;
 }
@@ -475,13 +677,21 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
   lbm::FusedConfig f;
   f.tile_y = tile_y;
   f.hold = hold;
-  f.zchunk = zchunk == 0 ? lbm::default_fused_config(c->args, c->p.storage).zchunk
-                         : zchunk;
-  if (zchunk < 0 || !lbm::valid_fused_config(f, c->p.storage))
+  f.zchunk = zchunk == 0
+                 ? (c->ncases > 1 ? 12 : lbm::default_fused_config(c->cases[0].args, c->storage).zchunk)
+                 : zchunk;
+  const bool ok = zchunk >= 0 && (c->ncases > 1 ? lbm::valid_batch_config(f)
+                                                : lbm::valid_fused_config(f, c->storage));
+  if (!ok)
     return fail(c, LBM_ERR_ARG,
-                "invalid fused configuration (tile_y 8 or 16, zchunk >= 0, hold 0..4, "
-                "hold 2-3 need tile_y 8, hold 4 needs tile_y 16)");
+                c->ncases > 1
+                    ? "invalid batch configuration ((tile_y, hold) = (8, 2), (8, 0) or (16, 1), zchunk >= 0)"
+                    : "invalid fused configuration (tile_y 8 or 16, zchunk >= 0, hold 0..6, "
+                      "hold 2, 3, 5, 6 need tile_y 8, hold 4 needs tile_y 16)");
   c->fused = f;
+  drop_graph(c);
+  lbm_status st = upload_case_table(c);
+  if (st != LBM_OK) return st;
   c->err[0] = 0;
   return LBM_OK;
 }
@@ -497,5 +707,5 @@ extern "C" lbm_status lbm_get_fused_config(const lbm_ctx* c, int* tile_y,
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
-  return c->p.kernel == LBM_KERNEL_TWO_PASS ? 2 : 1;
+  return (c->ncases == 1 && c->kernel == LBM_KERNEL_TWO_PASS) ? 2 : 1;
 }

@@ -14,6 +14,25 @@ cudaError_t launch_fused(int storage, const void* src, void* dst,
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
+                               const BatchCase* cases, int ncases,
+                               int total_items, bool walls,
+                               const FusedConfig& cfg, int sms, cudaStream_t s) {
+  switch (storage) {
+    case 0: return launch_fused_batch_storage<float>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
+    case 1: return launch_fused_batch_storage<__half>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
+    case 2: return launch_fused_batch_storage<__nv_bfloat16>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Batched kernel variants: (tile_y, hold) = (8, 2), (8, 0), (16, 1).
+bool valid_batch_config(const FusedConfig& c) {
+  const bool shape = (c.tile_y == 8 && (c.hold == 2 || c.hold == 0)) ||
+                     (c.tile_y == 16 && c.hold == 1);
+  return shape && c.zchunk > 0;
+}
+
 bool valid_fused_config(const FusedConfig& c, int storage) {
   if (c.tile_y != 8 && c.tile_y != 16) return false;
   if (c.hold < 0 || c.hold > 6) return false;

@@ -189,8 +189,10 @@ struct Geometry {
   bool col_ok, interior, xlo, xhi, ylo, yhi;
   int cx, cy;
   unsigned plane_cells;
-  __device__ __forceinline__ Geometry(const StepArgs& a, int tx, int ty) {
-    const int x0 = blockIdx.x * (kTileW - 2), y0 = blockIdx.y * (BY - 2);
+  // tile (bx, by) of the lattice's 30 x (BY - 2) interior tiles
+  __device__ __forceinline__ Geometry(const StepArgs& a, int tx, int ty, int bx,
+                                      int by) {
+    const int x0 = bx * (kTileW - 2), y0 = by * (BY - 2);
     cx = x0 - 1 + tx;
     cy = y0 - 1 + ty;  // unwrapped
     col_ok = true;
@@ -242,17 +244,16 @@ struct FusedSmem<BY, 2> {
 };
 
 // MINB: CTAs per SM the register allocation must allow (launch bounds).
-template <typename T, int BY, bool WALLS, int HOLD, int MINB>
-__global__ void __launch_bounds__(kTileW* BY, MINB)
-    k_fused(const T* __restrict__ src, T* __restrict__ dst,
-            const __grid_constant__ StepArgs a, int zchunk) {
+// One work item of the fused step: tile (bx, by), planes [zb, ze).
+template <typename T, int BY, bool WALLS, int HOLD>
+__device__ __forceinline__ void fused_work(const T* __restrict__ src,
+                                           T* __restrict__ dst,
+                                           const StepArgs& a, int bx, int by,
+                                           int zb, int ze,
+                                           FusedSmem<BY, HOLD>& sm) {
   using Pair = typename Store<T>::Pair;
-  __shared__ FusedSmem<BY, HOLD> sm;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int zb = blockIdx.z * zchunk;
-  const int ze = min(zb + zchunk, a.nz);
-  if (zb >= ze) return;
-  const Geometry<WALLS, BY> g(a, tx, ty);
+  const Geometry<WALLS, BY> g(a, tx, ty, bx, by);
   const unsigned plane = (unsigned)a.plane;
   const Pair* srcp = reinterpret_cast<const Pair*>(src);
 
@@ -325,6 +326,57 @@ __global__ void __launch_bounds__(kTileW* BY, MINB)
   }
 }
 
+template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+__global__ void __launch_bounds__(kTileW* BY, MINB)
+    k_fused(const T* __restrict__ src, T* __restrict__ dst,
+            const __grid_constant__ StepArgs a, int zchunk) {
+  __shared__ FusedSmem<BY, HOLD> sm;
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, a.nz);
+  if (zb >= ze) return;
+  fused_work<T, BY, WALLS, HOLD>(src, dst, a, blockIdx.x, blockIdx.y, zb, ze, sm);
+}
+
+// Batched step: many independent lattices ("cases") in one launch.  The
+// CTAs are persistent: CTA b takes work items b, b + gridDim.x, ...; the
+// items of a case are numbered (chunk, tile y, tile x) with tile x fastest,
+// so concurrently running CTAs work on neighbouring tiles of one chunk and
+// their ring re-reads hit L2.  The case's parameters are copied into shared
+// memory once per item.
+template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+__global__ void __launch_bounds__(kTileW* BY, MINB)
+    k_fused_batch(const BatchCase* __restrict__ cases, int ncases,
+                  int total_items, const T* __restrict__ src_base,
+                  T* __restrict__ dst_base, int zchunk) {
+  __shared__ FusedSmem<BY, HOLD> sm;
+  __shared__ StepArgs sa;
+  __shared__ int s_case, s_item;
+  for (int w = blockIdx.x; w < total_items; w += gridDim.x) {
+    __syncthreads();  // the previous item is done with sm and sa
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      int lo = 0, hi = ncases - 1;  // last case with item_start <= w
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cases[mid].item_start <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      s_case = lo;
+      s_item = w - cases[lo].item_start;
+      sa = cases[lo].args;
+    }
+    __syncthreads();
+    const BatchCase& bc = cases[s_case];
+    const int tiles_x = bc.tiles_x, tiles_y = bc.tiles_y;
+    const int item = s_item;
+    const int bx = item % tiles_x, rest = item / tiles_x;
+    const int by = rest % tiles_y, chunk = rest / tiles_y;
+    const int zb = chunk * zchunk;
+    const int ze = min(zb + zchunk, sa.nz);
+    const size_t off = 2 * (size_t)bc.pair_base;
+    fused_work<T, BY, WALLS, HOLD>(src_base + off, dst_base + off, sa, bx, by, zb, ze, sm);
+  }
+}
+
 // Two columns per thread: a CTA of 32 x 8 threads covers a 32 x 16 column
 // tile (interior 30 x 14), thread row ty handling tile rows ty and ty + 8.
 // The ring overhead of the moment pass falls from 256/180 to 512/420 and
@@ -347,7 +399,8 @@ __global__ void __launch_bounds__(kTileW * 8, 2)
   const int zb = blockIdx.z * zchunk;
   const int ze = min(zb + zchunk, a.nz);
   if (zb >= ze) return;
-  const Geometry<WALLS, kRows2> g0(a, tx, ty), g1(a, tx, ty + 8);
+  const Geometry<WALLS, kRows2> g0(a, tx, ty, blockIdx.x, blockIdx.y),
+      g1(a, tx, ty + 8, blockIdx.x, blockIdx.y);
   const unsigned plane = (unsigned)a.plane;
   const Pair* srcp = reinterpret_cast<const Pair*>(src);
 
@@ -436,7 +489,7 @@ __global__ void __launch_bounds__(kTileW* kAsyncBY, 2)
   const int zb = blockIdx.z * zchunk;
   const int ze = min(zb + zchunk, a.nz);
   if (zb >= ze) return;
-  const Geometry<WALLS, BY> g(a, tx, ty);
+  const Geometry<WALLS, BY> g(a, tx, ty, blockIdx.x, blockIdx.y);
   const unsigned plane = (unsigned)a.plane;
   const Pair* srcp = reinterpret_cast<const Pair*>(src);
   Pair* raw = &sm.raw[0][ty][tx];
@@ -579,6 +632,43 @@ static cudaError_t launch_fused_h(const void* src, void* dst,
       if constexpr (BY == 8) return launch_fused_v<T, BY, WALLS, 2, 4>(src, dst, a, zc, s);
       break;
   }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* cases,
+                                  int ncases, int total_items, int zc, int sms,
+                                  cudaStream_t s) {
+  static int per_sm = 0;  // resident CTAs per SM, queried once
+  if (per_sm == 0) {
+    int q = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &q, k_fused_batch<T, BY, WALLS, HOLD, MINB>, kTileW * BY, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = q < 1 ? 1 : q;
+  }
+  const int grid = min(total_items, sms * per_sm);
+  k_fused_batch<T, BY, WALLS, HOLD, MINB><<<grid, dim3(kTileW, BY), 0, s>>>(
+      cases, ncases, total_items, (const T*)src, (T*)dst, zc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fused_batch_storage(const void* src, void* dst,
+                                       const BatchCase* cases, int ncases,
+                                       int total_items, bool walls,
+                                       const FusedConfig& cfg, int sms,
+                                       cudaStream_t s) {
+  const int zc = cfg.zchunk;
+  if (cfg.tile_y == 8 && cfg.hold == 2)
+    return walls ? launch_batch_v<T, 8, true, 2, 2>(src, dst, cases, ncases, total_items, zc, sms, s)
+                 : launch_batch_v<T, 8, false, 2, 2>(src, dst, cases, ncases, total_items, zc, sms, s);
+  if (cfg.tile_y == 8 && cfg.hold == 0)
+    return walls ? launch_batch_v<T, 8, true, 0, 2>(src, dst, cases, ncases, total_items, zc, sms, s)
+                 : launch_batch_v<T, 8, false, 0, 2>(src, dst, cases, ncases, total_items, zc, sms, s);
+  if (cfg.tile_y == 16 && cfg.hold == 1)
+    return walls ? launch_batch_v<T, 16, true, 1, 1>(src, dst, cases, ncases, total_items, zc, sms, s)
+                 : launch_batch_v<T, 16, false, 1, 1>(src, dst, cases, ncases, total_items, zc, sms, s);
   return cudaErrorInvalidValue;
 }
 

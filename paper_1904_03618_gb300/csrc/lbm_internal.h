@@ -9,7 +9,7 @@
 
 namespace lbm {
 
-constexpr int kDiagSlots = 12;  // accumulated slots of lbm_diagnostics
+constexpr int kDiagSlots = 13;  // accumulated slots of lbm_diagnostics
 
 // Host helpers of the C-ABI layer.  Errors without a context are recorded
 // for lbm_last_error(NULL) of the calling thread.
@@ -52,6 +52,27 @@ cudaError_t launch_fused(int storage, const void* src, void* dst,
                          const StepArgs& a, const FusedConfig& cfg,
                          cudaStream_t s);
 FusedConfig default_fused_config(const StepArgs& a, int storage);
+
+// One case of a batch, as the batched kernel sees it.
+struct BatchCase {
+  StepArgs args;          // plane = the case's padded cell count
+  long long pair_base;    // offset of the case, in (red, blue) pairs, within
+                          // each population buffer
+  int item_start;         // first work item of the case
+  int tiles_x, tiles_y;   // 30 x (tile_y - 2) interior tiles
+  int pad_;
+};
+template <typename T>
+cudaError_t launch_fused_batch_storage(const void* src, void* dst,
+                                       const BatchCase* cases, int ncases,
+                                       int total_items, bool walls,
+                                       const FusedConfig& cfg, int sms,
+                                       cudaStream_t s);
+cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
+                               const BatchCase* cases, int ncases,
+                               int total_items, bool walls,
+                               const FusedConfig& cfg, int sms, cudaStream_t s);
+bool valid_batch_config(const FusedConfig& c);
 bool valid_fused_config(const FusedConfig& c, int storage);
 
 }  // namespace lbm

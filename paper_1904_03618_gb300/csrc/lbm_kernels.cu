@@ -173,9 +173,9 @@ template <typename T>
 __global__ void __launch_bounds__(kDiagBlock)
     k_diag_partial(const T* __restrict__ src, StepArgs a,
                    double* __restrict__ part) {
-  // slots 0..4, 9..11 compensated sums; 5, 6, 8 counts; 7 max
+  // slots 0..4, 9..11 compensated sums; 5, 6, 8, 12 counts; 7 max
   CSum mR, mB, jx, jy, jz, cx, cy, cz;
-  unsigned n_nonfinite = 0, n_negative = 0, n_red = 0;
+  unsigned n_nonfinite = 0, n_negative = 0, n_red = 0, n_colour_negative = 0;
   float umax = 0.f;
   const unsigned nx = (unsigned)a.nx, ny = (unsigned)a.ny;
   const unsigned N = nx * ny * (unsigned)a.nz;
@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kDiagBlock)
     cz.add(rRc * (float)z);
     const Macro m = macro_of(a, fR, fB);
     n_nonfinite += finite ? 0u : 1u;
-    n_negative += (m.rR < 0.f || m.rB < 0.f) ? 1u : 0u;
+    n_negative += (m.rho <= 0.f) ? 1u : 0u;
+    n_colour_negative += (m.rR < 0.f || m.rB < 0.f) ? 1u : 0u;
     const float um = sqrtf(m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     if (finite && um > umax) umax = um;
     n_red += phase_field(a, m.rR, m.rB) > 0.f ? 1u : 0u;
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kDiagBlock)
   double acc[kDiagSlots] = {mR.value(), mB.value(), jx.value(), jy.value(),
                             jz.value(), (double)n_nonfinite, (double)n_negative,
                             (double)umax, (double)n_red, cx.value(), cy.value(),
-                            cz.value()};
+                            cz.value(), (double)n_colour_negative};
   __shared__ double sh[kDiagBlock / 32][kDiagSlots];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

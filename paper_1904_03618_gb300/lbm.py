@@ -88,6 +88,23 @@ _lib.lbm_set_fused_config.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes
 _lib.lbm_set_fused_config.restype = ctypes.c_int
 _lib.lbm_get_fused_config.argtypes = [_ctx_p] + [ctypes.POINTER(ctypes.c_int)] * 3
 _lib.lbm_get_fused_config.restype = ctypes.c_int
+_lib.lbm_create_batch.argtypes = [ctypes.POINTER(LbmParams), ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]
+_lib.lbm_create_batch.restype = ctypes.c_int
+_lib.lbm_num_cases.argtypes = [_ctx_p]
+_lib.lbm_num_cases.restype = ctypes.c_int
+_lib.lbm_batch_init_fields.argtypes = [_ctx_p, ctypes.c_int, _fp, _fp, _fp]
+_lib.lbm_batch_init_fields.restype = ctypes.c_int
+_lib.lbm_batch_moments.argtypes = [_ctx_p, ctypes.c_int, _fp, _fp, _fp]
+_lib.lbm_batch_moments.restype = ctypes.c_int
+_lib.lbm_batch_diagnostics.argtypes = [_ctx_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+_lib.lbm_batch_diagnostics.restype = ctypes.c_int
+_lib.lbm_batch_get_f.argtypes = [_ctx_p, ctypes.c_int, _fp]
+_lib.lbm_batch_get_f.restype = ctypes.c_int
+_lib.lbm_batch_set_f.argtypes = [_ctx_p, ctypes.c_int, _fp]
+_lib.lbm_batch_set_f.restype = ctypes.c_int
+_lib.lbm_set_graphs.argtypes = [_ctx_p, ctypes.c_int]
+_lib.lbm_set_graphs.restype = ctypes.c_int
 _lib.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
 _lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_launches_per_step.argtypes = [_ctx_p]
@@ -101,6 +118,9 @@ EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
+            "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
+            "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
+            "lbm_batch_set_f", "lbm_set_graphs",
             "lbm_launches_per_step", "lbm_destroy", "lbm_last_error")
 
 
@@ -163,6 +183,50 @@ def lbm_create(params: LbmParams, stream=None):
     if st != LBM_OK:
         raise LbmError(st, lbm_last_error(None))
     return ctx
+
+
+def lbm_create_batch(params_list, stream=None):
+    arr = (LbmParams * len(params_list))(*params_list)
+    ctx = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream) if stream else None
+    st = _lib.lbm_create_batch(arr, len(params_list), s, ctypes.byref(ctx))
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
+    return ctx
+
+
+def lbm_num_cases(ctx) -> int:
+    return int(_lib.lbm_num_cases(ctx))
+
+
+def lbm_batch_init_fields(ctx, case, rho_R, rho_B, u):
+    _check(ctx, _lib.lbm_batch_init_fields(ctx, int(case), _addr(rho_R), _addr(rho_B),
+                                           _addr(u)))
+
+
+def lbm_batch_moments(ctx, case, rho_R, rho_B, u):
+    _check(ctx, _lib.lbm_batch_moments(ctx, int(case), _addr(rho_R), _addr(rho_B),
+                                       _addr(u)))
+
+
+def lbm_batch_diagnostics(ctx, case, raise_unstable=True):
+    out = (ctypes.c_double * 16)()
+    st = _lib.lbm_batch_diagnostics(ctx, int(case), out)
+    if st != LBM_OK and (raise_unstable or st != LBM_ERR_UNSTABLE):
+        raise LbmError(st, lbm_last_error(ctx))
+    return np.array(out[:], dtype=np.float64)
+
+
+def lbm_batch_get_f(ctx, case, f):
+    _check(ctx, _lib.lbm_batch_get_f(ctx, int(case), _addr(f)))
+
+
+def lbm_batch_set_f(ctx, case, f):
+    _check(ctx, _lib.lbm_batch_set_f(ctx, int(case), _addr(f)))
+
+
+def lbm_set_graphs(ctx, enable):
+    _check(ctx, _lib.lbm_set_graphs(ctx, 1 if enable else 0))
 
 
 def lbm_init_fields(ctx, rho_R, rho_B, u, solid=None):
@@ -282,6 +346,68 @@ class Lattice:
 
     def diagnostics(self, raise_unstable=True):
         return lbm_diagnostics(self.ctx, raise_unstable)
+
+    def close(self):
+        if self.ctx is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent lattices on one device, advanced together by
+    lbm_step (one kernel launch per step over all cases)."""
+
+    def __init__(self, params_list, device=None, stream=None):
+        self.device = torch.device(device or "cuda")
+        self.params = list(params_list)
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            self.ctx = lbm_create_batch(self.params, self.stream.cuda_stream)
+        self.shapes = [(p.nz, p.ny, p.nx) for p in self.params]
+
+    def _t(self, x):
+        if isinstance(x, torch.Tensor):
+            return x.to(device=self.device, dtype=torch.float32).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
+                               device=self.device)
+
+    def init_fields(self, case, rho_R, rho_B, u):
+        rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        lbm_batch_init_fields(self.ctx, case, rR, rB, uu)
+        self.stream.synchronize()
+
+    def set_f(self, case, f):
+        ft = self._t(f)
+        lbm_batch_set_f(self.ctx, case, ft)
+        self.stream.synchronize()
+
+    def get_f(self, case):
+        out = torch.empty((2, 19) + self.shapes[case], dtype=torch.float32,
+                          device=self.device)
+        lbm_batch_get_f(self.ctx, case, out)
+        self.stream.synchronize()
+        return out
+
+    def moments(self, case):
+        shape = self.shapes[case]
+        rR = torch.empty(shape, dtype=torch.float32, device=self.device)
+        rB = torch.empty_like(rR)
+        u = torch.empty((3,) + shape, dtype=torch.float32, device=self.device)
+        lbm_batch_moments(self.ctx, case, rR, rB, u)
+        self.stream.synchronize()
+        return rR, rB, u
+
+    def diagnostics(self, case, raise_unstable=True):
+        return lbm_batch_diagnostics(self.ctx, case, raise_unstable)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
 
     def close(self):
         if self.ctx is not None:

@@ -98,3 +98,21 @@ def random_fields(nx, ny, nz, seed=0, rho_lo=0.2, rho_hi=1.0, umax=0.05):
     rho_B = rng.uniform(rho_lo, rho_hi, (nz, ny, nx))
     u = rng.uniform(-umax, umax, (3, nz, ny, nx))
     return rho_R, rho_B, u
+
+
+def droplet_sweep(ncases, seed=1234, edges=(32, 48, 64, 96)):
+    """Sampled parameters of a batched droplet sweep: per case a cubic box
+    edge drawn uniformly from `edges`, a density ratio in [1, 20], a surface
+    tension in [0.001, 0.02] and a speed in [0, 0.05] along x; every second
+    case is static (speed 0).  Returns a list of dicts of raw samples."""
+    rng = np.random.default_rng(seed)
+    e = rng.choice(np.asarray(edges), size=ncases)
+    ratio = rng.uniform(1.0, 20.0, ncases)
+    sigma = rng.uniform(0.001, 0.02, ncases)
+    speed = rng.uniform(0.0, 0.05, ncases)
+    out = []
+    for k in range(ncases):
+        out.append(dict(edge=int(e[k]), density_ratio=float(ratio[k]),
+                        sigma=float(sigma[k]),
+                        speed=0.0 if k % 2 == 0 else float(speed[k])))
+    return out

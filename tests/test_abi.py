@@ -75,3 +75,19 @@ def test_null_context_calls_do_not_crash():
     assert lbm._lib.lbm_moments(None, None, None, None) == lbm.LBM_ERR_ARG
     assert lbm._lib.lbm_population_bytes(None) == 0
     lbm.lbm_destroy(None)
+
+
+def test_batch_creation_validates_every_case_on_the_host():
+    good = lbm.make_params(8, 8, 8)
+    bad = lbm.make_params(8, 8, 8, tau_R=0.3)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create_batch([good, bad])
+    assert ei.value.status == lbm.LBM_ERR_ARG and "case 1" in str(ei.value)
+    mixed = lbm.make_params(8, 8, 8, storage="f16")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create_batch([good, mixed])
+    assert "same storage" in str(ei.value)
+    two_pass = lbm.make_params(8, 8, 8, kernel="two_pass")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create_batch([two_pass, two_pass])
+    assert "fused kernel only" in str(ei.value)
