@@ -426,7 +426,7 @@ def batch_measure(args, dev):
     import numpy as np
     import torch
 
-    from paper_1904_03618_gb300 import lbm, params as P, workloads
+    from paper_1904_03618_gb300 import autotune, lbm, params as P, workloads
     samples = workloads.droplet_sweep(args.batch, seed=1234)
     cases = [P.droplet_case(s) for s in samples]
     cells = sum(c["nx"] ** 3 for c in cases)
@@ -454,6 +454,7 @@ def batch_measure(args, dev):
             lbm.lbm_batch_init_fields(b.ctx, k, rR, rB, u)
         stream.synchronize()
         del fields
+        tuned = autotune.tune(b.ctx, plist, stream, steps=6, cache_path=None)
         b.step(max(args.warmup, 4))
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -470,6 +471,8 @@ def batch_measure(args, dev):
         out[storage] = {"value": mlups, "unit": "MLUPS", "ms_per_step": ms,
                         "roofline_frac": mlups * 1e6 * bpc / (peak * 1e9),
                         "steps": args.batch_steps, "gpu_launches_per_step": 1,
+                        "autotuned_config": {"tile_y": tuned[0], "zchunk": tuned[1],
+                                             "hold": tuned[2]},
                         "nonfinite_cells_sampled": bad}
         torch.cuda.empty_cache()
     return out

@@ -1,0 +1,112 @@
+"""Launch-configuration autotuner for the fused step.
+
+The fused kernel's launch configuration -- tile height, planes per CTA
+(z chunk) and where a plane's reduced state waits between its pull and its
+collision -- does not change results (the parity tests run every
+configuration against the oracle); it only changes speed, and the best
+choice depends on the lattice shape, the storage type and, for batches, on
+the mix of box sizes.  `tune` times the candidate configurations on the
+live context with CUDA events on its stream, keeps the fastest, applies it,
+and records it in a JSON cache keyed by device, storage and lattice
+signature so that later runs of the same shape skip the timing.
+
+Timing advances the context's state (it runs real steps).  Tune before
+initialising the run that matters, or accept the extra steps.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+from . import lbm
+
+# (tile_y, hold) shapes; z chunks are tried for each
+SINGLE_SHAPES = [(8, 2), (8, 3), (8, 0), (16, 1), (16, 4)]
+BATCH_SHAPES = [(8, 2), (8, 0), (16, 1)]
+ZCHUNKS = [8, 12, 16, 24]
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1904_03618_gb300",
+                             "autotune.json")
+
+
+def signature(params_list, storage: int) -> str:
+    """Cache key of a lattice (one params) or a batch (several)."""
+    dev = torch.cuda.get_device_name()
+    if len(params_list) == 1:
+        p = params_list[0]
+        shape = "%dx%dx%d/w%d%d%d" % (p.nx, p.ny, p.nz, p.wall[0], p.wall[1], p.wall[2])
+    else:
+        sizes = sorted((p.nx, p.ny, p.nz) for p in params_list)
+        counts = {}
+        for s in sizes:
+            counts[s] = counts.get(s, 0) + 1
+        shape = "batch:" + ",".join("%dx%dx%d*%d" % (k + (v,)) for k, v in sorted(counts.items()))
+    return "%s|storage%d|%s" % (dev, storage, shape)
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, table):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time(ctx, stream, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lbm.lbm_step(ctx, 2)  # warm-up (and graph capture for this configuration)
+    e0.record(stream)
+    lbm.lbm_step(ctx, steps)
+    e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune(ctx, params_list, stream, steps=8, cache_path=DEFAULT_CACHE, use_cache=True,
+         candidates=None):
+    """Chooses and applies the fastest fused configuration for `ctx` (a
+    Lattice's or Batch's context; every case must be initialised).  Returns
+    (tile_y, zchunk, hold, ms_per_step, source) with source "cache" or
+    "timed"."""
+    params_list = list(params_list)
+    storage = int(params_list[0].storage)
+    key = signature(params_list, storage)
+    table = _load(cache_path) if (use_cache and cache_path) else {}
+    if use_cache and key in table:
+        t = table[key]
+        lbm.lbm_set_fused_config(ctx, t["tile_y"], t["zchunk"], t["hold"])
+        return t["tile_y"], t["zchunk"], t["hold"], t["ms"], "cache"
+    if candidates is None:
+        shapes = BATCH_SHAPES if len(params_list) > 1 else SINGLE_SHAPES
+        nz = max(p.nz for p in params_list)
+        candidates = [(ty, zc, hold) for ty, hold in shapes for zc in ZCHUNKS if zc <= max(nz, 8)]
+    best = None
+    for ty, zc, hold in candidates:
+        try:
+            lbm.lbm_set_fused_config(ctx, ty, zc, hold)
+        except lbm.LbmError:
+            continue
+        ms = _time(ctx, stream, steps)
+        if best is None or ms < best[3]:
+            best = (ty, zc, hold, ms)
+    if best is None:
+        raise RuntimeError("autotune: no valid configuration")
+    lbm.lbm_set_fused_config(ctx, best[0], best[1], best[2])
+    if cache_path:
+        table = _load(cache_path)
+        table[key] = {"tile_y": best[0], "zchunk": best[1], "hold": best[2], "ms": best[3],
+                      "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+        _store(cache_path, table)
+    return best + ("timed",)
