@@ -76,7 +76,15 @@ typedef struct {
                           "original model" of Sec. IV.A)                     */
   int storage;         /* lbm_storage                                        */
   int kernel;          /* lbm_kernel                                         */
-  int reserved0;       /* must be 0                                          */
+  int wetting;         /* 0: neutral walls (contact angle 90 degrees, Sec.
+                          IV.D: neighbours beyond a wall take the centre value
+                          in Eq. 49); 1: contact angle contact_angle_deg --
+                          at a fluid cell next to a wall the colour gradient
+                          keeps its magnitude and its direction along the wall
+                          and is turned to the angle pi - theta from the
+                          inward wall normal (theta measured through the red
+                          fluid) before the perturbation and recolouring use
+                          it.  The paper has only the neutral wall.          */
   double rho_in_R, rho_in_B; /* rho_k^in in rho^N, below Eq. 8 (> 0)         */
   double alpha_R, alpha_B;   /* alpha_k of Eq. 13, in [0, 1)                 */
   double tau_R, tau_B;       /* tau_v^R, tau_v^B of Eq. 52 (> 1/2)            */
@@ -90,6 +98,7 @@ typedef struct {
   double ref_R, ref_B; /* reference densities of the FP16/BF16 deviation
                           storage (ignored for LBM_F32): colour k is stored as
                           f_i^k - ref_k * phi_i^k                            */
+  double contact_angle_deg; /* theta in (0, 180) when wetting = 1            */
 } lbm_params;
 
 /* Creates a context: validates p, allocates the two population buffers and

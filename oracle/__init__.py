@@ -59,6 +59,8 @@ class OracleParams(ctypes.Structure):
         ("beta", ctypes.c_double), ("delta", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("gravity", ctypes.c_double * 3),
         ("eq18_coef", ctypes.c_double),
+        ("wetting", ctypes.c_int), ("pad2_", ctypes.c_int),
+        ("contact_angle_deg", ctypes.c_double),
     ]
 
 
@@ -72,7 +74,8 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
            rho_in_B=1.0, alpha_R=1.0 / 3.0, alpha_B=1.0 / 3.0, tau_R=1.0,
            tau_B=1.0, tau_e=1.0, tau_q=1.0, tau_pi=1.0, A_R=0.0, A_B=0.0,
            beta=0.7, delta=0.98, force=(0.0, 0.0, 0.0),
-           gravity=(0.0, 0.0, 0.0), eq18_coef=EQ18_COEF) -> OracleParams:
+           gravity=(0.0, 0.0, 0.0), eq18_coef=EQ18_COEF, wetting=False,
+           contact_angle_deg=90.0) -> OracleParams:
     p = OracleParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):
@@ -87,6 +90,8 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
     p.A_R, p.A_B = float(A_R), float(A_B)
     p.beta, p.delta = float(beta), float(delta)
     p.eq18_coef = float(eq18_coef)
+    p.wetting = 1 if wetting else 0
+    p.contact_angle_deg = float(contact_angle_deg)
     return p
 
 
@@ -94,7 +99,7 @@ def params_from(d: dict) -> OracleParams:
     """Build oracle params from a plain dict of the shared parameter names."""
     kw = dict(d)
     nx, ny, nz = kw.pop("nx"), kw.pop("ny"), kw.pop("nz")
-    for k in ("storage",):
+    for k in ("storage", "kernel", "ref_R", "ref_B"):
         kw.pop(k, None)
     return params(nx, ny, nz, **kw)
 
@@ -140,6 +145,7 @@ def _lib_handle():
         lib.or_force_guo.argtypes = [_dp, _dp, _dp]
         lib.or_perturbation.argtypes = [ctypes.c_double, _dp, _dp]
         lib.or_correction.argtypes = [_dp, _dp]
+        lib.or_wetting.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_double, _dp]
         lib.or_tau_v.argtypes = [ctypes.c_double] * 4
         lib.or_tau_v.restype = ctypes.c_double
         lib.or_moments.argtypes = [P, _dp, _dp, _dp, _dp]
@@ -203,6 +209,13 @@ def correction(Q) -> np.ndarray:
     q = _vec(Q, 3)
     _lib_handle().or_correction(_ptr(q), _ptr(out))
     return out
+
+
+def wetting(wall_side, theta_deg, grad) -> np.ndarray:
+    g = _vec(grad, 3).copy()
+    side = (ctypes.c_int * 3)(*[int(v) for v in wall_side])
+    _lib_handle().or_wetting(side, float(theta_deg), _ptr(g))
+    return g
 
 
 def tau_v(rhoN, tau_R, tau_B, delta=0.98) -> float:

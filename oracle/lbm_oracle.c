@@ -38,6 +38,12 @@
  *     Eq. 49 stencil a neighbour beyond a wall takes the centre-cell value.
  *   - |grad rho^N| < 1e-12: perturbation and recolouring cosine are zero;
  *     cos(phi_0) = 0 for the rest direction.
+ *   - Wetting (optional; the paper uses only the neutral wall, theta = 90
+ *     degrees): at a fluid cell next to a wall the colour gradient keeps its
+ *     magnitude and its direction along the wall but is turned to make the
+ *     angle pi - theta with the inward wall normal (theta measured through
+ *     the red phase), and this gradient then drives the perturbation and the
+ *     recolouring.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -207,6 +213,28 @@ void or_correction(const double *Q, double *C) {
   C[6] = Q[1] - Q[2];
 }
 
+/* Contact-angle rule at a wall-adjacent cell.  wall_side[a] = +1 if the
+   cell touches the wall at the low face of axis a (inward normal +e_a),
+   -1 at the high face, 0 otherwise.  grad is modified in place. */
+void or_wetting(const int *wall_side, double theta_deg, double *grad) {
+  double n[3] = {(double)wall_side[0], (double)wall_side[1], (double)wall_side[2]};
+  double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  if (nn == 0.0) return;
+  for (int a = 0; a < 3; ++a) n[a] /= sqrt(nn);
+  double gn = grad[0] * n[0] + grad[1] * n[1] + grad[2] * n[2];
+  double t[3], tt = 0.0, g2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    t[a] = grad[a] - gn * n[a];
+    tt += t[a] * t[a];
+    g2 += grad[a] * grad[a];
+  }
+  if (tt <= 0.0 || g2 <= 0.0) return;
+  double theta = theta_deg * M_PI / 180.0;
+  double g = sqrt(g2), tl = sqrt(tt);
+  for (int a = 0; a < 3; ++a)
+    grad[a] = g * (-cos(theta) * n[a] + sin(theta) * t[a] / tl);
+}
+
 /* Relaxation time tau_v of Eq. 52 with the parabolic g^R, g^B. */
 double or_tau_v(double rhoN, double tau_R, double tau_B, double delta) {
   double s = 2.0 * tau_R * tau_B / (tau_R + tau_B);
@@ -369,6 +397,16 @@ int or_step(const or_params *p, const double *f_in, double *f_out,
             grad[ax] = iso_grad(p, rhoN, x, y, z, ax);
             for (int k = 0; k < 2; ++k)
               Q[k][ax] = iso_grad(p, qbar + (k * 3 + ax) * N, x, y, z, ax);
+          }
+          if (p->wetting) {
+            int side[3] = {0, 0, 0};
+            const int xyz[3] = {x, y, z}, ext[3] = {p->nx, p->ny, p->nz};
+            for (int a = 0; a < 3; ++a) {
+              if (!p->wall[a]) continue;
+              if (xyz[a] == 0) side[a] += 1;
+              if (xyz[a] == ext[a] - 1) side[a] -= 1;
+            }
+            or_wetting(side, p->contact_angle_deg, grad);
           }
           double gnorm = sqrt(grad[0] * grad[0] + grad[1] * grad[1] +
                               grad[2] * grad[2]);

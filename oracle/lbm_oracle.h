@@ -28,6 +28,9 @@ typedef struct {
   double force[3];           /* uniform force density */
   double gravity[3];         /* acceleration; force density rho * g */
   double eq18_coef;          /* high-order term coefficient of Eq. 18 */
+  int wetting;               /* 1: contact-angle rule at wall-adjacent cells */
+  int pad2_;
+  double contact_angle_deg;  /* theta, measured through the red phase */
 } or_params;
 
 void or_matrix_M(double *M);
@@ -38,6 +41,7 @@ void or_force_guo(const double *Fk, const double *u, double *Fi);
 void or_perturbation(double A_k, const double *grad, double *om2);
 void or_correction(const double *Q, double *C);
 double or_tau_v(double rhoN, double tau_R, double tau_B, double delta);
+void or_wetting(const int *wall_side, double theta_deg, double *grad);
 int or_moments(const or_params *p, const double *f, double *rho_R,
                double *rho_B, double *u);
 int or_init(const or_params *p, const double *rho_R, const double *rho_B,

@@ -94,7 +94,10 @@ static lbm_status validate(const lbm_params* p) {
     return fail(nullptr, LBM_ERR_ARG, "storage must be LBM_F32, LBM_F16 or LBM_BF16");
   if (p->kernel != LBM_KERNEL_FUSED && p->kernel != LBM_KERNEL_TWO_PASS)
     return fail(nullptr, LBM_ERR_ARG, "kernel must be LBM_KERNEL_FUSED or LBM_KERNEL_TWO_PASS");
-  if (p->reserved0 != 0) return fail(nullptr, LBM_ERR_ARG, "reserved0 must be 0");
+  if (p->wetting != 0 && p->wetting != 1)
+    return fail(nullptr, LBM_ERR_ARG, "wetting must be 0 or 1");
+  if (p->wetting && !(p->contact_angle_deg > 0 && p->contact_angle_deg < 180))
+    return fail(nullptr, LBM_ERR_ARG, "contact_angle_deg must lie in (0, 180)");
   if (!(p->rho_in_R > 0) || !(p->rho_in_B > 0))
     return fail(nullptr, LBM_ERR_ARG, "rho_in_R and rho_in_B must be > 0");
   if (!(p->alpha_R >= 0 && p->alpha_R < 1) || !(p->alpha_B >= 0 && p->alpha_B < 1))
@@ -160,6 +163,10 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
   a.gx = (float)p->gravity[0];
   a.gy = (float)p->gravity[1];
   a.gz = (float)p->gravity[2];
+  a.wetting = p->wetting && (p->wall[0] || p->wall[1] || p->wall[2]);
+  const double th_rad = p->contact_angle_deg * 3.14159265358979323846 / 180.0;
+  a.cos_t = (float)cos(th_rad);
+  a.sin_t = (float)sin(th_rad);
   a.has_force = (p->force[0] != 0 || p->force[1] != 0 || p->force[2] != 0 ||
                  p->gravity[0] != 0 || p->gravity[1] != 0 || p->gravity[2] != 0);
   if (p->storage != LBM_F32) {

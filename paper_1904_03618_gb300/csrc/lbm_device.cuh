@@ -43,6 +43,8 @@ struct StepArgs {
   float par_a2, par_b2;         // par_a / (2 delta), par_b / (2 delta)
   float delta;                  // Eq. 52
   int has_force;                // any non-zero force or gravity component
+  int wetting;                  // contact-angle rule at wall-adjacent cells
+  float cos_t, sin_t;           // cos and sin of the contact angle
   float s_e, s_q, s_pi;         // 1/tau_e, 1/tau_q, 1/tau_pi (Eq. 44)
   float half_A;                 // (A_R + A_B) / 2, Eq. 8 summed over colours
   float beta;                   // Eq. 10-11
@@ -348,6 +350,35 @@ __device__ __forceinline__ float tau_v_of(const StepArgs& a, float rn) {
   if (rn >= -a.delta)
     return a.tau_h + rn * (a.par_b + a.par_b2 * rn);
   return a.tau_B;
+}
+
+// Contact-angle rule at a fluid cell next to a wall: the colour gradient
+// keeps its magnitude and its direction along the wall and is turned to
+// the angle pi - theta from the inward wall normal (theta through the red
+// fluid).  lo/hi flag the walls the cell touches on each axis; the normal
+// of an edge or corner cell is the normalised sum.  A gradient with no
+// component along the wall is left unchanged.
+__device__ __forceinline__ void wetting_rule(const StepArgs& a, bool xlo, bool xhi,
+                                             bool ylo, bool yhi, bool zlo, bool zhi,
+                                             float& Gx, float& Gy, float& Gz) {
+  float nx = (xlo ? 1.f : 0.f) - (xhi ? 1.f : 0.f);
+  float ny = (ylo ? 1.f : 0.f) - (yhi ? 1.f : 0.f);
+  float nz = (zlo ? 1.f : 0.f) - (zhi ? 1.f : 0.f);
+  const float nn = nx * nx + ny * ny + nz * nz;
+  if (nn == 0.f) return;
+  const float in = rsqrtf(nn);
+  nx *= in;
+  ny *= in;
+  nz *= in;
+  const float gn = Gx * nx + Gy * ny + Gz * nz;
+  const float tx = Gx - gn * nx, ty = Gy - gn * ny, tz = Gz - gn * nz;
+  const float tt = tx * tx + ty * ty + tz * tz;
+  const float g2 = Gx * Gx + Gy * Gy + Gz * Gz;
+  if (tt <= 0.f || g2 <= 0.f) return;
+  const float gm = sqrtf(g2), it = rsqrtf(tt);
+  Gx = gm * (-a.cos_t * nx + a.sin_t * tx * it);
+  Gy = gm * (-a.cos_t * ny + a.sin_t * ty * it);
+  Gz = gm * (-a.cos_t * nz + a.sin_t * tz * it);
 }
 
 // ---------------------------------------------------------------------------

@@ -298,6 +298,8 @@ __device__ __forceinline__ void fused_work(const T* __restrict__ src,
       float Gx, Gy, Gz, Qx, Qy, Qz;
       window_gradients<BY>(sm.win, z, ty, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi,
                            ctr, Gx, Gy, Gz, Qx, Qy, Qz);
+      if (WALLS && a.wetting)
+        wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
       Macro m;
       if constexpr (HOLD == 0) {
         float rR = 0.f, rB = 0.f;
@@ -432,6 +434,8 @@ __global__ void __launch_bounds__(kTileW * 8, 2)
     float Gx, Gy, Gz, Qx, Qy, Qz;
     window_gradients<kRows2>(sm.win, z, row, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi,
                              ctr, Gx, Gy, Gz, Qx, Qy, Qz);
+    if (WALLS && a.wetting)
+      wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
     const float(*h)[kRows2 - 2][kTileW - 2] = sm.hold[z & 1];
     float f[19];
 #pragma unroll
@@ -545,6 +549,8 @@ __global__ void __launch_bounds__(kTileW* kAsyncBY, 2)
       float Gx, Gy, Gz, Qx, Qy, Qz;
       window_gradients<BY>(sm.win, z, ty, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi,
                            ctr, Gx, Gy, Gz, Qx, Qy, Qz);
+      if (WALLS && a.wetting)
+        wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
       float f[19];
       const float* h = &sm.hold[z & 1][0][ty - 1][tx - 1];
 #pragma unroll

@@ -321,6 +321,9 @@ __global__ void __launch_bounds__(256)
       Qz += (ez(i) * w) * (vp.w - vm.w);
     }
   }
+  if (a.wetting)
+    wetting_rule(a, a.wx && x == 0, a.wx && x == a.nx - 1, a.wy && y == 0,
+                 a.wy && y == a.ny - 1, a.wz && z == 0, a.wz && z == a.nz - 1, Gx, Gy, Gz);
   const float rn = __ldg(&mom[c]).x;
   collide_cell(a, fR, fB, m, rn, Gx, Gy, Gz, Qx, Qy, Qz);
   store_cell<T>(dst, a, c, fR, fB);

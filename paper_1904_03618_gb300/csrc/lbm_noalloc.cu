@@ -99,6 +99,9 @@ __global__ void k_noalloc_collide(const float* __restrict__ f,
       Qz += (ez(i) * w) * (vp.w - vm.w);
     }
   }
+  if (a.wetting)
+    wetting_rule(a, a.wx && x == 0, a.wx && x == a.nx - 1, a.wy && y == 0,
+                 a.wy && y == a.ny - 1, a.wz && z == 0, a.wz && z == a.nz - 1, Gx, Gy, Gz);
   collide_cell(a, fR, fB, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {

@@ -41,7 +41,7 @@ class LbmParams(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("wall", ctypes.c_int * 3),
         ("improved", ctypes.c_int), ("storage", ctypes.c_int),
-        ("kernel", ctypes.c_int), ("reserved0", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("wetting", ctypes.c_int),
         ("rho_in_R", ctypes.c_double), ("rho_in_B", ctypes.c_double),
         ("alpha_R", ctypes.c_double), ("alpha_B", ctypes.c_double),
         ("tau_R", ctypes.c_double), ("tau_B", ctypes.c_double),
@@ -51,6 +51,7 @@ class LbmParams(ctypes.Structure):
         ("beta", ctypes.c_double), ("delta", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("gravity", ctypes.c_double * 3),
         ("ref_R", ctypes.c_double), ("ref_B", ctypes.c_double),
+        ("contact_angle_deg", ctypes.c_double),
     ]
 
 
@@ -139,7 +140,8 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
                 alpha_B=1.0 / 3.0, tau_R=1.0, tau_B=1.0, tau_e=1.0, tau_q=1.0,
                 tau_pi=1.0, A_R=0.0, A_B=0.0, beta=0.7, delta=0.98,
                 force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), ref_R=0.0,
-                ref_B=0.0, **_ignored) -> LbmParams:
+                ref_B=0.0, wetting=False, contact_angle_deg=90.0,
+                **_ignored) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):
@@ -150,7 +152,8 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.kernel = {"fused": LBM_KERNEL_FUSED, "two_pass": LBM_KERNEL_TWO_PASS}[kernel] \
         if isinstance(kernel, str) else int(kernel)
-    p.reserved0 = 0
+    p.wetting = 1 if wetting else 0
+    p.contact_angle_deg = float(contact_angle_deg)
     p.rho_in_R, p.rho_in_B = float(rho_in_R), float(rho_in_B)
     p.alpha_R, p.alpha_B = float(alpha_R), float(alpha_B)
     p.tau_R, p.tau_B = float(tau_R), float(tau_B)

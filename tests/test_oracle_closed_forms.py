@@ -248,3 +248,33 @@ def test_printed_parameter_identities():
         aR = oracle.alpha_R_from_balance(c["rho_in_R"], c["rho_in_B"], c["alpha_B"])
         assert c["rho_in_R"] * oracle.cs2(aR) == pytest.approx(
             c["rho_in_B"] * oracle.cs2(c["alpha_B"]))
+
+
+@pytest.mark.parametrize("theta", [30.0, 60.0, 90.0, 120.0, 150.0])
+@pytest.mark.parametrize("side", [(0, 0, 1), (0, -1, 0), (1, 0, 0)])
+def test_wetting_rule_sets_the_contact_angle(theta, side):
+    """The rotated gradient keeps its magnitude and its direction along the
+    wall, and makes the angle pi - theta with the inward wall normal."""
+    g = np.array([0.07, -0.03, 0.05])
+    out = oracle.wetting(side, theta, g)
+    n = np.array(side, dtype=float)
+    assert np.linalg.norm(out) == pytest.approx(np.linalg.norm(g), rel=1e-14)
+    ang = np.degrees(np.arccos(out @ n / np.linalg.norm(out)))
+    assert ang == pytest.approx(180.0 - theta, abs=1e-9)
+    t_in = g - (g @ n) * n
+    t_out = out - (out @ n) * n
+    assert np.allclose(t_out / np.linalg.norm(t_out), t_in / np.linalg.norm(t_in), atol=1e-14)
+
+
+def test_wetting_rule_edge_cases():
+    # no wall contact: unchanged; purely normal gradient: unchanged
+    g = np.array([0.1, 0.2, 0.3])
+    assert np.array_equal(oracle.wetting((0, 0, 0), 60.0, g), g)
+    assert np.array_equal(oracle.wetting((0, 0, 1), 60.0, [0.0, 0.0, 0.4]), [0.0, 0.0, 0.4])
+    # 90 degrees: the normal component is removed
+    out = oracle.wetting((0, 0, 1), 90.0, g)
+    assert abs(out[2]) < 1e-15 and np.linalg.norm(out) == pytest.approx(np.linalg.norm(g))
+    # edge cell: normal along the diagonal of the two walls
+    out = oracle.wetting((1, 0, 1), 45.0, g)
+    n = np.array([1.0, 0.0, 1.0]) / np.sqrt(2.0)
+    assert np.degrees(np.arccos(out @ n / np.linalg.norm(out))) == pytest.approx(135.0)

@@ -170,9 +170,12 @@ def _layered_case(name, improved, eq18_coef=oracle.EQ18_COEF, steps=50000):
 def test_layered_channel_improved_model_is_accurate_and_original_is_not():
     """Sec. IV.B: the improved model follows the analytic profile (paper:
     E_u = 0.66 % and 1.42 % for cases A and B) while the original model is
-    far off (44.6 % and 59.7 %).  The paper leaves tau and beta unstated, so
-    this is a band: improved below 5 % and 1.5 %, original above 20 % and
-    50 %, and the Eq. 18 coefficient as printed (3/2) clearly worse than 3."""
+    far off (44.6 % and 59.7 %).  Started from the analytic profile and
+    measured after 50,000 steps (case A is at steady state by then; case B's
+    slowest mode is still decaying -- the GPU test runs it to steady state).
+    The paper leaves tau and beta unstated, so this is a band: improved below
+    5 % and 1.5 %, original above 20 % and 50 %, and the Eq. 18 coefficient
+    as printed (3/2) clearly worse than 3."""
     eA = _layered_case("A", True)
     eB = _layered_case("B", True)
     assert eA < 0.05 and eB < 0.015
@@ -205,3 +208,26 @@ def test_laplace_law_static_droplet():
     assert abs(dp * Re / 2 / sigma - 1) < 0.10
     for k in range(2):
         assert abs(f[k].sum() - f0[k].sum()) / f0[k].sum() < 1e-12
+
+
+def test_wetting_switch_is_inert_without_walls():
+    """Periodic lattice: no wall-adjacent cells, so the wetting rule changes
+    nothing."""
+    pd = _pd(6, 5, 7)
+    rR, rB, u = wl.droplet(6, 5, 7, 2.0, 3.0, 1.0, noise=1e-2, seed=4)
+    p0 = oracle.params_from(pd)
+    p1 = oracle.params_from(dict(pd, wetting=True, contact_angle_deg=60.0))
+    f = oracle.init(p0, rR, rB, u)
+    assert np.array_equal(oracle.step(p0, f, 3), oracle.step(p1, f, 3))
+
+
+def test_wetting_rule_changes_only_wall_adjacent_cells_in_one_step():
+    pd = _pd(8, 7, 6, wall=(0, 0, 1))
+    rR, rB, u = wl.droplet(8, 7, 6, 3.0, 3.0, 1.0, center=(3.5, 3.0, 0.0), noise=1e-2, seed=6)
+    p0 = oracle.params_from(pd)
+    p1 = oracle.params_from(dict(pd, wetting=True, contact_angle_deg=45.0))
+    f = oracle.init(p0, rR, rB, u)
+    a, b = oracle.step(p0, f, 1), oracle.step(p1, f, 1)
+    diff = np.abs(a - b).max(axis=(0, 1, 3, 4))  # per z plane
+    # the rule acts at z = 0 and z = 5; streaming carries it one plane inward
+    assert diff[0] > 1e-6 and diff[2] == 0.0 and diff[3] == 0.0
