@@ -241,6 +241,51 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
                             float *f_out, void *cuda_stream);
 
+/* ---- Surrogate network (tensor cores) -----------------------------------
+   A fully connected network x -> tanh(x W_1 + b_1) -> ... (depth hidden
+   layers of `width`) -> (. W_out + b_out), trained with mean squared error
+   sum((y - t)^2) / (batch * n_out) and Adam (beta1 0.9, beta2 0.999, eps
+   1e-8).  It maps impact parameters to a spreading-factor series and screens
+   parameter sweeps; the lattice Boltzmann step remains its fallback and the
+   judge of its error.  The paper has no counterpart.  Every matrix product
+   runs on the 5th-generation tensor cores (tcgen05, BF16 operands, FP32
+   accumulation); weights, gradients, Adam moments and activations are FP32.
+   Parameters are one flat FP32 vector, layer by layer: W_l (fan_in x
+   fan_out, row-major, W[i][j] maps input i to output j), then b_l.
+   x (batch x n_in), t and y (batch x n_out) are row-major float32; x and t
+   must be device memory, y and the parameter / gradient arrays may be host
+   or device.  Work is queued on cuda_stream; calls returning values to the
+   host synchronise it.  1 <= n_in, width, n_out <= 256, 0 <= depth <= 64,
+   1 <= batch <= max_batch.  LBM_ERR_TIMEOUT reports a bounded wait for the
+   tensor cores that gave up (nothing traps). */
+typedef struct lbm_mlp lbm_mlp;
+lbm_status lbm_mlp_create(int n_in, int width, int depth, int n_out,
+                          int max_batch, void *cuda_stream, lbm_mlp **out);
+size_t lbm_mlp_num_params(const lbm_mlp *m);
+/* Copies the parameters in and resets the Adam state and step count. */
+lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *theta);
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *theta);
+lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, int batch, float *y);
+/* Loss (host float, nullable) and gradient (num_params floats, nullable). */
+lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *x, const float *t,
+                             int batch, float *loss, float *grad);
+/* Forward, backward and one Adam step with learning rate lr; loss
+   (nullable) receives the loss before the step (synchronises). */
+lbm_status lbm_mlp_train_step(lbm_mlp *m, const float *x, const float *t,
+                              int batch, float lr, float *loss);
+void lbm_mlp_destroy(lbm_mlp *m);
+const char *lbm_mlp_last_error(const lbm_mlp *m);
+
+/* The network's matrix product on its own: C(m, n) = sum_k A(m, k) B(k, n)
+   with A(m, k) = A[m*sa_m + k*sa_k], B(k, n) = B[k*sb_k + n*sb_n],
+   C[m*sc_m + n]; device pointers, operands rounded to BF16, FP32
+   accumulation, 1 <= N <= 256.  err (device int) is set to 1 if a bounded
+   wait gave up.  Queued on cuda_stream. */
+lbm_status lbm_gemm_bf16(const float *A, long long sa_m, long long sa_k,
+                         const float *B, long long sb_k, long long sb_n,
+                         float *C, long long sc_m, int M, int N, int K,
+                         int *err, void *cuda_stream);
+
 /* Releases everything the context owns.  NULL is allowed. */
 void lbm_destroy(lbm_ctx *ctx);
 

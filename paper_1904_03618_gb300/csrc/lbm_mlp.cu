@@ -1,0 +1,627 @@
+// Surrogate network on the 5th-generation tensor cores (sm_103a).
+//
+// The network maps impact parameters to a spreading-factor series: dense
+// layers x -> tanh(x W + b) -> ... -> (. W_out + b_out), trained with mean
+// squared error and Adam.  Every matrix product of the forward and backward
+// passes runs in k_gemm_tc:
+//   - a CTA owns a 128-row tile of C (all of C's columns, N <= 256);
+//   - the A (128 x 64) and B (N x 64) K-slices are converted to BF16 and
+//     written into shared memory in the canonical K-major layout without
+//     swizzle (8-row x 16-byte core matrices; K-adjacent core matrices 128 B
+//     apart, 8-row groups 1024 B apart);
+//   - one elected thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//     M = 128, K = 16 per instruction) into a TMEM accumulator, then
+//     tcgen05.commit signals an mbarrier; every thread waits on it with a
+//     bounded spin before the slices are overwritten;
+//   - the epilogue reads the accumulator with tcgen05.ld (one TMEM lane per
+//     row) and applies bias + tanh, or the tanh derivative of the backward
+//     pass, before storing FP32.
+// FP32 master weights and activations live in global memory; operands are
+// rounded to BF16 when staged (FP32 accumulation).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace mlp {
+
+constexpr int kM = 128;     // rows per CTA (UMMA M)
+constexpr int kKT = 64;     // K per shared-memory slice
+constexpr int kNMax = 256;  // UMMA N limit for M = 128
+constexpr int kThreads = 128;
+constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier wait
+
+struct GemmArgs {
+  const float* A;
+  long long sa_m, sa_k;  // A(m, k) = A[m * sa_m + k * sa_k]
+  const float* B;
+  long long sb_k, sb_n;  // B(k, n) = B[k * sb_k + n * sb_n]
+  int M, N, K;
+  const float* bias;     // epilogue: C = act(acc + bias) (bias nullable)
+  int act;               // 0 identity, 1 tanh
+  const float* H;        // if non-null: C = acc * (1 - H^2) (tanh backward)
+  long long sh_m;
+  float* C;
+  long long sc_m;
+  int* err;              // set to 1 if a bounded wait gives up
+};
+
+struct GemmSmem {
+  __nv_bfloat16 a[kM * kKT];      // 16 KB
+  __nv_bfloat16 b[kNMax * kKT];   // 32 KB
+  unsigned long long mbar;
+  unsigned tmem_base;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row, k) of a K-major slice in the canonical
+// no-swizzle layout.
+__device__ __forceinline__ unsigned core_offset(int row, int k) {
+  return (unsigned)(((row >> 3) * (kKT / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor (SM100 form): start address, leading-
+// dimension byte offset (between K-adjacent core matrices), stride byte
+// offset (between 8-row groups), version 1, no swizzle.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo,
+                                                        unsigned sbo) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((addr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N.
+__device__ __forceinline__ unsigned instr_desc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
+         ((unsigned)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned phase) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  GemmSmem& sm = *reinterpret_cast<GemmSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kM;
+  const int n_mma = (g.N + 15) / 16 * 16;  // UMMA N: multiple of 16
+  unsigned ncols = 32;
+  while ((int)ncols < n_mma) ncols <<= 1;  // TMEM allocation: power of 2 >= 32
+  const unsigned mbar = smem_u32(&sm.mbar);
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&sm.tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const unsigned tmem = sm.tmem_base;
+
+  const unsigned a_base = smem_u32(sm.a), b_base = smem_u32(sm.b);
+  const unsigned idesc = instr_desc(n_mma);
+  const bool a_rows_contig = g.sa_k == 1;
+  const bool b_cols_contig = g.sb_n == 1;
+  bool ok = true;
+  unsigned phase = 0;
+  const int nk = (g.K + kKT - 1) / kKT;
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int k0 = kt * kKT;
+    // stage A (128 x 64) and B (n_mma x 64) as BF16, zero outside the matrix
+    for (int e = tid; e < kM * kKT; e += kThreads) {
+      int r, k;
+      if (a_rows_contig) { r = e / kKT; k = e % kKT; }
+      else { k = e / kM; r = e % kM; }
+      const int m = m0 + r, kk = k0 + k;
+      const float v = (m < g.M && kk < g.K) ? g.A[m * g.sa_m + kk * g.sa_k] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.a) +
+                                        core_offset(r, k)) = __float2bfloat16_rn(v);
+    }
+    for (int e = tid; e < n_mma * kKT; e += kThreads) {
+      int n, k;
+      if (b_cols_contig) { k = e / n_mma; n = e % n_mma; }
+      else { n = e / kKT; k = e % kKT; }
+      const int kk = k0 + k;
+      const float v = (n < g.N && kk < g.K) ? g.B[kk * g.sb_k + n * g.sb_n] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.b) +
+                                        core_offset(n, k)) = __float2bfloat16_rn(v);
+    }
+    // make the generic-proxy writes visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int s = 0; s < kKT / 16; ++s) {
+        // K slice s = core matrices 2s, 2s + 1 along K
+        const unsigned long long da = smem_desc(a_base + s * 256, 128, 1024);
+        const unsigned long long db = smem_desc(b_base + s * 256, 128, 1024);
+        const unsigned accum = (kt > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(accum)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              mbar)
+          : "memory");
+    }
+    // wait for the MMAs of this slice before the slices are rewritten; the
+    // verdict is made uniform over the CTA so every thread leaves together
+    ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(g.err, 1);
+    // give in-flight MMAs a second bounded chance before TMEM is released
+    mbar_wait(mbar, phase ^ 1u);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 = rows of the tile
+    const int row = warp * 32 + lane;
+    const int m = m0 + row;
+    for (int c0 = 0; c0 < n_mma; c0 += 8) {
+      unsigned r[8];
+      const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+            "=r"(r[6]), "=r"(r[7])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (m < g.M) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = c0 + j;
+          if (n >= g.N) continue;
+          float v = __uint_as_float(r[j]);
+          if (g.H) {
+            const float h = g.H[m * g.sh_m + n];
+            v *= (1.f - h * h);
+          } else {
+            if (g.bias) v += g.bias[n];
+            if (g.act == 1) v = tanhf(v);
+          }
+          g.C[m * g.sc_m + n] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(ncols)
+                 : "memory");
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
+  static bool attr = false;
+  // 100 KB of shared memory per CTA keeps at most two CTAs on an SM, so
+  // their TMEM allocations (<= 256 columns each) never exceed the SM's 512.
+  const int bytes = (int)sizeof(GemmSmem) + 1024 > 100 * 1024 ? (int)sizeof(GemmSmem) + 1024
+                                                              : 100 * 1024;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (g.N < 1 || g.N > kNMax || g.M < 1 || g.K < 1) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((g.M + kM - 1) / kM);
+  k_gemm_tc<<<grid, kThreads, bytes, s>>>(g);
+  return cudaGetLastError();
+}
+
+// dY = 2 (Y - T) / (B n_out) and the loss sum((Y - T)^2) / (B n_out) (one
+// block, fixed-order reduction).
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, int n,
+                      float scale, float* __restrict__ dy, float* __restrict__ loss) {
+  __shared__ float sh[1024];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float d = y[i] - t[i];
+    dy[i] = 2.f * d * scale;
+    acc += d * d;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = sh[0] * scale;
+}
+
+// db[n] = sum_b dZ[b, n] (one thread per column, fixed order).
+__global__ void k_colsum(const float* __restrict__ dz, int rows, int cols,
+                         float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= cols) return;
+  float s = 0.f;
+  for (int b = 0; b < rows; ++b) s += dz[(size_t)b * cols + n];
+  db[n] = s;
+}
+
+// One Adam step over all parameters (bias-corrected, Kingma & Ba).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace mlp
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// C ABI of the surrogate network.
+// ---------------------------------------------------------------------------
+using namespace lbm::mlp;
+
+struct lbm_mlp {
+  int n_in, width, depth, n_out, max_batch, nlayers;
+  int dims[66];
+  long long woff[65], boff[65];  // offsets of W_l, b_l in the flat vector
+  long long nparams;
+  float *theta, *grad, *adam_m, *adam_v;
+  float* acts;         // activations: layer l input at acts + aoff[l]
+  long long aoff[66];
+  float* dz[2];        // ping-pong backward buffers (max_batch x max width)
+  float* dy;           // loss gradient (max_batch x n_out)
+  float* loss;         // device scalar
+  int* err;            // device error word of the GEMMs
+  long long step;
+  cudaStream_t stream;
+  char msg[512];
+};
+
+static thread_local char g_mlp_create_err[512];
+
+static lbm_status mlp_fail(lbm_mlp* m, lbm_status s, const char* fmt, ...) {
+  char* dst = m ? m->msg : g_mlp_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define MLP_CUDA(m, call, what)                                                     \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) return mlp_fail(m, LBM_ERR_CUDA, "%s: %s", what,         \
+                                           cudaGetErrorString(e_));                 \
+  } while (0)
+
+static void mlp_release(lbm_mlp* m) {
+  cudaFree(m->theta);
+  cudaFree(m->grad);
+  cudaFree(m->adam_m);
+  cudaFree(m->adam_v);
+  cudaFree(m->acts);
+  cudaFree(m->dz[0]);
+  cudaFree(m->dz[1]);
+  cudaFree(m->dy);
+  cudaFree(m->loss);
+  cudaFree(m->err);
+}
+
+extern "C" lbm_status lbm_mlp_create(int n_in, int width, int depth, int n_out,
+                                     int max_batch, void* cuda_stream, lbm_mlp** out) {
+  g_mlp_create_err[0] = 0;
+  if (!out) return mlp_fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_in < 1 || n_in > kNMax || width < 1 || width > kNMax || depth < 0 || depth > 64 ||
+      n_out < 1 || n_out > kNMax || max_batch < 1 || max_batch > (1 << 20))
+    return mlp_fail(nullptr, LBM_ERR_ARG,
+                    "need 1 <= n_in, width, n_out <= 256, 0 <= depth <= 64, "
+                    "1 <= max_batch <= 2^20");
+  lbm_mlp* m = new (std::nothrow) lbm_mlp;
+  if (!m) return mlp_fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+  memset(m, 0, sizeof(*m));
+  m->n_in = n_in;
+  m->width = width;
+  m->depth = depth;
+  m->n_out = n_out;
+  m->max_batch = max_batch;
+  m->stream = (cudaStream_t)cuda_stream;
+  m->nlayers = depth + 1;
+  m->dims[0] = n_in;
+  for (int l = 1; l <= depth; ++l) m->dims[l] = width;
+  m->dims[depth + 1] = n_out;
+  long long o = 0, ao = 0;
+  for (int l = 0; l < m->nlayers; ++l) {
+    m->woff[l] = o;
+    o += (long long)m->dims[l] * m->dims[l + 1];
+    m->boff[l] = o;
+    o += m->dims[l + 1];
+  }
+  for (int l = 0; l <= m->nlayers; ++l) {
+    m->aoff[l] = ao;
+    ao += (long long)max_batch * m->dims[l];
+  }
+  m->nparams = o;
+  const size_t pb = sizeof(float) * (size_t)o;
+  const size_t wmax = (size_t)max_batch * (size_t)(width > n_out ? (width > n_in ? width : n_in)
+                                                                  : (n_out > n_in ? n_out : n_in));
+  bool okay = cudaMalloc(&m->theta, pb) == cudaSuccess && cudaMalloc(&m->grad, pb) == cudaSuccess &&
+              cudaMalloc(&m->adam_m, pb) == cudaSuccess && cudaMalloc(&m->adam_v, pb) == cudaSuccess &&
+              cudaMalloc(&m->acts, sizeof(float) * (size_t)ao) == cudaSuccess &&
+              cudaMalloc(&m->dz[0], sizeof(float) * wmax) == cudaSuccess &&
+              cudaMalloc(&m->dz[1], sizeof(float) * wmax) == cudaSuccess &&
+              cudaMalloc(&m->dy, sizeof(float) * (size_t)max_batch * n_out) == cudaSuccess &&
+              cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->err, sizeof(int)) == cudaSuccess;
+  if (!okay) {
+    cudaGetLastError();
+    mlp_release(m);
+    delete m;
+    return mlp_fail(nullptr, LBM_ERR_OOM, "cudaMalloc failed");
+  }
+  cudaMemsetAsync(m->theta, 0, pb, m->stream);
+  cudaMemsetAsync(m->adam_m, 0, pb, m->stream);
+  cudaMemsetAsync(m->adam_v, 0, pb, m->stream);
+  cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
+  *out = m;
+  return LBM_OK;
+}
+
+extern "C" void lbm_mlp_destroy(lbm_mlp* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  else cudaDeviceSynchronize();
+  mlp_release(m);
+  delete m;
+}
+
+extern "C" const char* lbm_mlp_last_error(const lbm_mlp* m) {
+  return m ? m->msg : g_mlp_create_err;
+}
+
+extern "C" size_t lbm_mlp_num_params(const lbm_mlp* m) { return m ? (size_t)m->nparams : 0; }
+
+extern "C" lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* theta) {
+  if (!m || !theta) return m ? mlp_fail(m, LBM_ERR_ARG, "theta is NULL") : LBM_ERR_ARG;
+  MLP_CUDA(m, cudaMemcpyAsync(m->theta, theta, sizeof(float) * (size_t)m->nparams,
+                              cudaMemcpyDefault, m->stream),
+           "cudaMemcpyAsync");
+  MLP_CUDA(m, cudaMemsetAsync(m->adam_m, 0, sizeof(float) * (size_t)m->nparams, m->stream),
+           "cudaMemsetAsync");
+  MLP_CUDA(m, cudaMemsetAsync(m->adam_v, 0, sizeof(float) * (size_t)m->nparams, m->stream),
+           "cudaMemsetAsync");
+  MLP_CUDA(m, cudaStreamSynchronize(m->stream), "stream sync");
+  m->step = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_mlp_get_params(lbm_mlp* m, float* theta) {
+  if (!m || !theta) return m ? mlp_fail(m, LBM_ERR_ARG, "theta is NULL") : LBM_ERR_ARG;
+  MLP_CUDA(m, cudaMemcpyAsync(theta, m->theta, sizeof(float) * (size_t)m->nparams,
+                              cudaMemcpyDefault, m->stream),
+           "cudaMemcpyAsync");
+  MLP_CUDA(m, cudaStreamSynchronize(m->stream), "stream sync");
+  return LBM_OK;
+}
+
+static lbm_status gemm(lbm_mlp* m, const GemmArgs& g) {
+  MLP_CUDA(m, launch_gemm(g, m->stream), "tensor-core GEMM launch");
+  return LBM_OK;
+}
+
+// Forward pass for `batch` rows of x (device, batch x n_in); activations
+// stay in m->acts; returns the output pointer.
+static lbm_status mlp_forward_dev(lbm_mlp* m, const float* x, int batch, float** y_out) {
+  MLP_CUDA(m, cudaMemcpyAsync(m->acts + m->aoff[0], x, sizeof(float) * (size_t)batch * m->n_in,
+                              cudaMemcpyDeviceToDevice, m->stream),
+           "cudaMemcpyAsync");
+  for (int l = 0; l < m->nlayers; ++l) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    const int din = m->dims[l], dout = m->dims[l + 1];
+    g.A = m->acts + m->aoff[l];
+    g.sa_m = din;
+    g.sa_k = 1;
+    g.B = m->theta + m->woff[l];
+    g.sb_k = dout;
+    g.sb_n = 1;
+    g.M = batch;
+    g.N = dout;
+    g.K = din;
+    g.bias = m->theta + m->boff[l];
+    g.act = (l < m->nlayers - 1) ? 1 : 0;
+    g.C = m->acts + m->aoff[l + 1];
+    g.sc_m = dout;
+    g.err = m->err;
+    lbm_status st = gemm(m, g);
+    if (st != LBM_OK) return st;
+  }
+  *y_out = m->acts + m->aoff[m->nlayers];
+  return LBM_OK;
+}
+
+static lbm_status check_batch(lbm_mlp* m, int batch) {
+  if (batch < 1 || batch > m->max_batch)
+    return mlp_fail(m, LBM_ERR_ARG, "batch must lie in [1, %d]", m->max_batch);
+  return LBM_OK;
+}
+
+static lbm_status check_err(lbm_mlp* m) {
+  int e = 0;
+  MLP_CUDA(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream),
+           "cudaMemcpyAsync");
+  MLP_CUDA(m, cudaStreamSynchronize(m->stream), "stream sync");
+  if (e) return mlp_fail(m, LBM_ERR_TIMEOUT, "a tensor-core GEMM wait gave up");
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y) {
+  if (!m || !x || !y) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
+  lbm_status st = check_batch(m, batch);
+  if (st != LBM_OK) return st;
+  float* yd = nullptr;
+  if ((st = mlp_forward_dev(m, x, batch, &yd)) != LBM_OK) return st;
+  MLP_CUDA(m, cudaMemcpyAsync(y, yd, sizeof(float) * (size_t)batch * m->n_out,
+                              cudaMemcpyDefault, m->stream),
+           "cudaMemcpyAsync");
+  return LBM_OK;
+}
+
+// Loss and gradient into m->grad (device).
+static lbm_status mlp_backward(lbm_mlp* m, const float* x, const float* t, int batch) {
+  float* y = nullptr;
+  lbm_status st = mlp_forward_dev(m, x, batch, &y);
+  if (st != LBM_OK) return st;
+  const int nout = m->n_out;
+  k_mse<<<1, 1024, 0, m->stream>>>(y, t, batch * nout, 1.f / (float)(batch * nout), m->dy,
+                                   m->loss);
+  MLP_CUDA(m, cudaGetLastError(), "loss kernel");
+  const float* dz = m->dy;  // the output layer is linear: dZ = dY
+  int buf = 0;
+  for (int l = m->nlayers - 1; l >= 0; --l) {
+    const int din = m->dims[l], dout = m->dims[l + 1];
+    const float* h_in = m->acts + m->aoff[l];
+    // dW_l = H_{l-1}^T dZ_l  (M = din, N = dout, K = batch)
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.A = h_in;
+    g.sa_m = 1;
+    g.sa_k = din;
+    g.B = dz;
+    g.sb_k = dout;
+    g.sb_n = 1;
+    g.M = din;
+    g.N = dout;
+    g.K = batch;
+    g.C = m->grad + m->woff[l];
+    g.sc_m = dout;
+    g.err = m->err;
+    if ((st = gemm(m, g)) != LBM_OK) return st;
+    k_colsum<<<(dout + 127) / 128, 128, 0, m->stream>>>(dz, batch, dout, m->grad + m->boff[l]);
+    MLP_CUDA(m, cudaGetLastError(), "bias-gradient kernel");
+    if (l > 0) {
+      // dZ_{l-1} = (dZ_l W_l^T) * (1 - H_{l-1}^2)  (M = batch, N = din, K = dout)
+      GemmArgs h;
+      memset(&h, 0, sizeof(h));
+      h.A = dz;
+      h.sa_m = dout;
+      h.sa_k = 1;
+      h.B = m->theta + m->woff[l];
+      h.sb_k = 1;
+      h.sb_n = dout;
+      h.M = batch;
+      h.N = din;
+      h.K = dout;
+      h.H = h_in;
+      h.sh_m = din;
+      h.C = m->dz[buf];
+      h.sc_m = din;
+      h.err = m->err;
+      if ((st = gemm(m, h)) != LBM_OK) return st;
+      dz = m->dz[buf];
+      buf ^= 1;
+    }
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_mlp_loss_grad(lbm_mlp* m, const float* x, const float* t, int batch,
+                                        float* loss, float* grad) {
+  if (!m || !x || !t) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
+  lbm_status st = check_batch(m, batch);
+  if (st != LBM_OK) return st;
+  if ((st = mlp_backward(m, x, t, batch)) != LBM_OK) return st;
+  if (grad)
+    MLP_CUDA(m, cudaMemcpyAsync(grad, m->grad, sizeof(float) * (size_t)m->nparams,
+                                cudaMemcpyDefault, m->stream),
+             "cudaMemcpyAsync");
+  if (loss)
+    MLP_CUDA(m, cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDefault, m->stream),
+             "cudaMemcpyAsync");
+  return check_err(m);
+}
+
+extern "C" lbm_status lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* t, int batch,
+                                         float lr, float* loss) {
+  if (!m || !x || !t) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
+  lbm_status st = check_batch(m, batch);
+  if (st != LBM_OK) return st;
+  if ((st = mlp_backward(m, x, t, batch)) != LBM_OK) return st;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - pow(0.9, (double)m->step));
+  const float c2 = (float)(1.0 - pow(0.999, (double)m->step));
+  k_adam<<<(unsigned)((m->nparams + 255) / 256), 256, 0, m->stream>>>(
+      m->theta, m->grad, m->adam_m, m->adam_v, m->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  MLP_CUDA(m, cudaGetLastError(), "Adam kernel");
+  if (loss) {
+    MLP_CUDA(m, cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDefault, m->stream),
+             "cudaMemcpyAsync");
+    return check_err(m);
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_gemm_bf16(const float* A, long long sa_m, long long sa_k,
+                                    const float* B, long long sb_k, long long sb_n, float* C,
+                                    long long sc_m, int M, int N, int K, int* err,
+                                    void* cuda_stream) {
+  if (!A || !B || !C || !err || M < 1 || N < 1 || N > kNMax || K < 1)
+    return LBM_ERR_ARG;
+  GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.sa_m = sa_m;
+  g.sa_k = sa_k;
+  g.B = B;
+  g.sb_k = sb_k;
+  g.sb_n = sb_n;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.C = C;
+  g.sc_m = sc_m;
+  g.err = err;
+  return launch_gemm(g, (cudaStream_t)cuda_stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}

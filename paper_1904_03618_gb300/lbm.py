@@ -106,6 +106,29 @@ _lib.lbm_batch_set_f.argtypes = [_ctx_p, ctypes.c_int, _fp]
 _lib.lbm_batch_set_f.restype = ctypes.c_int
 _lib.lbm_set_graphs.argtypes = [_ctx_p, ctypes.c_int]
 _lib.lbm_set_graphs.restype = ctypes.c_int
+_mlp_p = ctypes.c_void_p
+_lib.lbm_mlp_create.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+_lib.lbm_mlp_create.restype = ctypes.c_int
+_lib.lbm_mlp_num_params.argtypes = [_mlp_p]
+_lib.lbm_mlp_num_params.restype = ctypes.c_size_t
+_lib.lbm_mlp_set_params.argtypes = [_mlp_p, _fp]
+_lib.lbm_mlp_set_params.restype = ctypes.c_int
+_lib.lbm_mlp_get_params.argtypes = [_mlp_p, _fp]
+_lib.lbm_mlp_get_params.restype = ctypes.c_int
+_lib.lbm_mlp_forward.argtypes = [_mlp_p, _fp, ctypes.c_int, _fp]
+_lib.lbm_mlp_forward.restype = ctypes.c_int
+_lib.lbm_mlp_loss_grad.argtypes = [_mlp_p, _fp, _fp, ctypes.c_int, _fp, _fp]
+_lib.lbm_mlp_loss_grad.restype = ctypes.c_int
+_lib.lbm_mlp_train_step.argtypes = [_mlp_p, _fp, _fp, ctypes.c_int, ctypes.c_float, _fp]
+_lib.lbm_mlp_train_step.restype = ctypes.c_int
+_lib.lbm_mlp_destroy.argtypes = [_mlp_p]
+_lib.lbm_mlp_destroy.restype = None
+_lib.lbm_mlp_last_error.argtypes = [_mlp_p]
+_lib.lbm_mlp_last_error.restype = ctypes.c_char_p
+_lib.lbm_gemm_bf16.argtypes = [_fp, ctypes.c_longlong, ctypes.c_longlong, _fp, ctypes.c_longlong,
+                               ctypes.c_longlong, _fp, ctypes.c_longlong, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, _fp, ctypes.c_void_p]
+_lib.lbm_gemm_bf16.restype = ctypes.c_int
 _lib.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
 _lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_launches_per_step.argtypes = [_ctx_p]
@@ -121,7 +144,10 @@ EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
             "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
-            "lbm_batch_set_f", "lbm_set_graphs",
+            "lbm_batch_set_f", "lbm_set_graphs", "lbm_mlp_create", "lbm_mlp_num_params",
+            "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_forward",
+            "lbm_mlp_loss_grad", "lbm_mlp_train_step", "lbm_mlp_destroy",
+            "lbm_mlp_last_error", "lbm_gemm_bf16",
             "lbm_launches_per_step", "lbm_destroy", "lbm_last_error")
 
 
@@ -290,6 +316,62 @@ def lbm_step_noalloc(params: LbmParams, f_in, f_out, stream=None):
     st = _lib.lbm_step_noalloc(ctypes.byref(params), _addr(f_in), _addr(f_out), s)
     if st != LBM_OK:
         raise LbmError(st, lbm_last_error(None))
+
+
+def _mlp_check(m, st):
+    if st != LBM_OK:
+        msg = _lib.lbm_mlp_last_error(m)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+def lbm_mlp_create(n_in, width, depth, n_out, max_batch, stream=None):
+    m = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream) if stream else None
+    _mlp_check(None, _lib.lbm_mlp_create(n_in, width, depth, n_out, max_batch, s,
+                                         ctypes.byref(m)))
+    return m
+
+
+def lbm_mlp_num_params(m) -> int:
+    return int(_lib.lbm_mlp_num_params(m))
+
+
+def lbm_mlp_set_params(m, theta):
+    _mlp_check(m, _lib.lbm_mlp_set_params(m, _addr(theta)))
+
+
+def lbm_mlp_get_params(m, theta):
+    _mlp_check(m, _lib.lbm_mlp_get_params(m, _addr(theta)))
+
+
+def lbm_mlp_forward(m, x, batch, y):
+    _mlp_check(m, _lib.lbm_mlp_forward(m, _addr(x), int(batch), _addr(y)))
+
+
+def lbm_mlp_loss_grad(m, x, t, batch, grad=None):
+    loss = ctypes.c_float()
+    _mlp_check(m, _lib.lbm_mlp_loss_grad(m, _addr(x), _addr(t), int(batch),
+                                         ctypes.addressof(loss), _addr(grad)))
+    return float(loss.value)
+
+
+def lbm_mlp_train_step(m, x, t, batch, lr, want_loss=False):
+    loss = ctypes.c_float()
+    _mlp_check(m, _lib.lbm_mlp_train_step(m, _addr(x), _addr(t), int(batch), float(lr),
+                                          ctypes.addressof(loss) if want_loss else None))
+    return float(loss.value) if want_loss else None
+
+
+def lbm_mlp_destroy(m):
+    _lib.lbm_mlp_destroy(m)
+
+
+def lbm_gemm_bf16(A, sa_m, sa_k, B, sb_k, sb_n, C, sc_m, M, N, K, err, stream=None):
+    s = ctypes.c_void_p(stream) if stream else None
+    st = _lib.lbm_gemm_bf16(_addr(A), sa_m, sa_k, _addr(B), sb_k, sb_n, _addr(C), sc_m,
+                            M, N, K, _addr(err), s)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_gemm_bf16 failed")
 
 
 def lbm_launches_per_step(ctx) -> int:
