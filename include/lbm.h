@@ -209,6 +209,15 @@ lbm_status lbm_batch_moments(lbm_ctx *ctx, int case_index, float *rho_R,
                              float *rho_B, float *u);
 lbm_status lbm_batch_diagnostics(lbm_ctx *ctx, int case_index,
                                  double out[16]);
+/* For every case, the number of cells of the lattice plane normal to `axis`
+   (0 = x, 1 = y, 2 = z) at coordinate `index` where the red colour dominates
+   (rho^N > 0, rho^N as defined below Eq. 8), at the current time level.  With a
+   wall at z = 0 and index 0 this is the wetted footprint of a red drop on
+   the floor (area in lattice cells); the paper has no counterpart.  counts:
+   ncases long longs, host or device.  index must lie inside every case;
+   synchronises the stream. */
+lbm_status lbm_batch_footprint(lbm_ctx *ctx, int axis, int index,
+                               long long *counts);
 lbm_status lbm_batch_get_f(lbm_ctx *ctx, int case_index, float *f);
 lbm_status lbm_batch_set_f(lbm_ctx *ctx, int case_index, const float *f);
 

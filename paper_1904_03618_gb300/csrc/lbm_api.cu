@@ -42,6 +42,7 @@ struct lbm_ctx {
   float* staging;           // device staging for host-pointer transfers
   size_t staging_floats;
   lbm::BatchCase* d_cases;  // device case table of the batched kernel
+  unsigned long long* foot; // per-case plane counts (lbm_batch_footprint)
   int total_items;
   cudaGraphExec_t graph;    // two captured steps (buffer 0 -> 1 -> 0)
   int use_graph;
@@ -206,6 +207,7 @@ static void release(lbm_ctx* c) {
   cudaFree(c->diag_out);
   cudaFree(c->staging);
   cudaFree(c->d_cases);
+  cudaFree(c->foot);
   delete[] c->cases;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -597,6 +599,33 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
 
 extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
   return lbm_batch_diagnostics(c, 0, out);
+}
+
+extern "C" lbm_status lbm_batch_footprint(lbm_ctx* c, int axis, int index,
+                                          long long* counts) {
+  if (!c || !counts) return c ? fail(c, LBM_ERR_ARG, "counts is NULL") : LBM_ERR_ARG;
+  if (axis < 0 || axis > 2) return fail(c, LBM_ERR_ARG, "axis must be 0, 1 or 2");
+  for (int k = 0; k < c->ncases; ++k) {
+    const lbm_params& p = c->cases[k].p;
+    const int n = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+    if (index < 0 || index >= n)
+      return fail(c, LBM_ERR_ARG, "plane index %d outside case %d (extent %d)", index, k, n);
+    if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "footprint before init (case %d)", k);
+  }
+  if (!c->foot)
+    LBM_CUDA(c, cudaMalloc(&c->foot, sizeof(unsigned long long) * c->ncases), "cudaMalloc");
+  LBM_CUDA(c, cudaMemsetAsync(c->foot, 0, sizeof(unsigned long long) * c->ncases, c->stream),
+           "cudaMemsetAsync");
+  for (int k = 0; k < c->ncases; ++k)
+    LBM_CUDA(c, lbm::launch_footprint(c->storage, case_buffer(c, c->cur, k), c->cases[k].args,
+                                      axis, index, c->foot + k, c->stream),
+             "footprint kernel");
+  static_assert(sizeof(long long) == sizeof(unsigned long long), "64-bit counts");
+  LBM_CUDA(c, cudaMemcpyAsync(counts, c->foot, sizeof(long long) * c->ncases,
+                              cudaMemcpyDefault, c->stream),
+           "cudaMemcpyAsync D2H");
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_batch_get_f(lbm_ctx* c, int k, float* f) {

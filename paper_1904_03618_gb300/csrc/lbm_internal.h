@@ -28,6 +28,8 @@ cudaError_t launch_get_f(int storage, const void* src, const StepArgs& a,
                          float* f, cudaStream_t s);
 cudaError_t launch_moments(int storage, const void* src, const StepArgs& a,
                            float* rR, float* rB, float* u, cudaStream_t s);
+cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, int axis,
+                             int index, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         double* part, int nblocks, double* out,
                         cudaStream_t s);

@@ -136,6 +136,31 @@ __global__ void k_moments(const T* __restrict__ src, StepArgs a,
   }
 }
 
+// Cells of one lattice plane (normal `axis`, at coordinate `index`) where the
+// red colour dominates, rho^N > 0, i.e. rho_R / rho_R^in > rho_B / rho_B^in
+// (the order-parameter definition of the phase field).  One thread per plane
+// cell, warp ballots, one atomic per warp into the 64-bit count.
+template <typename T>
+__global__ void k_footprint(const T* __restrict__ src, StepArgs a, int axis, int index,
+                            unsigned long long* __restrict__ count) {
+  const int n0 = axis == 0 ? a.ny : a.nx;
+  const int n1 = axis == 2 ? a.ny : a.nz;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  bool red = false;
+  if (e < n0 * n1) {
+    const int i = e % n0, j = e / n0;
+    const int x = axis == 0 ? index : i;
+    const int y = axis == 1 ? index : (axis == 0 ? i : j);
+    const int z = axis == 2 ? index : j;
+    float fR[19], fB[19];
+    pull_pairs<T>(src, a, x, y, z, fR, fB);
+    const Macro m = macro_of(a, fR, fB);
+    red = m.rR * a.inv_rin_R > m.rB * a.inv_rin_B;
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, red);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
 // ---------------------------------------------------------------------------
 // Diagnostics with FP64 results.  Each thread accumulates its cells' colour
 // masses, momentum and red-mass moments in FP32 with Neumaier compensation
@@ -362,6 +387,15 @@ cudaError_t launch_moments_t(const void* src, const StepArgs& a, float* rR,
   return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_footprint_t(const void* src, const StepArgs& a, int axis, int index,
+                               unsigned long long* count, cudaStream_t s) {
+  const int n0 = axis == 0 ? a.ny : a.nx;
+  const int n1 = axis == 2 ? a.ny : a.nz;
+  const unsigned blocks = (unsigned)((n0 * n1 + kAuxBlock - 1) / kAuxBlock);
+  k_footprint<T><<<blocks, kAuxBlock, 0, s>>>((const T*)src, a, axis, index, count);
+  return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
                           int nblocks, double* out, cudaStream_t s) {
   k_diag_partial<T><<<nblocks, kDiagBlock, 0, s>>>((const T*)src, a, part);
@@ -407,6 +441,10 @@ cudaError_t launch_get_f(int storage, const void* src, const StepArgs& a,
 cudaError_t launch_moments(int storage, const void* src, const StepArgs& a,
                            float* rR, float* rB, float* u, cudaStream_t s) {
   LBM_DISPATCH(storage, launch_moments_t, src, a, rR, rB, u, s)
+}
+cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, int axis,
+                             int index, unsigned long long* count, cudaStream_t s) {
+  LBM_DISPATCH(storage, launch_footprint_t, src, a, axis, index, count, s)
 }
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         double* part, int nblocks, double* out,

@@ -106,6 +106,8 @@ _lib.lbm_batch_set_f.argtypes = [_ctx_p, ctypes.c_int, _fp]
 _lib.lbm_batch_set_f.restype = ctypes.c_int
 _lib.lbm_set_graphs.argtypes = [_ctx_p, ctypes.c_int]
 _lib.lbm_set_graphs.restype = ctypes.c_int
+_lib.lbm_batch_footprint.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, _fp]
+_lib.lbm_batch_footprint.restype = ctypes.c_int
 _mlp_p = ctypes.c_void_p
 _lib.lbm_mlp_create.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
 _lib.lbm_mlp_create.restype = ctypes.c_int
@@ -144,7 +146,7 @@ EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
             "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
-            "lbm_batch_set_f", "lbm_set_graphs", "lbm_mlp_create", "lbm_mlp_num_params",
+            "lbm_batch_set_f", "lbm_batch_footprint", "lbm_set_graphs", "lbm_mlp_create", "lbm_mlp_num_params",
             "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_forward",
             "lbm_mlp_loss_grad", "lbm_mlp_train_step", "lbm_mlp_destroy",
             "lbm_mlp_last_error", "lbm_gemm_bf16",
@@ -490,6 +492,13 @@ class Batch:
 
     def diagnostics(self, case, raise_unstable=True):
         return lbm_batch_diagnostics(self.ctx, case, raise_unstable)
+
+    def footprint(self, axis=2, index=0):
+        """Red-dominated cell count of one plane, per case (int64 array)."""
+        out = np.zeros(len(self.params), dtype=np.int64)
+        _check(self.ctx, _lib.lbm_batch_footprint(self.ctx, int(axis), int(index),
+                                                  out.ctypes.data))
+        return out
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
