@@ -173,13 +173,21 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
    autotuner turns; results are identical for every valid configuration.
    Batch contexts accept (tile_y, hold) = (8, 2), (8, 0) or (16, 1).
    tile_y: CTA rows including the one-cell ring, 8 or 16 (the interior tile
-   is 30 x (tile_y - 2) cells).  zchunk: planes marched per CTA, 0 = the
+   is 30 x (tile_y - 2) cells), or 15 (below).  zchunk: planes marched per CTA, 0 = the
    library's default for this lattice.  hold: where the populations of a
    plane wait between the moment pass and the collision: 0 pulled again, 1
    registers, 2 shared memory (tile_y = 8 only), 3 shared memory filled by
    asynchronous copies issued two planes ahead (tile_y = 8 only), 4 shared
    memory with each thread handling two tile rows (tile_y = 16 only), 5 and
-   6 as 2 with registers capped for three and four CTAs per SM.
+   6 as 2 with registers capped for three and four CTAs per SM, 7 and 8 as
+   2 with each plane's pulls staged in shared memory by tensor copies (TMA)
+   issued two planes (7) or one plane (8) ahead, for single lattices with
+   nx * 8 bytes (FP32) or nx * 4 bytes (FP16/BF16) a multiple of 16;
+   tile_y = 8 is a 32 x 8 thread tile, tile_y = 16 a 16 x 16 thread tile
+   (interior 14 x 14; with hold 7 for 16-bit storage only) and tile_y = 15
+   (hold 7 and 8 only) a 34 x 15 thread tile (interior 32 x 13, one CTA per
+   SM).  The TMA waits are bounded and report LBM_ERR_TIMEOUT through
+   lbm_diagnostics.
    Errors: LBM_ERR_ARG. */
 lbm_status lbm_set_fused_config(lbm_ctx *ctx, int tile_y, int zchunk, int hold);
 lbm_status lbm_get_fused_config(const lbm_ctx *ctx, int *tile_y, int *zchunk,

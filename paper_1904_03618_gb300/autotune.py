@@ -24,7 +24,7 @@ import torch
 from . import lbm
 
 # (tile_y, hold) shapes; z chunks are tried for each
-SINGLE_SHAPES = [(8, 2), (8, 3), (8, 0), (16, 1), (16, 4)]
+SINGLE_SHAPES = [(8, 2), (8, 7), (8, 8), (16, 8), (16, 7), (8, 3), (8, 0), (16, 1), (16, 4)]
 BATCH_SHAPES = [(8, 2), (8, 0), (16, 1)]
 ZCHUNKS = [8, 12, 16, 24]
 

@@ -43,6 +43,9 @@ struct lbm_ctx {
   size_t staging_floats;
   lbm::BatchCase* d_cases;  // device case table of the batched kernel
   unsigned long long* foot; // per-case plane counts (lbm_batch_footprint)
+  int* d_flags;             // device error word of the kernels' bounded waits
+  bool tma_ok[3];           // tensor maps built, per tile kind (single lattice)
+  CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
   int total_items;
   cudaGraphExec_t graph;    // two captured steps (buffer 0 -> 1 -> 0)
   int use_graph;
@@ -208,6 +211,7 @@ static void release(lbm_ctx* c) {
   cudaFree(c->staging);
   cudaFree(c->d_cases);
   cudaFree(c->foot);
+  cudaFree(c->d_flags);
   delete[] c->cases;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -323,6 +327,24 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
     if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
         cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
+  }
+  if (st == LBM_OK) {
+    if (cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess)
+      st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the error word failed");
+  }
+  if (st == LBM_OK && ncases == 1 && c->kernel == LBM_KERNEL_FUSED &&
+      lbm::tma_eligible(c->cases[0].args, c->storage)) {
+    for (int w = 0; w < 3; ++w) {
+      c->tma_ok[w] = true;
+      for (int b = 0; b < 2 && c->tma_ok[w]; ++b)
+        c->tma_ok[w] = lbm::tma_build_maps(c->storage, c->pop[b], c->cases[0].args, w,
+                                           c->tmaps[b][w]) == cudaSuccess;
+    }
+    cudaGetLastError();
+    lbm::FusedConfig t;
+    if (lbm::tma_default_config(c->cases[0].args, c->storage, c->sms, c->tma_ok, &t))
+      c->fused = t;
   }
   if (st == LBM_OK && ncases > 1 &&
       cudaMalloc(&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
@@ -452,6 +474,14 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
                                 c->stream);
   else if (c->kernel == LBM_KERNEL_TWO_PASS)
     e = lbm::launch_twopass(c->storage, src, dst, c->cases[0].args, c->phase, c->stream);
+  else if (c->fused.hold == 7 || c->fused.hold == 8) {
+    const int w = lbm::tma_kind(c->fused.tile_y);
+    e = w >= 0 && c->tma_ok[w]
+            ? lbm::launch_fused_tma(c->storage, src, dst, c->cases[0].args, c->tmaps[from][w],
+                                    w, c->fused.hold == 7 ? 2 : 1, c->fused.zchunk,
+                                    c->d_flags, c->stream)
+            : cudaErrorInvalidValue;
+  }
   else
     e = lbm::launch_fused(c->storage, src, dst, c->cases[0].args, c->fused, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
@@ -590,6 +620,12 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   out[12] = (double)c->steps;
   out[13] = d[12];
   c->err[0] = 0;
+  int flags = 0;
+  LBM_CUDA(c, cudaMemcpy(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost),
+           "cudaMemcpy D2H");
+  if (flags)
+    return fail(c, LBM_ERR_TIMEOUT,
+                "a bounded wait of the step kernel gave up (code %d); results are invalid", flags);
   if (d[5] != 0.0 || d[6] != 0.0)
     return fail(c, LBM_ERR_UNSTABLE,
                 "%.0f cells with non-finite populations, %.0f with total density <= 0",
@@ -717,13 +753,19 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
                  ? (c->ncases > 1 ? 12 : lbm::default_fused_config(c->cases[0].args, c->storage).zchunk)
                  : zchunk;
   const bool ok = zchunk >= 0 && (c->ncases > 1 ? lbm::valid_batch_config(f)
-                                                : lbm::valid_fused_config(f, c->storage));
+                                                : lbm::valid_fused_config(f, c->storage)) &&
+                  ((f.hold != 7 && f.hold != 8) ||
+                   (lbm::tma_kind(f.tile_y) >= 0 && c->tma_ok[lbm::tma_kind(f.tile_y)] &&
+                    lbm::tma_config_fits(c->storage, lbm::tma_kind(f.tile_y),
+                                         f.hold == 7 ? 2 : 1)));
   if (!ok)
     return fail(c, LBM_ERR_ARG,
                 c->ncases > 1
                     ? "invalid batch configuration ((tile_y, hold) = (8, 2), (8, 0) or (16, 1), zchunk >= 0)"
-                    : "invalid fused configuration (tile_y 8 or 16, zchunk >= 0, hold 0..6, "
-                      "hold 2, 3, 5, 6 need tile_y 8, hold 4 needs tile_y 16)");
+                    : "invalid fused configuration (tile_y 8, 15 or 16, zchunk >= 0, hold "
+                      "0..8; hold 2, 3, 5, 6 need tile_y 8, hold 4 needs tile_y 16, tile_y 15 "
+                      "needs hold 7 or 8; hold 7 and 8 need nx * pair bytes a multiple of 16 "
+                      "and a tile whose stages fit shared memory)");
   c->fused = f;
   drop_graph(c);
   lbm_status st = upload_case_table(c);

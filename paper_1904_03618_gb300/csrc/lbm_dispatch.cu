@@ -26,6 +26,132 @@ cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fused_tma(int storage, const void* src, void* dst, const StepArgs& a,
+                             const CUtensorMap* maps, int kind, int ns, int zchunk, int* err,
+                             cudaStream_t s) {
+  switch (storage) {
+    case 0: return launch_fused_tma_storage<float>(src, dst, a, maps, kind, ns, zchunk, err, s);
+    case 1: return launch_fused_tma_storage<__half>(src, dst, a, maps, kind, ns, zchunk, err, s);
+    case 2:
+      return launch_fused_tma_storage<__nv_bfloat16>(src, dst, a, maps, kind, ns, zchunk, err,
+                                                     s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int tma_kind(int tile_y) { return tile_y == 8 ? 0 : (tile_y == 16 ? 1 : (tile_y == 15 ? 2 : -1)); }
+
+static const int kTmaTW[3] = {32, 16, 34}, kTmaBY[3] = {8, 16, 15};
+
+bool tma_config_fits(int storage, int kind, int ns) {
+  if (kind < 0 || kind > 2 || ns < 1 || ns > 2) return false;
+  switch (storage) {
+    case 0: return tma_config_fits_storage<float>(kind, ns);
+    case 1: return tma_config_fits_storage<__half>(kind, ns);
+    case 2: return tma_config_fits_storage<__nv_bfloat16>(kind, ns);
+  }
+  return false;
+}
+
+// Pair bytes of a storage type (red and blue value of one direction and cell).
+static int pair_bytes(int storage) { return storage == 0 ? 8 : 4; }
+
+bool tma_eligible(const StepArgs& a, int storage) {
+  return ((long long)a.nx * pair_bytes(storage)) % 16 == 0 && a.nz >= 3;
+}
+
+// Default TMA configuration.  Tile: the one with more interior cells per
+// launched thread for this nx x ny (the 34 x 15 tile wins where nx is a
+// multiple of 32, the 32 x 8 tile where it is a multiple of 30).  Stages:
+// two for FP32, one for 16-bit storage.  z chunk: each CTA refills two halo
+// planes (about half a plane of work), and CTAs run in rounds of (SMs x
+// CTAs per SM), so the chunk minimises rounds x (zchunk + 1/2).  On GB300 at
+// 128^3 this picks the 34 x 15 tile with 12-plane chunks: 14.4 GLUPS (FP32)
+// and 15.7 GLUPS (FP16) against 13.1 and 14.6 for the shared-memory hold.
+// 16-bit storage on a lattice where the 32 x 8 tile fits better keeps the
+// plain shared-memory hold, which is ahead of its TMA form there.
+bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind_ok[3],
+                        FusedConfig* out) {
+  if (!tma_eligible(a, storage)) return false;
+  double best_eff = -1.0;
+  int kind = -1;
+  for (int k : {0, 2}) {
+    if (!kind_ok[k]) continue;
+    const int tw = kTmaTW[k], by = kTmaBY[k];
+    const double tiles = (double)((a.nx + tw - 3) / (tw - 2)) * ((a.ny + by - 3) / (by - 2));
+    const double eff = (double)a.nx * a.ny / (tiles * tw * by);
+    if (eff > best_eff * 1.02) {
+      best_eff = eff;
+      kind = k;
+    }
+  }
+  if (kind < 0) return false;
+  const int ns = storage == 0 ? 2 : 1;
+  if (storage != 0 && kind == 0) return false;
+  if (!tma_config_fits(storage, kind, ns)) return false;
+  const int tw = kTmaTW[kind], by = kTmaBY[kind];
+  const long long cols = (long long)((a.nx + tw - 3) / (tw - 2)) * ((a.ny + by - 3) / (by - 2));
+  const long long slots = (long long)(sms > 0 ? sms : 152) * (kind == 2 ? 1 : 2);
+  int best_zc = 12;
+  double best_cost = 1e300;
+  for (int zc = 6; zc <= 24; ++zc) {
+    const long long ctas = cols * ((a.nz + zc - 1) / zc);
+    const double cost = (double)((ctas + slots - 1) / slots) * (zc + 1.5);
+    if (cost <= best_cost + 1e-9) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  out->tile_y = by;
+  out->hold = ns == 2 ? 7 : 8;
+  out->zchunk = best_zc < a.nz ? best_zc : a.nz;
+  return true;
+}
+
+// Two tensor maps over a population buffer seen as a 4-D array of pairs
+// [direction][z][y][x] (x fastest; direction stride = the padded plane),
+// for a tile of tw x by threads: FP32 map 0 has tw-pair boxes, map 1
+// (tw + 2)-pair boxes; 16-bit storage uses tw + 4 pairs rounded up to a
+// multiple of 4 (map 1 = map 0).  Boxes are by rows by one plane by one direction, no swizzle; cells
+// beyond the array read as zero.
+cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
+                           CUtensorMap maps[2]) {
+  if (kind < 0 || kind > 2) return cudaErrorInvalidValue;
+  const int tw = kTmaTW[kind], by = kTmaBY[kind];
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return e != cudaSuccess ? e : cudaErrorNotSupported;
+    encode = (EncodeFn)fn;
+  }
+  if (!tma_eligible(a, storage)) return cudaErrorInvalidValue;
+  const cuuint64_t E = (cuuint64_t)pair_bytes(storage);
+  const cuuint64_t dims[4] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz, 19};
+  const cuuint64_t strides[3] = {E * a.nx, E * a.nx * a.ny, E * (cuuint64_t)a.plane};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt =
+      storage == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  for (int m = 0; m < 2; ++m) {
+    const cuuint32_t w =
+        (cuuint32_t)(storage == 0 ? (m == 0 ? tw : tw + 2) : (tw + 4 + 3) / 4 * 4);
+    const cuuint32_t box[4] = {w, (cuuint32_t)by, 1, 1};
+    const CUresult r = encode(&maps[m], dt, 4, const_cast<void*>(base), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
 // Batched kernel variants: (tile_y, hold) = (8, 2), (8, 0), (16, 1).
 bool valid_batch_config(const FusedConfig& c) {
   const bool shape = (c.tile_y == 8 && (c.hold == 2 || c.hold == 0)) ||
@@ -34,9 +160,10 @@ bool valid_batch_config(const FusedConfig& c) {
 }
 
 bool valid_fused_config(const FusedConfig& c, int storage) {
+  if (c.tile_y == 15) return (c.hold == 7 || c.hold == 8) && c.zchunk > 0;
   if (c.tile_y != 8 && c.tile_y != 16) return false;
-  if (c.hold < 0 || c.hold > 6) return false;
-  if ((c.hold == 2 || c.hold == 3 || c.hold >= 5) && c.tile_y != 8) return false;
+  if (c.hold < 0 || c.hold > 8) return false;
+  if ((c.hold == 2 || c.hold == 3 || c.hold == 5 || c.hold == 6) && c.tile_y != 8) return false;
   if (c.hold == 4 && c.tile_y != 16) return false;
   (void)storage;
   return c.zchunk > 0;

@@ -150,9 +150,9 @@ __device__ __forceinline__ void store_recoloured(T* dst, unsigned plane,
 // from the shared window, as weighted differences of opposite neighbours so
 // that a uniform field gives an exactly zero gradient.  A neighbour beyond a
 // wall takes the centre value.
-template <int BY>
+template <int BY, int TW = kTileW>
 __device__ __forceinline__ void window_gradients(
-    const float4 (*win)[BY][kTileW], int z, int ty, int tx, bool xlo, bool xhi,
+    const float4 (*win)[BY][TW], int z, int ty, int tx, bool xlo, bool xhi,
     bool ylo, bool yhi, bool zlo, bool zhi, float4& ctr, float& Gx, float& Gy,
     float& Gz, float& Qx, float& Qy, float& Qz) {
   ctr = win[z & 3][ty][tx];
@@ -182,8 +182,9 @@ __device__ __forceinline__ void window_gradients(
   }
 }
 
-// Per-thread geometry shared by both kernels.
-template <bool WALLS, int BY>
+// Per-thread geometry shared by the kernels: a CTA tile of TW x BY columns
+// (interior (TW - 2) x (BY - 2) plus the one-cell ring).
+template <bool WALLS, int BY, int TW = kTileW>
 struct Geometry {
   ColOff co;
   bool col_ok, interior, xlo, xhi, ylo, yhi;
@@ -192,7 +193,7 @@ struct Geometry {
   // tile (bx, by) of the lattice's 30 x (BY - 2) interior tiles
   __device__ __forceinline__ Geometry(const StepArgs& a, int tx, int ty, int bx,
                                       int by) {
-    const int x0 = bx * (kTileW - 2), y0 = by * (BY - 2);
+    const int x0 = bx * (TW - 2), y0 = by * (BY - 2);
     cx = x0 - 1 + tx;
     cy = y0 - 1 + ty;  // unwrapped
     col_ok = true;
@@ -211,7 +212,7 @@ struct Geometry {
     co.byl = WALLS && a.wy && gy == 0;
     co.byh = WALLS && a.wy && gy == a.ny - 1;
     plane_cells = (unsigned)a.nx * (unsigned)a.ny;
-    interior = tx >= 1 && tx <= kTileW - 2 && ty >= 1 && ty <= BY - 2 &&
+    interior = tx >= 1 && tx <= TW - 2 && ty >= 1 && ty <= BY - 2 &&
                cx < a.nx && cy < a.ny;
     xlo = WALLS && a.wx && cx == 0;
     xhi = WALLS && a.wx && cx == a.nx - 1;

@@ -1,0 +1,446 @@
+// TMA-pipelined fused step for sm_103a (included once per storage type).
+//
+// Same z-march as k_fused with the shared-memory hold (four-slot window of
+// (rho^N, Qbar), one barrier per plane), on a CTA tile of TW x BY threads,
+// interior (TW - 2) x (BY - 2) plus the one-cell ring: 32 x 8 (two CTAs per
+// SM), 16 x 16 (two CTAs per SM, two tile rows per warp) or 34 x 15 (one CTA
+// of 16 warps per SM; 32-wide interiors tile lattices whose nx is a multiple
+// of 32 without a ragged column of tiles, and the ring lanes are spread over
+// all warps), but the pulls of a plane do not come from per-thread global
+// loads.  One thread issues, per
+// plane and direction i, one tensor copy (cp.async.bulk.tensor, TMA) of the
+// box of source cells x - e_i of the tile's columns into a shared-memory
+// stage.  With NS = 2 stages the copies of plane z + 2 are in flight while
+// plane z + 1 is reduced and plane z collides; with NS = 1 the copies of
+// plane z + 1 are issued after plane z's barrier and land during its
+// collision.  Each thread reads its 19 pairs from shared memory at fixed
+// offsets (row ty, column tx + const) with no address arithmetic.
+//
+// Box geometry (pairs = red/blue values of one direction and cell):
+//   FP32 (8-byte pairs): directions with e_ix = +1 start at x0 - 2, with
+//     e_ix = -1 at x0, both TW pairs wide; e_ix = 0 starts at x0 - 2 and is
+//     TW + 2 pairs wide.  x0 = (TW - 2) bx is even, so every start is
+//     16-byte aligned.
+//   FP16 / BF16 (4-byte pairs): every box starts at (x0 - 2) rounded down to
+//     a multiple of 4 pairs and is TW + 4 pairs wide, rounded up to a
+//     multiple of 4.
+//   Rows y0 - 1 - e_iy ... (BY rows); plane z - e_iz, wrapped periodically
+//   in z.  Each box is padded to a multiple of 128 bytes in the stage.
+// A copy whose box reaches beyond the lattice in x or y fills zeros there
+// (TMA bounds handling); the cells whose sources lie beyond the lattice in x
+// or y -- the periodic wrap and bounce-back links, i.e. cells on the first
+// and last row and column -- pull from global memory as k_fused does, and so
+// do the first and last plane of a lattice with walls in z (they get no
+// copies).
+//
+// Waits on the stage mbarriers are bounded (kTmaWaitNs); a wait that
+// gives up sets *err, waits (bounded) for the CTA's copies still in flight
+// and leaves the CTA.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_fused.cuh"
+
+namespace lbm {
+
+// A stage's copies land within microseconds; a wait gives up after this.
+constexpr unsigned long long kTmaWaitNs = 20ull * 1000 * 1000;
+
+template <typename T>
+__host__ __device__ constexpr int tma_pair_bytes() {
+  return (int)sizeof(typename Store<T>::Pair);
+}
+// Box width of direction i, in pairs, for a tile TW threads wide (16-bit
+// boxes rounded up to whole 16-byte rows).
+template <typename T, int TW>
+__host__ __device__ constexpr int tma_width(int i) {
+  return tma_pair_bytes<T>() == 8 ? (ex(i) == 0 ? TW + 2 : TW) : (TW + 4 + 3) / 4 * 4;
+}
+// Bytes of direction i's box in a stage, padded to a multiple of 128 so
+// that every box starts 128-byte aligned.
+template <typename T, int TW, int BY>
+__host__ __device__ constexpr int tma_box_bytes(int i) {
+  return (tma_width<T, TW>(i) * BY * tma_pair_bytes<T>() + 127) / 128 * 128;
+}
+template <typename T, int TW, int BY>
+__host__ __device__ constexpr int tma_box_off(int i) {
+  int o = 0;
+  for (int j = 0; j < i; ++j) o += tma_box_bytes<T, TW, BY>(j);
+  return o;
+}
+template <typename T, int TW, int BY>
+__host__ __device__ constexpr int tma_stage_bytes() {
+  return tma_box_off<T, TW, BY>(19);
+}
+// Bytes the 19 copies of a plane deliver (the boxes without their padding):
+// the transaction count the stage's mbarrier expects.
+template <typename T, int TW, int BY>
+__host__ __device__ constexpr int tma_stage_tx_bytes() {
+  int b = 0;
+  for (int i = 0; i < 19; ++i) b += tma_width<T, TW>(i) * BY * tma_pair_bytes<T>();
+  return b;
+}
+// Which of the two tensor maps direction i uses (FP32: 0 = TW wide, 1 =
+// TW + 2 wide; 16-bit pairs: map 0 only).
+template <typename T>
+__host__ __device__ constexpr int tma_map(int i) {
+  return tma_pair_bytes<T>() == 8 && ex(i) == 0 ? 1 : 0;
+}
+
+constexpr int kTmaSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
+template <int TW, int BY>
+__host__ __device__ constexpr int tma_win_bytes() {
+  return 4 * BY * TW * 16;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int tma_hold_bytes(int vals) {
+  return vals * (BY - 2) * (TW - 2) * 4;
+}
+// Values a cell holds between its pull and its collision: f (19), rho_R,
+// rho_B and, where shared memory allows, u (recomputed from f otherwise).
+template <typename T, int TW, int BY, int NS>
+__host__ __device__ constexpr int tma_hold_vals() {
+  return NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
+                     tma_hold_bytes<TW, BY>(24) + 16 <=
+                 (TW * BY > 256 ? kTmaSmemLimit : 113 * 1024)
+             ? 24
+             : 21;
+}
+template <typename T, int TW, int BY, int NS>
+__host__ __device__ constexpr int tma_smem_bytes() {
+  return NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
+         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS>()) + 16;
+}
+// Resident CTAs per SM the configuration is laid out for.
+template <int TW, int BY>
+__host__ __device__ constexpr int tma_ctas_per_sm() {
+  return TW * BY > 256 ? 1 : 2;
+}
+template <typename T, int TW, int BY, int NS>
+__host__ __device__ constexpr bool tma_fits() {
+  return tma_smem_bytes<T, TW, BY, NS>() <=
+         (tma_ctas_per_sm<TW, BY>() == 1 ? kTmaSmemLimit : 113 * 1024);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned mbar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for a phase of a stage mbarrier (kTmaWaitNs of wall time).
+__device__ __forceinline__ bool tma_wait(unsigned mbar, unsigned parity) {
+  if (mbar_try(mbar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(mbar, parity))
+    if (global_ns() - t0 > kTmaWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            int z, int d, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(d),
+      "r"(mbar)
+      : "memory");
+}
+
+// Issues the 19 copies of one plane into a stage.
+template <typename T, int TW, int BY, int I>
+struct TmaIssue {
+  __device__ __forceinline__ static void run(unsigned stage, const CUtensorMap* m0,
+                                             const CUtensorMap* m1, int x0, int y0, int zz,
+                                             int nz, unsigned mbar) {
+    int x;
+    if constexpr (tma_pair_bytes<T>() == 8)
+      x = ex(I) < 0 ? x0 : x0 - 2;
+    else
+      x = (x0 - 2) & ~3;
+    tma_load_4d(stage + tma_box_off<T, TW, BY>(I), tma_map<T>(I) ? m1 : m0, x,
+                y0 - 1 - ey(I), wrap1(zz - ez(I), nz), I, mbar);
+    TmaIssue<T, TW, BY, I + 1>::run(stage, m0, m1, x0, y0, zz, nz, mbar);
+  }
+};
+template <typename T, int TW, int BY>
+struct TmaIssue<T, TW, BY, 19> {
+  __device__ __forceinline__ static void run(unsigned, const CUtensorMap*, const CUtensorMap*,
+                                             int, int, int, int, unsigned) {}
+};
+
+// Reads the 19 pairs of one cell from a stage, reduced on the fly to
+// (f_i = fR_i + fB_i, rho_R, rho_B).  col0 = tx (FP32) or tx + 1 + o (16-bit).
+template <typename T, int TW, int BY, int I>
+struct StageReduce {
+  __device__ __forceinline__ static void run(const unsigned char* stage, int ty, int col0,
+                                             const StepArgs& a, float* f, float& rR,
+                                             float& rB) {
+    using Pair = typename Store<T>::Pair;
+    int col;
+    if constexpr (tma_pair_bytes<T>() == 8)
+      col = col0 + (ex(I) == 0 ? 1 : 0);
+    else
+      col = col0 - ex(I);
+    const Pair* box = reinterpret_cast<const Pair*>(stage + tma_box_off<T, TW, BY>(I));
+    float2 v = Store<T>::to_float2(box[ty * tma_width<T, TW>(I) + col]);
+    add_offsets<T, I>(a, v);
+    rR += v.x;
+    rB += v.y;
+    f[I] = v.x + v.y;
+    StageReduce<T, TW, BY, I + 1>::run(stage, ty, col0, a, f, rR, rB);
+  }
+};
+template <typename T, int TW, int BY>
+struct StageReduce<T, TW, BY, 19> {
+  __device__ __forceinline__ static void run(const unsigned char*, int, int, const StepArgs&,
+                                             float*, float&, float&) {}
+};
+
+template <typename T, bool WALLS, int TW, int BY, int NS>
+__global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
+    k_fused_tma(const T* __restrict__ src, T* __restrict__ dst,
+                const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap map0,
+                const __grid_constant__ CUtensorMap map1, int zchunk, int* __restrict__ err) {
+  constexpr int SB = tma_stage_bytes<T, TW, BY>();
+  constexpr int TX = tma_stage_tx_bytes<T, TW, BY>();
+  constexpr int HV = tma_hold_vals<T, TW, BY, NS>();
+  using Pair = typename Store<T>::Pair;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stage0 = smem;
+  float4(*win)[BY][TW] = reinterpret_cast<float4(*)[BY][TW]>(smem + NS * SB);
+  float(*hold)[BY - 2][TW - 2] =
+      reinterpret_cast<float(*)[BY - 2][TW - 2]>(smem + NS * SB + tma_win_bytes<TW, BY>());
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(
+      smem + NS * SB + tma_win_bytes<TW, BY>() + tma_hold_bytes<TW, BY>(HV));
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TW + tx;
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, a.nz);
+  if (zb >= ze) return;
+  if (smem_addr(smem) & 127u) {  // the copies need 128-byte aligned boxes
+    if (tid == 0) atomicExch(err, 2);
+    return;
+  }
+  const Geometry<WALLS, BY, TW> g(a, tx, ty, blockIdx.x, blockIdx.y);
+  const unsigned plane = (unsigned)a.plane;
+  const Pair* srcp = reinterpret_cast<const Pair*>(src);
+  const int x0 = blockIdx.x * (TW - 2), y0 = blockIdx.y * (BY - 2);
+  // every source x - e_i, y - e_i of this column lies inside the lattice
+  const bool col_fast = g.cx >= 1 && g.cx <= a.nx - 2 && g.cy >= 1 && g.cy <= a.ny - 2;
+  int col0 = tx;
+  if constexpr (tma_pair_bytes<T>() != 8) col0 = tx + 1 + ((x0 - 2) - ((x0 - 2) & ~3));
+  const unsigned st_base = smem_addr(stage0), mb_base = smem_addr(mbar);
+  auto st_addr = [&](int k) { return st_base + (unsigned)((NS == 2 ? (k & 1) : 0) * SB); };
+  auto mb = [&](int k) { return mb_base + (unsigned)((NS == 2 ? (k & 1) : 0) * 8); };
+  // parity of the mbarrier phase that fill k completes
+  auto par = [&](int k) { return (unsigned)((NS == 2 ? (k >> 1) : k) & 1); };
+
+  // fill index k = plane zb - 1 + k; with walls in z the first and last
+  // plane are pulled from global memory (bounce-back links) and get no copies
+  const int K = ze - zb + 2;
+  auto staged = [&](int zl) {
+    if (!(WALLS && a.wz)) return true;
+    return zl >= 1 && zl <= a.nz - 2;
+  };
+  auto issue = [&](int k) {  // one thread
+    const int zl = zb - 1 + k;
+    const unsigned m = mb(k);
+    if (staged(zl)) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m),
+                   "r"(TX)
+                   : "memory");
+      TmaIssue<T, TW, BY, 0>::run(st_addr(k), &map0, &map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
+    } else {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(m) : "memory");
+    }
+  };
+  // Pulls plane zl: window slot and reduced state (f, rho_R, rho_B, u).
+  auto fill = [&](int k, float* f, float* hu) {
+    const int zl = zb - 1 + k;
+    if (!g.plane_ok(a, zl)) return;
+    float rR = 0.f, rB = 0.f;
+    if (col_fast && staged(zl))
+      StageReduce<T, TW, BY, 0>::run(stage0 + (NS == 2 ? (k & 1) : 0) * SB, ty, col0, a, f,
+                                     rR, rB);
+    else
+      PullReduce<T, WALLS, 0>::run(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f, rR,
+                                   rB);
+    const Macro m = macro_total(a, f, rR, rB);
+    hu[0] = rR;
+    hu[1] = rB;
+    hu[2] = m.ux;
+    hu[3] = m.uy;
+    hu[4] = m.uz;
+    win[zl & 3][ty][tx] = stencil_entry(a, m);
+  };
+  // after a failed wait: the copies of fills k .. k + NS - 1 may be in flight
+  auto drain = [&](int k) {
+    if (tid == 0) atomicExch(err, 1);
+    for (int j = k; j < k + NS && j < K; ++j) tma_wait(mb(j), par(j));
+  };
+
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb(q)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  float cf[19], ch[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if constexpr (NS == 2) {
+    if (tid == 0) {
+      issue(0);
+      issue(1);
+    }
+    float tf[19], th[5];
+    bool ok = tma_wait(mb(0), par(0));
+    if (ok) fill(0, tf, th);
+    ok = ok && tma_wait(mb(1), par(1));
+    if (ok) fill(1, cf, ch);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      drain(0);
+      return;
+    }
+    if (tid == 0) {
+      if (K > 2) issue(2);
+      if (K > 3) issue(3);
+    }
+  } else {
+    if (tid == 0) issue(0);
+    float tf[19], th[5];
+    bool ok = tma_wait(mb(0), par(0));
+    if (ok) fill(0, tf, th);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      drain(0);
+      return;
+    }
+    if (tid == 0) issue(1);
+    ok = tma_wait(mb(1), par(1));
+    if (ok) fill(1, cf, ch);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      drain(1);
+      return;
+    }
+    if (tid == 0 && K > 2) issue(2);
+  }
+  for (int k = 2; k < K; ++k) {
+    const int z = zb + k - 2;  // plane that collides; plane z + 1 is filled
+    float nf[19], nh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool got = tma_wait(mb(k), par(k));
+    if (got) {
+      fill(k, nf, nh);
+      if (g.interior) {  // private slot of this thread
+#pragma unroll
+        for (int i = 0; i < 19; ++i) hold[i][ty - 1][tx - 1] = nf[i];
+#pragma unroll
+        for (int i = 0; i < HV - 19; ++i) hold[19 + i][ty - 1][tx - 1] = nh[i];
+      }
+    }
+    if (!__syncthreads_and(got ? 1 : 0)) {
+      drain(k);
+      return;
+    }
+    // the stage of fill k is consumed by every thread: refill it
+    if (tid == 0 && k + NS < K) issue(k + NS);
+    if (g.interior) {
+      const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
+      float4 ctr;
+      float Gx, Gy, Gz, Qx, Qy, Qz;
+      window_gradients<BY, TW>(win, z, ty, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, ctr, Gx,
+                               Gy, Gz, Qx, Qy, Qz);
+      if (WALLS && a.wetting)
+        wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
+      const Macro m = HV == 24 ? macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4])
+                               : macro_total(a, cf, ch[0], ch[1]);
+      const Recolour rc = collide_total(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+      store_recoloured<T>(dst, plane, a, (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1],
+                          rc, cf);
+#pragma unroll
+      for (int i = 0; i < 19; ++i) cf[i] = hold[i][ty - 1][tx - 1];
+#pragma unroll
+      for (int i = 0; i < HV - 19; ++i) ch[i] = hold[19 + i][ty - 1][tx - 1];
+    }
+  }
+}
+
+// Tensor maps are built on the host (lbm_dispatch.cu); the launcher only
+// sets the dynamic shared-memory limit once per instantiation.
+template <typename T, bool WALLS, int TW, int BY, int NS>
+static cudaError_t launch_tma_v(const void* src, void* dst, const StepArgs& a,
+                                const CUtensorMap* maps, int zc, int* err, cudaStream_t s) {
+  if constexpr (!tma_fits<T, TW, BY, NS>()) {
+    return cudaErrorInvalidValue;
+  } else {
+    static bool attr_set = false;
+    constexpr int bytes = tma_smem_bytes<T, TW, BY, NS>();
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_fused_tma<T, WALLS, TW, BY, NS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    dim3 blk(TW, BY);
+    dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
+    k_fused_tma<T, WALLS, TW, BY, NS><<<grd, blk, bytes, s>>>((const T*)src, (T*)dst, a, maps[0],
+                                                             maps[1], zc, err);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, bool WALLS>
+static cudaError_t launch_tma_w(const void* src, void* dst, const StepArgs& a,
+                                const CUtensorMap* maps, int kind, int ns, int zc, int* err,
+                                cudaStream_t s) {
+  switch (kind * 2 + (ns - 1)) {
+    case 0: return launch_tma_v<T, WALLS, 32, 8, 1>(src, dst, a, maps, zc, err, s);
+    case 1: return launch_tma_v<T, WALLS, 32, 8, 2>(src, dst, a, maps, zc, err, s);
+    case 2: return launch_tma_v<T, WALLS, 16, 16, 1>(src, dst, a, maps, zc, err, s);
+    case 3: return launch_tma_v<T, WALLS, 16, 16, 2>(src, dst, a, maps, zc, err, s);
+    case 4: return launch_tma_v<T, WALLS, 34, 15, 1>(src, dst, a, maps, zc, err, s);
+    case 5: return launch_tma_v<T, WALLS, 34, 15, 2>(src, dst, a, maps, zc, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// kind: tile 0 = 32 x 8, 1 = 16 x 16, 2 = 34 x 15 threads; ns: stages (1, 2);
+// maps: the two tensor maps of the source buffer for that tile.
+template <typename T>
+cudaError_t launch_fused_tma_storage(const void* src, void* dst, const StepArgs& a,
+                                     const CUtensorMap* maps, int kind, int ns, int zchunk,
+                                     int* err, cudaStream_t s) {
+  const int zc = zchunk > 0 ? zchunk : a.nz;
+  const bool walls = a.wx || a.wy || a.wz;
+  return walls ? launch_tma_w<T, true>(src, dst, a, maps, kind, ns, zc, err, s)
+               : launch_tma_w<T, false>(src, dst, a, maps, kind, ns, zc, err, s);
+}
+
+// Whether (kind, ns) fits the shared memory for the storage type.
+template <typename T>
+bool tma_config_fits_storage(int kind, int ns) {
+  switch (kind * 2 + (ns - 1)) {
+    case 0: return tma_fits<T, 32, 8, 1>();
+    case 1: return tma_fits<T, 32, 8, 2>();
+    case 2: return tma_fits<T, 16, 16, 1>();
+    case 3: return tma_fits<T, 16, 16, 2>();
+    case 4: return tma_fits<T, 34, 15, 1>();
+    case 5: return tma_fits<T, 34, 15, 2>();
+  }
+  return false;
+}
+
+}  // namespace lbm

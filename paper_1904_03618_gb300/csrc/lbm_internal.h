@@ -2,6 +2,7 @@
 // translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -38,14 +39,17 @@ cudaError_t launch_twopass(int storage, const void* src, void* dst,
 
 // Fused z-marching step.
 struct FusedConfig {
-  int tile_y;  // CTA rows including the ring: 8 or 16 (interior 30 x (tile_y - 2))
+  int tile_y;  // CTA rows including the ring: 8 or 16 (interior 30 x (tile_y - 2));
+               // 16 with hold 7 / 8 is the 16 x 16 thread tile, 15 (hold 7 / 8
+               // only) the 34 x 15 tile
   int zchunk;  // planes marched per CTA (> 0)
   int hold;    // where plane z waits between its two uses: 0 re-pulled from
                // L1/L2, 1 registers, 2 shared memory (tile_y = 8 only),
                // 3 shared memory with cp.async prefetch of plane z + 2
                // (tile_y = 8), 4 shared memory with two tile rows per
                // thread (tile_y = 16), 5 / 6 as 2 with registers capped
-               // for 3 / 4 CTAs per SM
+               // for 3 / 4 CTAs per SM, 7 / 8 shared memory with the
+               // pulls staged by tensor copies (TMA) in two / one stages
 };
 template <typename T>
 cudaError_t launch_fused_storage(const void* src, void* dst, const StepArgs& a,
@@ -54,6 +58,29 @@ cudaError_t launch_fused(int storage, const void* src, void* dst,
                          const StepArgs& a, const FusedConfig& cfg,
                          cudaStream_t s);
 FusedConfig default_fused_config(const StepArgs& a, int storage);
+
+// TMA-staged fused step (hold 7: two stages, hold 8: one stage).  Tile
+// kinds: 0 = 32 x 8 threads (tile_y 8), 1 = 16 x 16 (tile_y 16), 2 = 34 x 15
+// (tile_y 15).  Needs an x row of 16-byte multiple length (nx even for
+// FP32, nx a multiple of 4 for 16-bit storage); maps[2] are the two tensor
+// maps of the source buffer for the tile (tma_build_maps).
+bool tma_eligible(const StepArgs& a, int storage);
+int tma_kind(int tile_y);  // -1 for a tile_y without a TMA form
+cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
+                           CUtensorMap maps[2]);
+bool tma_config_fits(int storage, int kind, int ns);
+// Default TMA configuration for a single lattice (false: keep the plain one).
+bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind_ok[3],
+                        FusedConfig* out);
+template <typename T>
+bool tma_config_fits_storage(int kind, int ns);
+template <typename T>
+cudaError_t launch_fused_tma_storage(const void* src, void* dst, const StepArgs& a,
+                                     const CUtensorMap* maps, int kind, int ns, int zchunk,
+                                     int* err, cudaStream_t s);
+cudaError_t launch_fused_tma(int storage, const void* src, void* dst, const StepArgs& a,
+                             const CUtensorMap* maps, int kind, int ns, int zchunk, int* err,
+                             cudaStream_t s);
 
 // One case of a batch, as the batched kernel sees it.
 struct BatchCase {

@@ -34,7 +34,7 @@ constexpr int kM = 128;     // rows per CTA (UMMA M)
 constexpr int kKT = 64;     // K per shared-memory slice
 constexpr int kNMax = 256;  // UMMA N limit for M = 128
 constexpr int kThreads = 128;
-constexpr long long kSpinLimit = 1LL << 26;  // bounded mbarrier wait
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;  // bounded mbarrier wait
 
 struct GemmArgs {
   const float* A;
@@ -88,19 +88,27 @@ __device__ __forceinline__ unsigned instr_desc(int n) {
          ((unsigned)(kM >> 4) << 24);
 }
 
+__device__ __forceinline__ bool mbar_poll(unsigned addr, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait (kWaitNs of wall time on the global timer).
 __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned phase) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(phase)
-        : "memory");
-    if (done) return true;
+  if (mbar_poll(addr, phase)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (!mbar_poll(addr, phase)) {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kWaitNs) return false;
   }
-  return false;
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {

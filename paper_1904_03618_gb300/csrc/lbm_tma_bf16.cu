@@ -1,0 +1,10 @@
+// TMA-staged fused step kernels for __nv_bfloat16 population storage (a translation
+// unit of its own so that they compile in parallel with the other kernels).
+#include "lbm_fused_tma.cuh"
+
+namespace lbm {
+template cudaError_t launch_fused_tma_storage<__nv_bfloat16>(const void*, void*, const StepArgs&,
+                                                   const CUtensorMap*, int, int, int,
+                                                   int*, cudaStream_t);
+template bool tma_config_fits_storage<__nv_bfloat16>(int, int);
+}  // namespace lbm

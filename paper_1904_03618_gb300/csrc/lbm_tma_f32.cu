@@ -1,0 +1,10 @@
+// TMA-staged fused step kernels for float population storage (a translation
+// unit of its own so that they compile in parallel with the other kernels).
+#include "lbm_fused_tma.cuh"
+
+namespace lbm {
+template cudaError_t launch_fused_tma_storage<float>(const void*, void*, const StepArgs&,
+                                                   const CUtensorMap*, int, int, int,
+                                                   int*, cudaStream_t);
+template bool tma_config_fits_storage<float>(int, int);
+}  // namespace lbm
