@@ -45,19 +45,20 @@ __device__ __forceinline__ void add_offsets(const StepArgs& a, float2& v) {
 }
 
 // Pull of the 19 pairs of one column / plane, reduced on the fly to
-// (f_i = fR_i + fB_i, rho_R, rho_B).
+// (f_i = fR_i + fB_i, rho_R, rho_B).  The colour sums run as one paired
+// FP32 add per direction (the red and blue values arrive as a pair; each
+// component rounds as its scalar add would).
 template <typename T, bool WALLS, int I>
 struct PullReduce {
   __device__ __forceinline__ static void run(const typename Store<T>::Pair* src,
                                              unsigned plane, const StepArgs& a,
                                              const ColOff& c, const PlaneOff& p,
-                                             float* f, float& rR, float& rB) {
+                                             float* f, float2& rho) {
     float2 v = Store<T>::to_float2(__ldg(src + pull_index<WALLS, I>(plane, c, p)));
     add_offsets<T, I>(a, v);
-    rR += v.x;
-    rB += v.y;
+    rho = __fadd2_rn(rho, v);
     f[I] = v.x + v.y;
-    PullReduce<T, WALLS, I + 1>::run(src, plane, a, c, p, f, rR, rB);
+    PullReduce<T, WALLS, I + 1>::run(src, plane, a, c, p, f, rho);
   }
 };
 template <typename T, bool WALLS>
@@ -65,8 +66,18 @@ struct PullReduce<T, WALLS, 19> {
   __device__ __forceinline__ static void run(const typename Store<T>::Pair*,
                                              unsigned, const StepArgs&,
                                              const ColOff&, const PlaneOff&,
-                                             float*, float&, float&) {}
+                                             float*, float2&) {}
 };
+template <typename T, bool WALLS>
+__device__ __forceinline__ void pull_reduce(const typename Store<T>::Pair* src, unsigned plane,
+                                            const StepArgs& a, const ColOff& c,
+                                            const PlaneOff& p, float* f, float& rR,
+                                            float& rB) {
+  float2 rho = make_float2(rR, rB);
+  PullReduce<T, WALLS, 0>::run(src, plane, a, c, p, f, rho);
+  rR = rho.x;
+  rB = rho.y;
+}
 
 // cp.async of one pair (8 bytes for FP32, 4 bytes for FP16/BF16), global ->
 // shared, L1-allocating form.
@@ -263,7 +274,7 @@ __device__ __forceinline__ void fused_work(const T* __restrict__ src,
   auto fill = [&](int zl, float* f, float* hu) {
     if (!g.plane_ok(a, zl)) return;
     float rR = 0.f, rB = 0.f;
-    PullReduce<T, WALLS, 0>::run(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)),
+    pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)),
                                  f, rR, rB);
     const Macro m = macro_total(a, f, rR, rB);
     hu[0] = rR;
@@ -304,7 +315,7 @@ __device__ __forceinline__ void fused_work(const T* __restrict__ src,
       Macro m;
       if constexpr (HOLD == 0) {
         float rR = 0.f, rB = 0.f;
-        PullReduce<T, WALLS, 0>::run(srcp, plane, a, g.co, g.plane(a, z), cf, rR, rB);
+        pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, z), cf, rR, rB);
         m = macro_total(a, cf, rR, rB);
       } else {
         m = macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4]);
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(kTileW * 8, 2)
   auto fill = [&](const Geometry<WALLS, kRows2>& g, int row, int zl) {
     if (!g.plane_ok(a, zl)) return;
     float f[19], rR = 0.f, rB = 0.f;
-    PullReduce<T, WALLS, 0>::run(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f,
+    pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f,
                                  rR, rB);
     const Macro m = macro_total(a, f, rR, rB);
     sm.win[zl & 3][row][tx] = stencil_entry(a, m);

@@ -189,8 +189,7 @@ struct TmaIssue<T, TW, BY, 19> {
 template <typename T, int TW, int BY, int I>
 struct StageReduce {
   __device__ __forceinline__ static void run(const unsigned char* stage, int ty, int col0,
-                                             const StepArgs& a, float* f, float& rR,
-                                             float& rB) {
+                                             const StepArgs& a, float* f, float2& rho) {
     using Pair = typename Store<T>::Pair;
     int col;
     if constexpr (tma_pair_bytes<T>() == 8)
@@ -200,16 +199,15 @@ struct StageReduce {
     const Pair* box = reinterpret_cast<const Pair*>(stage + tma_box_off<T, TW, BY>(I));
     float2 v = Store<T>::to_float2(box[ty * tma_width<T, TW>(I) + col]);
     add_offsets<T, I>(a, v);
-    rR += v.x;
-    rB += v.y;
+    rho = __fadd2_rn(rho, v);  // (rho_R, rho_B) as one paired add
     f[I] = v.x + v.y;
-    StageReduce<T, TW, BY, I + 1>::run(stage, ty, col0, a, f, rR, rB);
+    StageReduce<T, TW, BY, I + 1>::run(stage, ty, col0, a, f, rho);
   }
 };
 template <typename T, int TW, int BY>
 struct StageReduce<T, TW, BY, 19> {
   __device__ __forceinline__ static void run(const unsigned char*, int, int, const StepArgs&,
-                                             float*, float&, float&) {}
+                                             float*, float2&) {}
 };
 
 template <typename T, bool WALLS, int TW, int BY, int NS>
@@ -275,12 +273,15 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     const int zl = zb - 1 + k;
     if (!g.plane_ok(a, zl)) return;
     float rR = 0.f, rB = 0.f;
-    if (col_fast && staged(zl))
+    if (col_fast && staged(zl)) {
+      float2 rho = make_float2(0.f, 0.f);
       StageReduce<T, TW, BY, 0>::run(stage0 + (NS == 2 ? (k & 1) : 0) * SB, ty, col0, a, f,
-                                     rR, rB);
-    else
-      PullReduce<T, WALLS, 0>::run(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f, rR,
-                                   rB);
+                                     rho);
+      rR = rho.x;
+      rB = rho.y;
+    } else {
+      pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f, rR, rB);
+    }
     const Macro m = macro_total(a, f, rR, rB);
     hu[0] = rR;
     hu[1] = rB;
