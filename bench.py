@@ -137,7 +137,7 @@ def profiled_traffic(kernel, storage, n):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("lbm_fused.cuh", "lbm_device.cuh"):
+    for f in ("lbm_fused.cuh", "lbm_fused_tma.cuh", "lbm_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
     key = "%s_%s" % (kernel, storage)
     if vals.get("source_sha256") != h.hexdigest()[:16] or key + "_bytes_per_cell" not in vals:
