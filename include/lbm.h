@@ -171,7 +171,10 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
 
 /* Launch configuration of the fused kernel (LBM_KERNEL_FUSED), the knob the
    autotuner turns; results are identical for every valid configuration.
-   Batch contexts accept (tile_y, hold) = (8, 2), (8, 0) or (16, 1).
+   Batch contexts accept (tile_y, hold) = (8, 2), (8, 0), (16, 1) and, when
+   every case has an x row of 16-byte multiple length, the TMA forms (8 or
+   15, 7 or 8); their default is then (15, 32, 8) for FP32 and (15, 32, 7)
+   for 16-bit storage.
    tile_y: CTA rows including the one-cell ring, 8 or 16 (the interior tile
    is 30 x (tile_y - 2) cells), or 15 (below).  zchunk: planes marched per CTA, 0 = the
    library's default for this lattice.  hold: where the populations of a
@@ -202,8 +205,10 @@ int lbm_launches_per_step(const lbm_ctx *ctx);
    lbm_params (size, walls, densities, alpha, relaxation times, surface
    tension, beta, forces); all cases share storage (p->storage) and run the
    fused kernel.  lbm_step advances every case by n steps with one kernel
-   launch per step: persistent CTAs take (case, tile, z-chunk) work items in
-   turn, so cases of uneven sizes share the GPU without idle tails.  Cases
+   launch per step: persistent CTAs take (case, z-chunk, tile) work items in
+   turn, so cases of uneven sizes share the GPU without idle tails; in the
+   TMA forms each case's pulls are staged by tensor copies described by
+   per-case tensor maps held in device memory.  Cases
    must be initialised (lbm_batch_init_fields or lbm_batch_set_f) before
    lbm_step.  The single-lattice calls (lbm_init_fields, lbm_moments,
    lbm_diagnostics, lbm_get_f, lbm_set_f) act on case 0 of a batch. */

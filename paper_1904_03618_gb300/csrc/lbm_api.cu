@@ -46,6 +46,8 @@ struct lbm_ctx {
   int* d_flags;             // device error word of the kernels' bounded waits
   bool tma_ok[3];           // tensor maps built, per tile kind (single lattice)
   CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
+  CUtensorMap* d_bmaps[2][3];  // batches: [buffer][tile kind] -> device table, 2 per case
+  bool batch_tma_ok[3];        // batch tables built, per tile kind
   int total_items;
   cudaGraphExec_t graph;    // two captured steps (buffer 0 -> 1 -> 0)
   int use_graph;
@@ -212,6 +214,8 @@ static void release(lbm_ctx* c) {
   cudaFree(c->d_cases);
   cudaFree(c->foot);
   cudaFree(c->d_flags);
+  for (int b = 0; b < 2; ++b)
+    for (int w = 0; w < 3; ++w) cudaFree(c->d_bmaps[b][w]);
   delete[] c->cases;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -234,7 +238,8 @@ static lbm_status upload_case_table(lbm_ctx* c) {
     h[k].args = r.args;
     h[k].pair_base = r.pair_base;
     h[k].item_start = (int)items;
-    h[k].tiles_x = (r.p.nx + 29) / 30;
+    const int iw = lbm::tile_interior_x(ty);
+    h[k].tiles_x = (r.p.nx + iw - 1) / iw;
     h[k].tiles_y = (r.p.ny + ty - 3) / (ty - 2);
     h[k].pad_ = 0;
     items += (long long)h[k].tiles_x * h[k].tiles_y * ((r.p.nz + zc - 1) / zc);
@@ -345,6 +350,38 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
     lbm::FusedConfig t;
     if (lbm::tma_default_config(c->cases[0].args, c->storage, c->sms, c->tma_ok, &t))
       c->fused = t;
+  }
+  if (st == LBM_OK && ncases > 1) {
+    // tensor maps of every case for the batched TMA step (tile kinds 0, 2)
+    bool all = true;
+    for (int k = 0; k < ncases && all; ++k)
+      all = lbm::tma_eligible(c->cases[k].args, c->storage);
+    CUtensorMap* hm = all ? new (std::nothrow) CUtensorMap[2 * (size_t)ncases] : nullptr;
+    for (int w : {0, 2}) {
+      bool ok = hm != nullptr;
+      for (int b = 0; b < 2 && ok; ++b) {
+        for (int k = 0; k < ncases && ok; ++k)
+          ok = lbm::tma_build_maps(c->storage,
+                                   (char*)c->pop[b] + (size_t)c->cases[k].pair_base * 2 * c->elem,
+                                   c->cases[k].args, w, hm + 2 * k) == cudaSuccess;
+        ok = ok && cudaMalloc(&c->d_bmaps[b][w], sizeof(CUtensorMap) * 2 * ncases) == cudaSuccess &&
+             cudaMemcpy(c->d_bmaps[b][w], hm, sizeof(CUtensorMap) * 2 * ncases,
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+      }
+      c->batch_tma_ok[w] = ok;
+    }
+    delete[] hm;
+    cudaGetLastError();
+    // Batch default: the TMA form of the 34 x 15 tile, 32-plane chunks, one
+    // stage for FP32 and two for 16-bit storage (GB300, 512-case droplet
+    // sweep: 11.4 and 14.6 GLUPS against 10.0 and 12.5 for the 32 x 8
+    // shared-memory hold).
+    const int ns = c->storage == LBM_F32 ? 1 : 2;
+    if (c->batch_tma_ok[2] && lbm::tma_config_fits(c->storage, 2, ns)) {
+      c->fused.tile_y = 15;
+      c->fused.zchunk = 32;
+      c->fused.hold = ns == 2 ? 7 : 8;
+    }
   }
   if (st == LBM_OK && ncases > 1 &&
       cudaMalloc(&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
@@ -468,7 +505,15 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
   const void* src = c->pop[from];
   void* dst = c->pop[from ^ 1];
   cudaError_t e;
-  if (c->ncases > 1)
+  if (c->ncases > 1 && (c->fused.hold == 7 || c->fused.hold == 8)) {
+    const int w = lbm::tma_kind(c->fused.tile_y);
+    e = (w == 0 || w == 2) && c->batch_tma_ok[w]
+            ? lbm::launch_fused_tma_batch(c->storage, src, dst, c->d_cases, c->ncases,
+                                          c->total_items, c->any_walls, c->d_bmaps[from][w], w,
+                                          c->fused.hold == 7 ? 2 : 1, c->fused.zchunk,
+                                          c->d_flags, c->sms, c->stream)
+            : cudaErrorInvalidValue;
+  } else if (c->ncases > 1)
     e = lbm::launch_fused_batch(c->storage, src, dst, c->d_cases, c->ncases,
                                 c->total_items, c->any_walls, c->fused, c->sms,
                                 c->stream);
@@ -752,16 +797,23 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
   f.zchunk = zchunk == 0
                  ? (c->ncases > 1 ? 12 : lbm::default_fused_config(c->cases[0].args, c->storage).zchunk)
                  : zchunk;
-  const bool ok = zchunk >= 0 && (c->ncases > 1 ? lbm::valid_batch_config(f)
-                                                : lbm::valid_fused_config(f, c->storage)) &&
-                  ((f.hold != 7 && f.hold != 8) ||
-                   (lbm::tma_kind(f.tile_y) >= 0 && c->tma_ok[lbm::tma_kind(f.tile_y)] &&
-                    lbm::tma_config_fits(c->storage, lbm::tma_kind(f.tile_y),
-                                         f.hold == 7 ? 2 : 1)));
+  const bool batch_tma =
+      (hold == 7 || hold == 8) && (tile_y == 8 || tile_y == 15) &&
+      c->batch_tma_ok[lbm::tma_kind(tile_y)] &&
+      lbm::tma_config_fits(c->storage, lbm::tma_kind(tile_y), hold == 7 ? 2 : 1);
+  const bool single_tma =
+      lbm::tma_kind(f.tile_y) >= 0 && c->tma_ok[lbm::tma_kind(f.tile_y)] &&
+      lbm::tma_config_fits(c->storage, lbm::tma_kind(f.tile_y), f.hold == 7 ? 2 : 1);
+  const bool ok =
+      zchunk >= 0 &&
+      (c->ncases > 1
+           ? lbm::valid_batch_config(f) && ((hold != 7 && hold != 8) || batch_tma)
+           : lbm::valid_fused_config(f, c->storage) && ((hold != 7 && hold != 8) || single_tma));
   if (!ok)
     return fail(c, LBM_ERR_ARG,
                 c->ncases > 1
-                    ? "invalid batch configuration ((tile_y, hold) = (8, 2), (8, 0) or (16, 1), zchunk >= 0)"
+                    ? "invalid batch configuration ((tile_y, hold) = (8, 2), (8, 0), (16, 1), "
+                      "or (8 or 15, 7 or 8) where every case has tensor maps; zchunk >= 0)"
                     : "invalid fused configuration (tile_y 8, 15 or 16, zchunk >= 0, hold "
                       "0..8; hold 2, 3, 5, 6 need tile_y 8, hold 4 needs tile_y 16, tile_y 15 "
                       "needs hold 7 or 8; hold 7 and 8 need nx * pair bytes a multiple of 16 "

@@ -39,6 +39,26 @@ cudaError_t launch_fused_tma(int storage, const void* src, void* dst, const Step
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fused_tma_batch(int storage, const void* src, void* dst,
+                                   const BatchCase* cases, int ncases, int total_items,
+                                   bool walls, const CUtensorMap* maps, int kind, int ns, int zc,
+                                   int* err, int sms, cudaStream_t s) {
+  if (kind != 0 && kind != 2) return cudaErrorInvalidValue;
+  switch (storage) {
+    case 0:
+      return launch_fused_tma_batch_storage<float>(src, dst, cases, ncases, total_items, walls,
+                                                   maps, kind, ns, zc, err, sms, s);
+    case 1:
+      return launch_fused_tma_batch_storage<__half>(src, dst, cases, ncases, total_items, walls,
+                                                    maps, kind, ns, zc, err, sms, s);
+    case 2:
+      return launch_fused_tma_batch_storage<__nv_bfloat16>(src, dst, cases, ncases, total_items,
+                                                           walls, maps, kind, ns, zc, err, sms,
+                                                           s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 int tma_kind(int tile_y) { return tile_y == 8 ? 0 : (tile_y == 16 ? 1 : (tile_y == 15 ? 2 : -1)); }
 
 static const int kTmaTW[3] = {32, 16, 34}, kTmaBY[3] = {8, 16, 15};
@@ -152,10 +172,12 @@ cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int
   return cudaSuccess;
 }
 
-// Batched kernel variants: (tile_y, hold) = (8, 2), (8, 0), (16, 1).
+// Batched kernel variants: (tile_y, hold) = (8, 2), (8, 0), (16, 1), and
+// the TMA forms (8 or 15, 7 or 8) where the context built tensor maps.
 bool valid_batch_config(const FusedConfig& c) {
   const bool shape = (c.tile_y == 8 && (c.hold == 2 || c.hold == 0)) ||
-                     (c.tile_y == 16 && c.hold == 1);
+                     (c.tile_y == 16 && c.hold == 1) ||
+                     ((c.tile_y == 8 || c.tile_y == 15) && (c.hold == 7 || c.hold == 8));
   return shape && c.zchunk > 0;
 }
 

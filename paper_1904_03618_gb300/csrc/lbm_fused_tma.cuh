@@ -210,16 +210,22 @@ struct StageReduce<T, TW, BY, 19> {
                                              float*, float2&) {}
 };
 
+// One work item of the TMA-staged step: tile (bx, by) of the lattice `a`,
+// planes [zb, ze).  The CTA's stage mbarriers are initialised; G0 counts
+// the fills of the CTA's earlier items (their stage use), so that the
+// stages and mbarrier phases continue across items.  map0 / map1: the
+// source buffer's tensor maps (param or global space).  Returns false after
+// a wait gave up (*err set, the CTA's copies drained).
 template <typename T, bool WALLS, int TW, int BY, int NS>
-__global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
-    k_fused_tma(const T* __restrict__ src, T* __restrict__ dst,
-                const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap map0,
-                const __grid_constant__ CUtensorMap map1, int zchunk, int* __restrict__ err) {
+__device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restrict__ dst,
+                                          const StepArgs& a, const CUtensorMap* map0,
+                                          const CUtensorMap* map1, int bx, int by, int zb,
+                                          int ze, unsigned char* smem, unsigned G0,
+                                          int* __restrict__ err) {
   constexpr int SB = tma_stage_bytes<T, TW, BY>();
   constexpr int TX = tma_stage_tx_bytes<T, TW, BY>();
   constexpr int HV = tma_hold_vals<T, TW, BY, NS>();
   using Pair = typename Store<T>::Pair;
-  extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage0 = smem;
   float4(*win)[BY][TW] = reinterpret_cast<float4(*)[BY][TW]>(smem + NS * SB);
   float(*hold)[BY - 2][TW - 2] =
@@ -228,26 +234,24 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
       smem + NS * SB + tma_win_bytes<TW, BY>() + tma_hold_bytes<TW, BY>(HV));
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TW + tx;
-  const int zb = blockIdx.z * zchunk;
-  const int ze = min(zb + zchunk, a.nz);
-  if (zb >= ze) return;
-  if (smem_addr(smem) & 127u) {  // the copies need 128-byte aligned boxes
-    if (tid == 0) atomicExch(err, 2);
-    return;
-  }
-  const Geometry<WALLS, BY, TW> g(a, tx, ty, blockIdx.x, blockIdx.y);
+  const Geometry<WALLS, BY, TW> g(a, tx, ty, bx, by);
   const unsigned plane = (unsigned)a.plane;
   const Pair* srcp = reinterpret_cast<const Pair*>(src);
-  const int x0 = blockIdx.x * (TW - 2), y0 = blockIdx.y * (BY - 2);
+  const int x0 = bx * (TW - 2), y0 = by * (BY - 2);
   // every source x - e_i, y - e_i of this column lies inside the lattice
   const bool col_fast = g.cx >= 1 && g.cx <= a.nx - 2 && g.cy >= 1 && g.cy <= a.ny - 2;
   int col0 = tx;
   if constexpr (tma_pair_bytes<T>() != 8) col0 = tx + 1 + ((x0 - 2) - ((x0 - 2) & ~3));
   const unsigned st_base = smem_addr(stage0), mb_base = smem_addr(mbar);
-  auto st_addr = [&](int k) { return st_base + (unsigned)((NS == 2 ? (k & 1) : 0) * SB); };
-  auto mb = [&](int k) { return mb_base + (unsigned)((NS == 2 ? (k & 1) : 0) * 8); };
-  // parity of the mbarrier phase that fill k completes
-  auto par = [&](int k) { return (unsigned)((NS == 2 ? (k >> 1) : k) & 1); };
+  // fill k of this item is the CTA's fill G0 + k: its stage and the parity
+  // of the mbarrier phase it completes
+  auto stage_of = [&](int k) { return NS == 2 ? (int)((G0 + (unsigned)k) & 1u) : 0; };
+  auto st_addr = [&](int k) { return st_base + (unsigned)(stage_of(k) * SB); };
+  auto mb = [&](int k) { return mb_base + 8u * (unsigned)stage_of(k); };
+  auto par = [&](int k) {
+    const unsigned n = G0 + (unsigned)k;
+    return (NS == 2 ? n >> 1 : n) & 1u;
+  };
 
   // fill index k = plane zb - 1 + k; with walls in z the first and last
   // plane are pulled from global memory (bounce-back links) and get no copies
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m),
                    "r"(TX)
                    : "memory");
-      TmaIssue<T, TW, BY, 0>::run(st_addr(k), &map0, &map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
+      TmaIssue<T, TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
     } else {
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(m) : "memory");
     }
@@ -275,8 +279,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     float rR = 0.f, rB = 0.f;
     if (col_fast && staged(zl)) {
       float2 rho = make_float2(0.f, 0.f);
-      StageReduce<T, TW, BY, 0>::run(stage0 + (NS == 2 ? (k & 1) : 0) * SB, ty, col0, a, f,
-                                     rho);
+      StageReduce<T, TW, BY, 0>::run(stage0 + stage_of(k) * SB, ty, col0, a, f, rho);
       rR = rho.x;
       rB = rho.y;
     } else {
@@ -296,12 +299,6 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     for (int j = k; j < k + NS && j < K; ++j) tma_wait(mb(j), par(j));
   };
 
-  if (tid == 0) {
-    for (int q = 0; q < NS; ++q)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb(q)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  __syncthreads();
   float cf[19], ch[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if constexpr (NS == 2) {
     if (tid == 0) {
@@ -315,7 +312,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     if (ok) fill(1, cf, ch);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(0);
-      return;
+      return false;
     }
     if (tid == 0) {
       if (K > 2) issue(2);
@@ -328,14 +325,14 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     if (ok) fill(0, tf, th);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(0);
-      return;
+      return false;
     }
     if (tid == 0) issue(1);
     ok = tma_wait(mb(1), par(1));
     if (ok) fill(1, cf, ch);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(1);
-      return;
+      return false;
     }
     if (tid == 0 && K > 2) issue(2);
   }
@@ -354,7 +351,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     }
     if (!__syncthreads_and(got ? 1 : 0)) {
       drain(k);
-      return;
+      return false;
     }
     // the stage of fill k is consumed by every thread: refill it
     if (tid == 0 && k + NS < K) issue(k + NS);
@@ -376,6 +373,94 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
 #pragma unroll
       for (int i = 0; i < HV - 19; ++i) ch[i] = hold[19 + i][ty - 1][tx - 1];
     }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_init_barriers(unsigned char* mbar_bytes, int ns) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int q = 0; q < ns; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mbar_bytes + 8 * q))
+                   : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+}
+
+template <typename T, int TW, int BY, int NS>
+__device__ __forceinline__ unsigned char* tma_mbar_bytes(unsigned char* smem) {
+  return smem + NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
+         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS>());
+}
+
+template <typename T, bool WALLS, int TW, int BY, int NS>
+__global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
+    k_fused_tma(const T* __restrict__ src, T* __restrict__ dst,
+                const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap map0,
+                const __grid_constant__ CUtensorMap map1, int zchunk, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, a.nz);
+  if (zb >= ze) return;
+  if (smem_addr(smem) & 127u) {  // the copies need 128-byte aligned boxes
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
+    return;
+  }
+  tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS>(smem), NS);
+  __syncthreads();
+  tma_chunk<T, WALLS, TW, BY, NS>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y, zb, ze,
+                                  smem, 0u, err);
+}
+
+// Batched TMA step: persistent CTAs take the work items (case, z chunk,
+// tile row, tile column) -- tile column fastest, so that CTAs running at
+// the same time march neighbouring tiles of one chunk and share their halo
+// lines in L2.  Per item the case's StepArgs are copied to shared memory;
+// its tensor maps come from a device table (two per case for the source
+// buffer), made visible to the tensor-map proxy before use.
+template <typename T, bool WALLS, int TW, int BY, int NS>
+__global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
+    k_fused_tma_batch(const BatchCase* __restrict__ cases, int ncases, int total_items,
+                      const CUtensorMap* __restrict__ maps, const T* __restrict__ src_base,
+                      T* __restrict__ dst_base, int zchunk, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ StepArgs sa;
+  __shared__ int s_case, s_item;
+  if (smem_addr(smem) & 127u) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
+    return;
+  }
+  tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS>(smem), NS);
+  unsigned G0 = 0;
+  for (int w = blockIdx.x; w < total_items; w += gridDim.x) {
+    __syncthreads();  // the previous item is done with the shared state
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      int lo = 0, hi = ncases - 1;  // last case with item_start <= w
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cases[mid].item_start <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      s_case = lo;
+      s_item = w - cases[lo].item_start;
+      sa = cases[lo].args;
+      const CUtensorMap* m = maps + 2 * lo;
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(m)
+                   : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(m + 1)
+                   : "memory");
+    }
+    __syncthreads();
+    const BatchCase& bc = cases[s_case];
+    const int item = s_item;
+    const int bx = item % bc.tiles_x, rest = item / bc.tiles_x;
+    const int by = rest % bc.tiles_y, chunk = rest / bc.tiles_y;
+    const int zb = chunk * zchunk;
+    const int ze = min(zb + zchunk, sa.nz);
+    const size_t off = 2 * (size_t)bc.pair_base;
+    if (!tma_chunk<T, WALLS, TW, BY, NS>(src_base + off, dst_base + off, sa, maps + 2 * s_case,
+                                         maps + 2 * s_case + 1, bx, by, zb, ze, smem, G0, err))
+      return;
+    G0 += (unsigned)(ze - zb + 2);
   }
 }
 
@@ -428,6 +513,52 @@ cudaError_t launch_fused_tma_storage(const void* src, void* dst, const StepArgs&
   const bool walls = a.wx || a.wy || a.wz;
   return walls ? launch_tma_w<T, true>(src, dst, a, maps, kind, ns, zc, err, s)
                : launch_tma_w<T, false>(src, dst, a, maps, kind, ns, zc, err, s);
+}
+
+template <typename T, bool WALLS, int TW, int BY, int NS>
+static cudaError_t launch_tma_batch_v(const void* src, void* dst, const BatchCase* cases,
+                                      int ncases, int total_items, const CUtensorMap* maps,
+                                      int zc, int* err, int sms, cudaStream_t s) {
+  if constexpr (!tma_fits<T, TW, BY, NS>()) {
+    return cudaErrorInvalidValue;
+  } else {
+    static int per_sm = 0;  // resident CTAs per SM, queried once
+    constexpr int bytes = tma_smem_bytes<T, TW, BY, NS>();
+    if (per_sm == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k_fused_tma_batch<T, WALLS, TW, BY, NS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return e;
+      int q = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &q, k_fused_tma_batch<T, WALLS, TW, BY, NS>, TW * BY, bytes);
+      if (e != cudaSuccess) return e;
+      per_sm = q < 1 ? 1 : q;
+    }
+    const int grid = min(total_items, sms * per_sm);
+    k_fused_tma_batch<T, WALLS, TW, BY, NS><<<grid, dim3(TW, BY), bytes, s>>>(
+        cases, ncases, total_items, maps, (const T*)src, (T*)dst, zc, err);
+    return cudaGetLastError();
+  }
+}
+
+// Batched TMA step; kind 0 (32 x 8) or 2 (34 x 15), ns stages; maps: the
+// device table of the source buffer's tensor maps, two per case.
+template <typename T>
+cudaError_t launch_fused_tma_batch_storage(const void* src, void* dst, const BatchCase* cases,
+                                           int ncases, int total_items, bool walls,
+                                           const CUtensorMap* maps, int kind, int ns, int zc,
+                                           int* err, int sms, cudaStream_t s) {
+  switch ((kind == 2 ? 2 : 0) + (ns - 1) + (walls ? 4 : 0)) {
+    case 0: return launch_tma_batch_v<T, false, 32, 8, 1>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 1: return launch_tma_batch_v<T, false, 32, 8, 2>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 2: return launch_tma_batch_v<T, false, 34, 15, 1>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 3: return launch_tma_batch_v<T, false, 34, 15, 2>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 4: return launch_tma_batch_v<T, true, 32, 8, 1>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 5: return launch_tma_batch_v<T, true, 32, 8, 2>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 6: return launch_tma_batch_v<T, true, 34, 15, 1>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+    case 7: return launch_tma_batch_v<T, true, 34, 15, 2>(src, dst, cases, ncases, total_items, maps, zc, err, sms, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // Whether (kind, ns) fits the shared memory for the storage type.

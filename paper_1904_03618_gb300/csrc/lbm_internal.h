@@ -69,6 +69,8 @@ int tma_kind(int tile_y);  // -1 for a tile_y without a TMA form
 cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
                            CUtensorMap maps[2]);
 bool tma_config_fits(int storage, int kind, int ns);
+// Interior width of a tile (30, or 32 for the 34 x 15 tile, tile_y 15).
+inline int tile_interior_x(int tile_y) { return tile_y == 15 ? 32 : 30; }
 // Default TMA configuration for a single lattice (false: keep the plain one).
 bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind_ok[3],
                         FusedConfig* out);
@@ -101,6 +103,17 @@ cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
                                const BatchCase* cases, int ncases,
                                int total_items, bool walls,
                                const FusedConfig& cfg, int sms, cudaStream_t s);
+// Batched TMA step (kind 0 or 2): maps = the device table of the source
+// buffer's tensor maps, two per case.
+template <typename T>
+cudaError_t launch_fused_tma_batch_storage(const void* src, void* dst, const BatchCase* cases,
+                                           int ncases, int total_items, bool walls,
+                                           const CUtensorMap* maps, int kind, int ns, int zc,
+                                           int* err, int sms, cudaStream_t s);
+cudaError_t launch_fused_tma_batch(int storage, const void* src, void* dst,
+                                   const BatchCase* cases, int ncases, int total_items,
+                                   bool walls, const CUtensorMap* maps, int kind, int ns, int zc,
+                                   int* err, int sms, cudaStream_t s);
 bool valid_batch_config(const FusedConfig& c);
 bool valid_fused_config(const FusedConfig& c, int storage);
 

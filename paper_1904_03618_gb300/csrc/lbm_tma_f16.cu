@@ -6,5 +6,8 @@ namespace lbm {
 template cudaError_t launch_fused_tma_storage<__half>(const void*, void*, const StepArgs&,
                                                    const CUtensorMap*, int, int, int,
                                                    int*, cudaStream_t);
+template cudaError_t launch_fused_tma_batch_storage<__half>(
+    const void*, void*, const BatchCase*, int, int, bool, const CUtensorMap*, int, int, int, int*,
+    int, cudaStream_t);
 template bool tma_config_fits_storage<__half>(int, int);
 }  // namespace lbm

@@ -73,6 +73,56 @@ def test_batch_cases_equal_single_lattices(cfg, storage):
     b.close()
 
 
+# every case with a 16-byte multiple x row in FP32 and 16-bit storage, so
+# that the batch has tensor maps for the TMA-staged forms
+TMA_CASES = [
+    _case(32, 32, 32, rho_in_R=1.0, alpha_R=1 / 3, alpha_B=1 / 3, A_R=0.0225, A_B=0.0225),
+    _case(44, 17, 23, wall=(0, 0, 1), gravity=(0, 0, -1e-5)),
+    _case(64, 13, 9, wall=(1, 1, 0), improved=False, force=(1e-5, 0, 0)),
+    _case(4, 40, 4, wall=(0, 1, 0), rho_in_R=0.8, rho_in_B=0.1, alpha_B=0.2,
+          alpha_R=1 - 0.8 * 0.1 / 0.8, force=(1e-6, 0, 0)),
+    _case(20, 20, 20, rho_in_R=10.0, alpha_R=0.97, A_R=0.01125, A_B=0.01125),
+    _case(36, 24, 12, wall=(0, 0, 1), wetting=True, contact_angle_deg=120.0),
+]
+
+
+@pytest.mark.parametrize("cfg", [(8, 0, 7), (8, 5, 8), (15, 0, 7), (15, 5, 8), (15, 3, 7)])
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_tma_cases_equal_single_lattices(cfg, storage):
+    """The batched TMA-staged step: tensor maps per case from a device
+    table, persistent CTAs over (case, chunk, tile) items, the stage
+    mbarrier phases carried across items."""
+    stream = torch.cuda.Stream(DEV)
+    params = [lbm.make_params(storage=storage, **d) for d in TMA_CASES]
+    b = lbm.Batch(params, device=DEV, stream=stream)
+    lbm.lbm_set_fused_config(b.ctx, *cfg)
+    for k, d in enumerate(TMA_CASES):
+        b.init_fields(k, *_fields(d, 7))
+    b.step(7)
+    d0 = b.diagnostics(0)
+    for k, d in enumerate(TMA_CASES):
+        got = b.get_f(k)
+        ref = _run_single(d, 7, storage=storage)
+        tol = 1e-5 if storage == "f32" else 2.0 ** -10
+        err = (got.double() - ref.double()).abs().max() / ref.double().abs().max()
+        assert err.item() <= tol, (k, err.item())
+    assert d0[5] == 0
+    b.close()
+
+
+def test_batch_tma_rejected_without_maps():
+    """A batch with a case whose x row is not a 16-byte multiple has no
+    tensor maps: the TMA forms are refused, the others run."""
+    params = [lbm.make_params(**d) for d in CASES]
+    b = lbm.Batch(params, device=DEV)
+    try:
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_fused_config(b.ctx, 15, 0, 7)
+        lbm.lbm_set_fused_config(b.ctx, 8, 0, 2)
+    finally:
+        b.close()
+
+
 def test_batch_case_against_oracle():
     d = CASES[1]
     b = lbm.Batch([lbm.make_params(**dd) for dd in CASES], device=DEV,
