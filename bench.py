@@ -229,6 +229,24 @@ def config_block(args, world):
 
 
 # ---------------------------------------------------------------------------
+# Replica bookkeeping of N > 1 runs (no data-path collective: each rank
+# advances its own lattice; only the timings meet).
+def max_over_ranks(value, dist, device=None):
+    """The largest of the ranks' values (every rank gets it)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells_per_rank, seconds):
+    """Cell updates of all ranks over the slowest rank's time, in MLUPS."""
+    return world * cells_per_rank / seconds / 1e6
+
+
+# ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -287,12 +305,9 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     diag = lat.diagnostics(raise_unstable=False)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * N / (ms_per_step * 1e-3) / 1e6
+    value = whole_job_mlups(world, N, ms_per_step * 1e-3)
 
     # --- end to end through the C ABI with host buffers -------------------
     pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
@@ -313,11 +328,8 @@ def run_ours(args, rank, world, local_rank):
     lbm.lbm_moments(lat.ctx, oR, oB, ou)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * N * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_value = whole_job_mlups(world, N * e2e_steps, e2e_s)
     h2d = 5 * 4 * N / e2e_steps
     d2h = (5 * 4 * N + e2e_steps * 12 * 8) / e2e_steps
 
