@@ -49,6 +49,7 @@ struct GemmArgs {
   float* C;
   long long sc_m;
   int* err;              // set to 1 if a bounded wait gives up
+  int splits;            // K split over gridDim.y CTAs; > 1: C zeroed, partials added
 };
 
 struct GemmSmem {
@@ -111,6 +112,97 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned phase) {
   return true;
 }
 
+// Stages the ROWS x 64 slice X(r, k), r in [r0, r0 + ROWS), k in [k0, k0 + 64),
+// of X(r, k) = X[r * s_r + k * s_k] into the K-major core layout as BF16, zero
+// outside [0, R) x [0, K).  Where one stride is 1 and 16-byte groups are
+// aligned, each thread issues a batch of 16-byte loads before converting
+// and storing any of them (memory-level parallelism); the ragged edge and
+// other strides take scalar loads.
+template <int ROWS>
+__device__ __forceinline__ void stage_slice(unsigned char* dst, const float* __restrict__ X,
+                                            long long s_r, long long s_k, int r0, int R,
+                                            int k0, int K, int tid) {
+  constexpr int kBatch = 8;
+  const bool aligned = (reinterpret_cast<unsigned long long>(X) & 15u) == 0;
+  if (s_k == 1 && aligned && (s_r & 3) == 0) {
+    // groups of 4 consecutive k: ROWS x 16 groups
+    constexpr int G = ROWS * (kKT / 4);
+    for (int base = 0; base < G; base += kThreads * kBatch) {
+      float4 v[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int t = base + b * kThreads + tid;
+        const int r = t / (kKT / 4), kq = (t % (kKT / 4)) * 4;
+        const int m = r0 + r, kk = k0 + kq;
+        v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < G && m < R) {
+          const float* p = X + m * s_r + kk;
+          if (kk + 3 < K) {
+            v[b] = __ldg(reinterpret_cast<const float4*>(p));
+          } else {
+            if (kk < K) v[b].x = __ldg(p);
+            if (kk + 1 < K) v[b].y = __ldg(p + 1);
+            if (kk + 2 < K) v[b].z = __ldg(p + 2);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int t = base + b * kThreads + tid;
+        if (t >= G) continue;
+        const int r = t / (kKT / 4), kq = (t % (kKT / 4)) * 4;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[b].x, v[b].y);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[b].z, v[b].w);
+        uint2 w;
+        w.x = *reinterpret_cast<unsigned*>(&lo);
+        w.y = *reinterpret_cast<unsigned*>(&hi);
+        *reinterpret_cast<uint2*>(dst + core_offset(r, kq)) = w;
+      }
+    }
+  } else if (s_r == 1 && aligned && (s_k & 3) == 0) {
+    // groups of 4 consecutive rows: (ROWS / 4) x 64 groups
+    constexpr int G = (ROWS / 4) * kKT;
+    for (int base = 0; base < G; base += kThreads * kBatch) {
+      float4 v[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int t = base + b * kThreads + tid;
+        const int k = t / (ROWS / 4), rq = (t % (ROWS / 4)) * 4;
+        const int m = r0 + rq, kk = k0 + k;
+        v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < G && kk < K) {
+          const float* p = X + m + kk * s_k;
+          if (m + 3 < R) {
+            v[b] = __ldg(reinterpret_cast<const float4*>(p));
+          } else {
+            if (m < R) v[b].x = __ldg(p);
+            if (m + 1 < R) v[b].y = __ldg(p + 1);
+            if (m + 2 < R) v[b].z = __ldg(p + 2);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int t = base + b * kThreads + tid;
+        if (t >= G) continue;
+        const int k = t / (ROWS / 4), rq = (t % (ROWS / 4)) * 4;
+        const float e[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          *reinterpret_cast<__nv_bfloat16*>(dst + core_offset(rq + j, k)) =
+              __float2bfloat16_rn(e[j]);
+      }
+    }
+  } else {
+    for (int e = tid; e < ROWS * kKT; e += kThreads) {
+      const int r = e / kKT, k = e % kKT;
+      const int m = r0 + r, kk = k0 + k;
+      const float v = (m < R && kk < K) ? X[m * s_r + kk * s_k] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(dst + core_offset(r, k)) = __float2bfloat16_rn(v);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(smem_raw);
@@ -139,32 +231,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
 
   const unsigned a_base = smem_u32(sm.a), b_base = smem_u32(sm.b);
   const unsigned idesc = instr_desc(n_mma);
-  const bool a_rows_contig = g.sa_k == 1;
-  const bool b_cols_contig = g.sb_n == 1;
   bool ok = true;
   unsigned phase = 0;
   const int nk = (g.K + kKT - 1) / kKT;
-  for (int kt = 0; kt < nk && ok; ++kt) {
+  // this CTA's share of the K slices (split K over gridDim.y)
+  const int per = (nk + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int kt0 = (int)blockIdx.y * per, kt1 = min(nk, kt0 + per);
+  for (int kt = kt0; kt < kt1 && ok; ++kt) {
     const int k0 = kt * kKT;
-    // stage A (128 x 64) and B (n_mma x 64) as BF16, zero outside the matrix
-    for (int e = tid; e < kM * kKT; e += kThreads) {
-      int r, k;
-      if (a_rows_contig) { r = e / kKT; k = e % kKT; }
-      else { k = e / kM; r = e % kM; }
-      const int m = m0 + r, kk = k0 + k;
-      const float v = (m < g.M && kk < g.K) ? g.A[m * g.sa_m + kk * g.sa_k] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.a) +
-                                        core_offset(r, k)) = __float2bfloat16_rn(v);
-    }
-    for (int e = tid; e < n_mma * kKT; e += kThreads) {
-      int n, k;
-      if (b_cols_contig) { k = e / n_mma; n = e % n_mma; }
-      else { n = e / kKT; k = e % kKT; }
-      const int kk = k0 + k;
-      const float v = (n < g.N && kk < g.K) ? g.B[kk * g.sb_k + n * g.sb_n] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.b) +
-                                        core_offset(n, k)) = __float2bfloat16_rn(v);
-    }
+    // stage A (128 x 64) and B (n_mma x 64; B as rows n) as BF16, zero
+    // outside the matrix
+    stage_slice<kM>(reinterpret_cast<unsigned char*>(sm.a), g.A, g.sa_m, g.sa_k, m0, g.M, k0,
+                    g.K, tid);
+    if (n_mma <= 128)
+      stage_slice<128>(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, 0, g.N,
+                       k0, g.K, tid);
+    else
+      stage_slice<kNMax>(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, 0, g.N,
+                         k0, g.K, tid);
     // make the generic-proxy writes visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
@@ -175,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
         // K slice s = core matrices 2s, 2s + 1 along K
         const unsigned long long da = smem_desc(a_base + s * 256, 128, 1024);
         const unsigned long long db = smem_desc(b_base + s * 256, 128, 1024);
-        const unsigned accum = (kt > 0 || s > 0) ? 1u : 0u;
+        const unsigned accum = (kt > kt0 || s > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -197,11 +281,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
     if (tid == 0) atomicExch(g.err, 1);
     // give in-flight MMAs a second bounded chance before TMEM is released
     mbar_wait(mbar, phase ^ 1u);
-  } else {
+  } else if (kt0 < kt1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 = rows of the tile
     const int row = warp * 32 + lane;
     const int m = m0 + row;
+    const bool vec = g.splits == 1 && (g.sc_m & 3) == 0 &&
+                     (reinterpret_cast<unsigned long long>(g.C) & 15u) == 0;
     for (int c0 = 0; c0 < n_mma; c0 += 8) {
       unsigned r[8];
       const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
@@ -212,20 +298,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (m < g.M) {
+      if (m >= g.M) continue;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = c0 + j;
+        v[j] = __uint_as_float(r[j]);
+        if (n >= g.N) continue;
+        if (g.H) {
+          const float h = g.H[m * g.sh_m + n];
+          v[j] *= (1.f - h * h);
+        } else {
+          if (g.bias) v[j] += g.bias[n];
+          // tanh on the special-function unit: its error (about 2^-11
+          // relative) is below the BF16 rounding of the operands
+          if (g.act == 1) asm("tanh.approx.f32 %0, %0;" : "+f"(v[j]));
+        }
+      }
+      float* crow = g.C + m * g.sc_m + c0;
+      if (vec && c0 + 7 < g.N) {
+        reinterpret_cast<float4*>(crow)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(crow)[1] = make_float4(v[4], v[5], v[6], v[7]);
+      } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int n = c0 + j;
-          if (n >= g.N) continue;
-          float v = __uint_as_float(r[j]);
-          if (g.H) {
-            const float h = g.H[m * g.sh_m + n];
-            v *= (1.f - h * h);
-          } else {
-            if (g.bias) v += g.bias[n];
-            if (g.act == 1) v = tanhf(v);
-          }
-          g.C[m * g.sc_m + n] = v;
+          if (c0 + j >= g.N) continue;
+          if (g.splits > 1) atomicAdd(crow + j, v[j]);
+          else crow[j] = v[j];
         }
       }
     }
@@ -238,7 +337,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
                  : "memory");
 }
 
-cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
+// K split for products with few row tiles and many K slices (linear
+// epilogues only: no bias, no activation); C is zeroed and the CTAs add.
+static int choose_splits(const GemmArgs& g) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  if (g.bias || g.act || g.sc_m != g.N) return 1;  // contiguous C: one memset zeroes it
+  const int mt = (g.M + kM - 1) / kM, nk = (g.K + kKT - 1) / kKT;
+  int want = (2 * sms) / mt;  // about two CTAs per SM in all
+  if (want > nk) want = nk;
+  if (want <= 1) return 1;
+  const int per = (nk + want - 1) / want;
+  return (nk + per - 1) / per;  // no split left without slices
+}
+
+cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
+  GemmArgs g = g_in;
+  g.splits = choose_splits(g);
   static bool attr = false;
   // 100 KB of shared memory per CTA keeps at most two CTAs on an SM, so
   // their TMEM allocations (<= 256 columns each) never exceed the SM's 512.
@@ -251,7 +371,11 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
     attr = true;
   }
   if (g.N < 1 || g.N > kNMax || g.M < 1 || g.K < 1) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((g.M + kM - 1) / kM);
+  if (g.splits > 1) {
+    cudaError_t e = cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.N, s);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((unsigned)((g.M + kM - 1) / kM), (unsigned)g.splits);
   k_gemm_tc<<<grid, kThreads, bytes, s>>>(g);
   return cudaGetLastError();
 }
