@@ -327,8 +327,7 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
       cudaMalloc(&c->phase, sizeof(float4) * (size_t)c->max_cells) != cudaSuccess)
     st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the phase field failed");
   if (st == LBM_OK) {
-    long long nb = (c->max_cells + 255) / 256;
-    c->diag_blocks = (int)(nb < 4 * c->sms ? nb : 4 * c->sms);
+    c->diag_blocks = lbm::diag_capacity(c->storage, c->sms);
     if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
         cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
@@ -645,10 +644,8 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   if (st != LBM_OK) return st;
   if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "diagnostics before init");
   const CaseRec& r = c->cases[k];
-  long long nb = (r.N + 255) / 256;
-  const int blocks = (int)(nb < c->diag_blocks ? nb : c->diag_blocks);
   LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
-                               c->diag_part, blocks, c->diag_out, c->stream),
+                               c->diag_part, c->diag_blocks, c->diag_out, c->stream),
            "diagnostics kernels");
   double d[lbm::kDiagSlots];
   LBM_CUDA(c, cudaMemcpyAsync(d, c->diag_out, sizeof(d), cudaMemcpyDeviceToHost,

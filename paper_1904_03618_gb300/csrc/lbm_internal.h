@@ -31,9 +31,12 @@ cudaError_t launch_moments(int storage, const void* src, const StepArgs& a,
                            float* rR, float* rB, float* u, cudaStream_t s);
 cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, int axis,
                              int index, unsigned long long* count, cudaStream_t s);
+// Diagnostics into out[kDiagSlots]; part holds max_blocks * kDiagSlots
+// doubles, max_blocks from diag_capacity (the blocks resident at once).
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
-                        double* part, int nblocks, double* out,
+                        double* part, int max_blocks, double* out,
                         cudaStream_t s);
+int diag_capacity(int storage, int sms);
 cudaError_t launch_twopass(int storage, const void* src, void* dst,
                            const StepArgs& a, float4* mom, cudaStream_t s);
 

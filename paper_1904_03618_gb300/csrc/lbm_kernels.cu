@@ -162,16 +162,24 @@ __global__ void k_footprint(const T* __restrict__ src, StepArgs a, int axis, int
 }
 
 // ---------------------------------------------------------------------------
-// Diagnostics with FP64 results.  Each thread accumulates its cells' colour
-// masses, momentum and red-mass moments in FP32 with Neumaier compensation
-// (running sum plus running error), which keeps the sums to about FP64
-// accuracy at FP32 cost -- the part's FP64 rate is far below its FP32 rate.
-// The per-thread sums are converted to FP64 once, reduced per block (warp
-// shuffles, then shared memory) into a scratch array, and one warp per slot
-// folds the block partials in a fixed order, so the result is
-// deterministic.
+// Diagnostics with FP64 results.  A thread walks one (x, y) column over a z
+// range (and further columns when the grid has fewer threads than the
+// lattice has columns), so the column's offsets are formed once and no cell
+// index is divided.  The colour masses and the momentum are exact to about
+// FP64 accuracy at FP32 cost (the part's FP64 rate is far below its FP32
+// rate): every thread keeps one compensated FP32 accumulator (Neumaier:
+// running sum plus running error) per colour and direction, each pulled
+// value enters its own accumulator with one compensated add (38 per cell),
+// and since the masses and the momentum are linear in the per-direction
+// sums they are formed from the 38 accumulators once per thread.  The
+// per-cell quantities (finiteness, densities, |u|, the sign of rho^N) come
+// from the plain FP32 cell macroscopics the step itself uses, and the
+// red-mass centroid moments from the plain per-cell rho_R (centroid to FP32
+// accuracy).  Per-thread sums are folded across the warp as compensated
+// pairs, across the block in FP64, and one warp per slot folds the block
+// partials in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
-constexpr int kDiagBlock = 256;
+constexpr int kDiagBlock = 128;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -191,68 +199,110 @@ struct CSum {
     c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
     s = t;
   }
+  // adds sign * (o.s + o.c)
+  __device__ __forceinline__ void merge(const CSum& o, float sign = 1.f) {
+    add(sign * o.s);
+    c += sign * o.c;
+  }
+  // adds x * (o.s + o.c) with the product's rounding error kept (FMA)
+  __device__ __forceinline__ void add_scaled(float x, const CSum& o) {
+    const float p = x * o.s;
+    add(p);
+    c += fmaf(x, o.s, -p) + x * o.c;
+  }
+  // sum over the warp, in lane 0
+  __device__ __forceinline__ void warp_fold() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+      add(s2);
+      c += c2;
+    }
+  }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kDiagBlock)
-    k_diag_partial(const T* __restrict__ src, StepArgs a,
+__global__ void __launch_bounds__(kDiagBlock, 3)
+    k_diag_partial(const T* __restrict__ src, StepArgs a, int zc,
                    double* __restrict__ part) {
-  // slots 0..4, 9..11 compensated sums; 5, 6, 8, 12 counts; 7 max
-  CSum mR, mB, jx, jy, jz, cx, cy, cz;
+  CSum sR[19], sB[19];     // per-direction sums of the pulled values
+  CSum cx, cy, cz;         // red-mass moments
   unsigned n_nonfinite = 0, n_negative = 0, n_red = 0, n_colour_negative = 0;
-  float umax = 0.f;
-  const unsigned nx = (unsigned)a.nx, ny = (unsigned)a.ny;
-  const unsigned N = nx * ny * (unsigned)a.nz;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < N;
-       c += gridDim.x * blockDim.x) {
-    const unsigned x = c % nx, t = c / nx;
-    const unsigned y = t % ny, z = t / ny;
-    float fR[19], fB[19];
-    pull_pairs<T>(src, a, (int)x, (int)y, (int)z, fR, fB);
-    bool finite = true;
-    CSum cR;
+  float u2max = 0.f;
+  const unsigned nx = (unsigned)a.nx, cols = nx * (unsigned)a.ny;
+  const int z0 = blockIdx.y * zc;
+  const int z1 = min(a.nz, z0 + zc);
+  const auto* pairs = reinterpret_cast<const typename Store<T>::Pair*>(src);
+  for (unsigned col = blockIdx.x * kDiagBlock + threadIdx.x; col < cols;
+       col += gridDim.x * kDiagBlock) {
+    const unsigned y = col / nx, x = col - y * nx;
+    const ColOff co = col_off(a, (int)x, (int)y);
+    CSum colR, colZ;
+    for (int z = z0; z < z1; ++z) {
+      float fR[19], fB[19];
+      PullPairs<T, 0>::run(pairs, a, co, plane_off(a, z), fR, fB);
+      // x * 0 is 0 for finite x and NaN for infinities and NaN
+      float bad = 0.f;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-      finite = finite && isfinite(fR[i]) && isfinite(fB[i]);
-      cR.add(fR[i]);
-      mR.add(fR[i]);
-      mB.add(fB[i]);
-      if (ex(i)) {
-        jx.add(ex(i) * fR[i]);
-        jx.add(ex(i) * fB[i]);
+      for (int i = 0; i < 19; ++i) {
+        sR[i].add(fR[i]);
+        sB[i].add(fB[i]);
+        bad = fmaf(fR[i], 0.f, bad);
+        bad = fmaf(fB[i], 0.f, bad);
       }
-      if (ey(i)) {
-        jy.add(ey(i) * fR[i]);
-        jy.add(ey(i) * fB[i]);
-      }
-      if (ez(i)) {
-        jz.add(ez(i) * fR[i]);
-        jz.add(ez(i) * fB[i]);
-      }
+      const bool finite = bad == 0.f;
+      const Macro m = macro_of(a, fR, fB);
+      n_nonfinite += finite ? 0u : 1u;
+      n_negative += (m.rho <= 0.f) ? 1u : 0u;
+      n_colour_negative += (m.rR < 0.f || m.rB < 0.f) ? 1u : 0u;
+      const float u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+      if (finite && u2 > u2max) u2max = u2;
+      n_red += phase_field(a, m.rR, m.rB) > 0.f ? 1u : 0u;
+      colR.add(m.rR);
+      colZ.add(m.rR * (float)z);
     }
-    const float rRc = cR.s + cR.c;
-    cx.add(rRc * (float)x);
-    cy.add(rRc * (float)y);
-    cz.add(rRc * (float)z);
-    const Macro m = macro_of(a, fR, fB);
-    n_nonfinite += finite ? 0u : 1u;
-    n_negative += (m.rho <= 0.f) ? 1u : 0u;
-    n_colour_negative += (m.rR < 0.f || m.rB < 0.f) ? 1u : 0u;
-    const float um = sqrtf(m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    if (finite && um > umax) umax = um;
-    n_red += phase_field(a, m.rR, m.rB) > 0.f ? 1u : 0u;
+    cx.add_scaled((float)x, colR);
+    cy.add_scaled((float)y, colR);
+    cz.merge(colZ);
   }
-  double acc[kDiagSlots] = {mR.value(), mB.value(), jx.value(), jy.value(),
-                            jz.value(), (double)n_nonfinite, (double)n_negative,
-                            (double)umax, (double)n_red, cx.value(), cy.value(),
-                            cz.value(), (double)n_colour_negative};
+  CSum mR, mB, jx, jy, jz;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    mR.merge(sR[i]);
+    mB.merge(sB[i]);
+    if (ex(i)) { jx.merge(sR[i], (float)ex(i)); jx.merge(sB[i], (float)ex(i)); }
+    if (ey(i)) { jy.merge(sR[i], (float)ey(i)); jy.merge(sB[i], (float)ey(i)); }
+    if (ez(i)) { jz.merge(sR[i], (float)ez(i)); jz.merge(sB[i], (float)ez(i)); }
+  }
+  CSum* sums[8] = {&mR, &mB, &jx, &jy, &jz, &cx, &cy, &cz};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sums[k]->warp_fold();
+  const unsigned full = 0xffffffffu;
+  n_nonfinite = __reduce_add_sync(full, n_nonfinite);
+  n_negative = __reduce_add_sync(full, n_negative);
+  n_red = __reduce_add_sync(full, n_red);
+  n_colour_negative = __reduce_add_sync(full, n_colour_negative);
+  // u2max >= 0 and never NaN, so its bit pattern orders like the value
+  const unsigned u2bits = __reduce_max_sync(full, __float_as_uint(u2max));
   __shared__ double sh[kDiagBlock / 32][kDiagSlots];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int s = 0; s < kDiagSlots; ++s) {
-    const double v = (s == 7) ? warp_max(acc[s]) : warp_sum(acc[s]);
-    if (lane == 0) sh[wid][s] = v;
+  if (lane == 0) {
+    double* w = sh[wid];
+    w[0] = mR.value();
+    w[1] = mB.value();
+    w[2] = jx.value();
+    w[3] = jy.value();
+    w[4] = jz.value();
+    w[5] = (double)n_nonfinite;
+    w[6] = (double)n_negative;
+    w[7] = sqrt((double)__uint_as_float(u2bits));
+    w[8] = (double)n_red;
+    w[9] = cx.value();
+    w[10] = cy.value();
+    w[11] = cz.value();
+    w[12] = (double)n_colour_negative;
   }
   __syncthreads();
   if (threadIdx.x < kDiagSlots) {
@@ -260,7 +310,7 @@ __global__ void __launch_bounds__(kDiagBlock)
     double v = 0.0;
     for (int w = 0; w < kDiagBlock / 32; ++w)
       v = (s == 7) ? fmax(v, sh[w][s]) : v + sh[w][s];
-    part[(size_t)blockIdx.x * kDiagSlots + s] = v;
+    part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kDiagSlots + s] = v;
   }
 }
 
@@ -395,14 +445,33 @@ cudaError_t launch_footprint_t(const void* src, const StepArgs& a, int axis, int
   k_footprint<T><<<blocks, kAuxBlock, 0, s>>>((const T*)src, a, axis, index, count);
   return cudaGetLastError();
 }
+// Grid of the diagnostics: column blocks (x) times z ranges (y), at most
+// max_blocks blocks in all (the partials scratch holds that many).
 template <typename T>
 cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
-                          int nblocks, double* out, cudaStream_t s) {
-  k_diag_partial<T><<<nblocks, kDiagBlock, 0, s>>>((const T*)src, a, part);
+                          int max_blocks, double* out, cudaStream_t s) {
+  const long long cols = (long long)a.nx * a.ny;
+  const long long cb = (cols + kDiagBlock - 1) / kDiagBlock;
+  const int gx = (int)(cb < max_blocks ? cb : max_blocks);
+  int gy = max_blocks / gx;
+  if (gy > a.nz) gy = a.nz;
+  if (gy < 1) gy = 1;
+  const int zc = (a.nz + gy - 1) / gy;
+  gy = (a.nz + zc - 1) / zc;
+  k_diag_partial<T><<<dim3(gx, gy), kDiagBlock, 0, s>>>((const T*)src, a, zc, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_diag_final<<<1, 32 * kDiagSlots, 0, s>>>(part, nblocks, out);
+  k_diag_final<<<1, 32 * kDiagSlots, 0, s>>>(part, gx * gy, out);
   return cudaGetLastError();
+}
+template <typename T>
+int diag_capacity_t(int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_partial<T>,
+                                                    kDiagBlock, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * sms;
 }
 template <typename T>
 cudaError_t launch_twopass_t(const void* src, void* dst, const StepArgs& a,
@@ -447,9 +516,16 @@ cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, in
   LBM_DISPATCH(storage, launch_footprint_t, src, a, axis, index, count, s)
 }
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
-                        double* part, int nblocks, double* out,
+                        double* part, int max_blocks, double* out,
                         cudaStream_t s) {
-  LBM_DISPATCH(storage, launch_diag_t, src, a, part, nblocks, out, s)
+  LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, out, s)
+}
+int diag_capacity(int storage, int sms) {
+  switch (storage) {
+    case 1: return diag_capacity_t<__half>(sms);
+    case 2: return diag_capacity_t<__nv_bfloat16>(sms);
+    default: return diag_capacity_t<float>(sms);
+  }
 }
 cudaError_t launch_twopass(int storage, const void* src, void* dst,
                            const StepArgs& a, float4* mom, cudaStream_t s) {

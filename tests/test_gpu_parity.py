@@ -247,6 +247,50 @@ def test_diagnostics_and_mass_conservation():
     assert e.nx == 40
 
 
+_E = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1],
+               [0, 0, -1], [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1],
+               [-1, 0, -1], [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1],
+               [0, -1, 1]], float)
+
+
+@pytest.mark.parametrize("shape,wall,storage,steps", [
+    ((40, 24, 16), (0, 0, 1), "f32", 50),      # z walls, several z ranges per column
+    ((256, 256, 4), (0, 0, 0), "f32", 3),      # more columns than threads: strided
+    ((36, 20, 12), (1, 1, 0), "f16", 20),      # x and y walls, 16-bit storage
+])
+def test_every_diagnostics_slot_against_fp64_sums(shape, wall, storage, steps):
+    nx, ny, nz = shape
+    pd = base(nx, ny, nz, wall=wall)
+    f0 = droplet_state(pd, min(nx, ny, nz) / 3.0, (0.02, -0.01, 0.0))
+    p = lbm.make_params(storage=storage, **pd)
+    lat = lbm.Lattice(p, device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    lat.step(steps)
+    d = lat.diagnostics()
+    f = lat.get_f().double().cpu().numpy()
+    lat.close()
+    rR, rB = f[0].sum(0), f[1].sum(0)
+    rho = rR + rB
+    F = np.array(pd["force"])[:, None, None, None] + \
+        rho[None] * np.array(pd["gravity"])[:, None, None, None]
+    j = np.einsum("ia,kizyx->azyx", _E, f)
+    u = (j + 0.5 * F) / rho[None]
+    assert d[0] == pytest.approx(rR.sum(), rel=1e-12)
+    assert d[1] == pytest.approx(rB.sum(), rel=1e-12)
+    assert np.allclose(d[2:5], j.sum((1, 2, 3)), rtol=1e-9, atol=1e-12 * np.abs(f).sum())
+    assert d[5] == 0 and d[6] == 0 and d[12] == steps
+    assert d[7] == pytest.approx(np.sqrt((u ** 2).sum(0)).max(), rel=1e-5)
+    r, b = rR / pd["rho_in_R"], rB / pd["rho_in_B"]
+    phase = (r - b) / (r + b)
+    assert abs(d[8] - (phase > 0).sum()) <= (np.abs(phase) < 1e-5).sum()
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for k, coord in zip((9, 10, 11), (xx, yy, zz)):
+        assert d[k] == pytest.approx((rR * coord).sum() / rR.sum(), rel=1e-6, abs=1e-5)
+    neg = (rR < 0) | (rB < 0)
+    near = (np.abs(rR) < 1e-6 * rho) | (np.abs(rB) < 1e-6 * rho)
+    assert abs(d[13] - neg.sum()) <= near.sum()
+
+
 def test_non_finite_state_is_reported_not_faulted():
     pd = base(16, 8, 4)
     f0 = droplet_state(pd, 3.0)
