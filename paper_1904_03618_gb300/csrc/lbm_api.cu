@@ -37,7 +37,9 @@ struct lbm_ctx {
   int cur;                  // buffer holding the current state (pull layout)
   float4* phase;            // two-pass scratch: (rho^N, Qbar) per cell
   double* diag_part;        // per-block partial sums of the diagnostics
-  double* diag_out;         // folded sums (device)
+  double* diag_out;         // folded sums and the error word (device)
+  unsigned* diag_done;      // block counter of the diagnostics kernel
+  double* diag_host;        // pinned host copy of diag_out
   int diag_blocks;
   float* staging;           // device staging for host-pointer transfers
   size_t staging_floats;
@@ -210,6 +212,8 @@ static void release(lbm_ctx* c) {
   cudaFree(c->phase);
   cudaFree(c->diag_part);
   cudaFree(c->diag_out);
+  cudaFree(c->diag_done);
+  cudaFreeHost(c->diag_host);
   cudaFree(c->staging);
   cudaFree(c->d_cases);
   cudaFree(c->foot);
@@ -329,7 +333,10 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
   if (st == LBM_OK) {
     c->diag_blocks = lbm::diag_capacity(c->storage, c->sms);
     if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
-        cudaMalloc(&c->diag_out, sizeof(double) * lbm::kDiagSlots) != cudaSuccess)
+        cudaMalloc(&c->diag_out, sizeof(double) * (lbm::kDiagSlots + 1)) != cudaSuccess ||
+        cudaMalloc(&c->diag_done, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&c->diag_host, sizeof(double) * (lbm::kDiagSlots + 1)) != cudaSuccess ||
+        cudaMemset(c->diag_done, 0, sizeof(unsigned)) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
   }
   if (st == LBM_OK) {
@@ -645,11 +652,13 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "diagnostics before init");
   const CaseRec& r = c->cases[k];
   LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
-                               c->diag_part, c->diag_blocks, c->diag_out, c->stream),
-           "diagnostics kernels");
-  double d[lbm::kDiagSlots];
-  LBM_CUDA(c, cudaMemcpyAsync(d, c->diag_out, sizeof(d), cudaMemcpyDeviceToHost,
-                              c->stream),
+                               c->diag_part, c->diag_blocks, c->diag_done, c->d_flags,
+                               c->diag_out, c->stream),
+           "diagnostics kernel");
+  const double* d = c->diag_host;
+  LBM_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_out,
+                              sizeof(double) * (lbm::kDiagSlots + 1),
+                              cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync D2H");
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   for (int i = 0; i < 16; ++i) out[i] = 0.0;
@@ -662,9 +671,7 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   out[12] = (double)c->steps;
   out[13] = d[12];
   c->err[0] = 0;
-  int flags = 0;
-  LBM_CUDA(c, cudaMemcpy(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost),
-           "cudaMemcpy D2H");
+  const int flags = (int)d[lbm::kDiagSlots];
   if (flags)
     return fail(c, LBM_ERR_TIMEOUT,
                 "a bounded wait of the step kernel gave up (code %d); results are invalid", flags);

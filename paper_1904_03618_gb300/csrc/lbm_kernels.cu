@@ -225,8 +225,9 @@ struct CSum {
 
 template <typename T>
 __global__ void __launch_bounds__(kDiagBlock, 3)
-    k_diag_partial(const T* __restrict__ src, StepArgs a, int zc,
-                   double* __restrict__ part) {
+    k_diag(const T* __restrict__ src, StepArgs a, int zc,
+           double* __restrict__ part, unsigned* __restrict__ done,
+           const int* __restrict__ flags, double* __restrict__ out) {
   CSum sR[19], sB[19];     // per-direction sums of the pulled values
   CSum cx, cy, cz;         // red-mass moments
   unsigned n_nonfinite = 0, n_negative = 0, n_red = 0, n_colour_negative = 0;
@@ -311,22 +312,32 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
     for (int w = 0; w < kDiagBlock / 32; ++w)
       v = (s == 7) ? fmax(v, sh[w][s]) : v + sh[w][s];
     part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kDiagSlots + s] = v;
+    __threadfence();
   }
-}
-
-// One warp per slot: lanes stride over the block partials, then a fixed
-// shuffle tree.
-__global__ void k_diag_final(const double* __restrict__ part, int nblocks,
-                             double* __restrict__ out) {
-  const int s = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (s >= kDiagSlots) return;
-  double v = 0.0;
-  for (int b = lane; b < nblocks; b += 32) {
-    const double p = part[(size_t)b * kDiagSlots + s];
-    v = (s == 7) ? fmax(v, p) : v + p;
+  // The last block to finish folds every block's partials: one warp per
+  // slot, lanes striding over the blocks, then a fixed shuffle tree, so the
+  // order does not depend on which block came last.  It also copies the
+  // step kernels' error word beside the sums and re-arms the counter.
+  __shared__ bool last;
+  __syncthreads();
+  const unsigned nb = gridDim.x * gridDim.y;
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == nb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int s = wid; s < kDiagSlots; s += kDiagBlock / 32) {
+    double v = 0.0;
+    for (unsigned b = lane; b < nb; b += 32) {
+      const double p = __ldcg(part + (size_t)b * kDiagSlots + s);
+      v = (s == 7) ? fmax(v, p) : v + p;
+    }
+    v = (s == 7) ? warp_max(v) : warp_sum(v);
+    if (lane == 0) out[s] = v;
   }
-  v = (s == 7) ? warp_max(v) : warp_sum(v);
-  if (lane == 0) out[s] = v;
+  if (threadIdx.x == 0) {
+    out[kDiagSlots] = (double)__ldcg(flags);
+    *done = 0u;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -449,7 +460,8 @@ cudaError_t launch_footprint_t(const void* src, const StepArgs& a, int axis, int
 // max_blocks blocks in all (the partials scratch holds that many).
 template <typename T>
 cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
-                          int max_blocks, double* out, cudaStream_t s) {
+                          int max_blocks, unsigned* done, const int* flags,
+                          double* out, cudaStream_t s) {
   const long long cols = (long long)a.nx * a.ny;
   const long long cb = (cols + kDiagBlock - 1) / kDiagBlock;
   const int gx = (int)(cb < max_blocks ? cb : max_blocks);
@@ -458,16 +470,14 @@ cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
   if (gy < 1) gy = 1;
   const int zc = (a.nz + gy - 1) / gy;
   gy = (a.nz + zc - 1) / zc;
-  k_diag_partial<T><<<dim3(gx, gy), kDiagBlock, 0, s>>>((const T*)src, a, zc, part);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_diag_final<<<1, 32 * kDiagSlots, 0, s>>>(part, gx * gy, out);
+  k_diag<T><<<dim3(gx, gy), kDiagBlock, 0, s>>>((const T*)src, a, zc, part, done,
+                                                 flags, out);
   return cudaGetLastError();
 }
 template <typename T>
 int diag_capacity_t(int sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_partial<T>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag<T>,
                                                     kDiagBlock, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -516,9 +526,9 @@ cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, in
   LBM_DISPATCH(storage, launch_footprint_t, src, a, axis, index, count, s)
 }
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
-                        double* part, int max_blocks, double* out,
-                        cudaStream_t s) {
-  LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, out, s)
+                        double* part, int max_blocks, unsigned* done,
+                        const int* flags, double* out, cudaStream_t s) {
+  LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, done, flags, out, s)
 }
 int diag_capacity(int storage, int sms) {
   switch (storage) {
