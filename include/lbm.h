@@ -140,11 +140,30 @@ lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
    [12] number of completed steps
    [13] count of cells with rho_R < 0 or rho_B < 0 (small negative colour
         densities in the minority phase are a normal effect of the
-        recolouring, Eq. 10-11; informational)   [14..15] 0 (reserved).
-   Sums are accumulated in compensated FP32 per thread and FP64 across
-   threads.  Synchronises the context stream.  Returns LBM_ERR_UNSTABLE if
-   [5] or [6] is non-zero (out is still filled). */
+        recolouring, Eq. 10-11; informational)
+   [14] error word of the step kernels' bounded waits (0: none)
+   [15] 0 (reserved).
+   The colour masses and the momentum are exact to about FP64 accuracy
+   (one compensated FP32 accumulator per colour and direction per thread,
+   FP64 across threads); the centroid and |u| come from the FP32 cell
+   moments.  One kernel launch and one 128-byte copy; synchronises the
+   context stream.  Returns LBM_ERR_TIMEOUT if [14] is non-zero, else
+   LBM_ERR_UNSTABLE if [5] or [6] is non-zero (out is filled either way). */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[16]);
+
+/* Monitored stepping without host waits: advances n >= 0 steps (as
+   lbm_step) and queues the diagnostics of the state they reach (case 0 of
+   a batch) and an asynchronous copy of their 16 slots (as lbm_diagnostics)
+   into out, which may be pinned host memory or device memory (pageable
+   host memory makes the copy synchronous).  Returns after queueing: out is
+   valid once the context stream has passed the copy (lbm_sync).  State
+   errors are reported in the slots ([5], [6], [14]), not by the return
+   value.  Errors: LBM_ERR_ARG (out NULL, n < 0), LBM_ERR_STATE,
+   LBM_ERR_CUDA. */
+lbm_status lbm_step_diagnostics_async(lbm_ctx *ctx, int n, double *out);
+
+/* Waits until all work queued on the context stream has finished. */
+lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Copies f_i^k(x, t) -- the populations after streaming at the current
    time level, the paper's state variable -- as float32 [2][19][N] into f

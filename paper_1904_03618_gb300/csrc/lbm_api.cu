@@ -333,9 +333,9 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
   if (st == LBM_OK) {
     c->diag_blocks = lbm::diag_capacity(c->storage, c->sms);
     if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
-        cudaMalloc(&c->diag_out, sizeof(double) * (lbm::kDiagSlots + 1)) != cudaSuccess ||
+        cudaMalloc(&c->diag_out, sizeof(double) * 16) != cudaSuccess ||
         cudaMalloc(&c->diag_done, sizeof(unsigned)) != cudaSuccess ||
-        cudaMallocHost(&c->diag_host, sizeof(double) * (lbm::kDiagSlots + 1)) != cudaSuccess ||
+        cudaMallocHost(&c->diag_host, sizeof(double) * 16) != cudaSuccess ||
         cudaMemset(c->diag_done, 0, sizeof(unsigned)) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
   }
@@ -645,40 +645,54 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
   return lbm_batch_moments(c, 0, rho_R, rho_B, u);
 }
 
+static lbm_status enqueue_diag(lbm_ctx* c, int k) {
+  const CaseRec& r = c->cases[k];
+  LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
+                               c->diag_part, c->diag_blocks, c->diag_done, c->d_flags,
+                               c->steps, c->diag_out, c->stream),
+           "diagnostics kernel");
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
   if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "diagnostics before init");
-  const CaseRec& r = c->cases[k];
-  LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
-                               c->diag_part, c->diag_blocks, c->diag_done, c->d_flags,
-                               c->diag_out, c->stream),
-           "diagnostics kernel");
-  const double* d = c->diag_host;
-  LBM_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_out,
-                              sizeof(double) * (lbm::kDiagSlots + 1),
+  if ((st = enqueue_diag(c, k)) != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_out, sizeof(double) * 16,
                               cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync D2H");
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
-  for (int i = 0; i < 16; ++i) out[i] = 0.0;
-  for (int i = 0; i < 12; ++i) out[i] = d[i];
-  if (d[0] > 0) {
-    out[9] = d[9] / d[0];
-    out[10] = d[10] / d[0];
-    out[11] = d[11] / d[0];
-  }
-  out[12] = (double)c->steps;
-  out[13] = d[12];
+  for (int i = 0; i < 16; ++i) out[i] = c->diag_host[i];
   c->err[0] = 0;
-  const int flags = (int)d[lbm::kDiagSlots];
+  const int flags = (int)out[14];
   if (flags)
     return fail(c, LBM_ERR_TIMEOUT,
                 "a bounded wait of the step kernel gave up (code %d); results are invalid", flags);
-  if (d[5] != 0.0 || d[6] != 0.0)
+  if (out[5] != 0.0 || out[6] != 0.0)
     return fail(c, LBM_ERR_UNSTABLE,
                 "%.0f cells with non-finite populations, %.0f with total density <= 0",
-                d[5], d[6]);
+                out[5], out[6]);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step_diagnostics_async(lbm_ctx* c, int n, double* out) {
+  if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
+  lbm_status st = lbm_step(c, n);
+  if (st != LBM_OK) return st;
+  if ((st = enqueue_diag(c, 0)) != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(out, c->diag_out, sizeof(double) * 16, cudaMemcpyDefault,
+                              c->stream),
+           "cudaMemcpyAsync of the diagnostics");
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_ERR_ARG;
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+  c->err[0] = 0;
   return LBM_OK;
 }
 

@@ -31,13 +31,15 @@ cudaError_t launch_moments(int storage, const void* src, const StepArgs& a,
                            float* rR, float* rB, float* u, cudaStream_t s);
 cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, int axis,
                              int index, unsigned long long* count, cudaStream_t s);
-// Diagnostics into out[kDiagSlots], and the error word *flags into
-// out[kDiagSlots]; part holds max_blocks * kDiagSlots doubles, max_blocks
-// from diag_capacity (the blocks resident at once); *done is a block
-// counter, zero between launches (the kernel re-arms it).
+// Diagnostics into the 16 result slots out[] of lbm_diagnostics (device
+// memory), with steps in [12] and the error word *flags in [14]; part holds
+// max_blocks * kDiagSlots doubles, max_blocks from diag_capacity (the blocks
+// resident at once); *done is a block counter, zero between launches (the
+// kernel re-arms it).
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         double* part, int max_blocks, unsigned* done,
-                        const int* flags, double* out, cudaStream_t s);
+                        const int* flags, long long steps, double* out,
+                        cudaStream_t s);
 int diag_capacity(int storage, int sms);
 cudaError_t launch_twopass(int storage, const void* src, void* dst,
                            const StepArgs& a, float4* mom, cudaStream_t s);

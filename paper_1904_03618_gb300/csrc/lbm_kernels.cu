@@ -227,7 +227,7 @@ template <typename T>
 __global__ void __launch_bounds__(kDiagBlock, 3)
     k_diag(const T* __restrict__ src, StepArgs a, int zc,
            double* __restrict__ part, unsigned* __restrict__ done,
-           const int* __restrict__ flags, double* __restrict__ out) {
+           const int* __restrict__ flags, double steps, double* __restrict__ out) {
   CSum sR[19], sB[19];     // per-direction sums of the pulled values
   CSum cx, cy, cz;         // red-mass moments
   unsigned n_nonfinite = 0, n_negative = 0, n_red = 0, n_colour_negative = 0;
@@ -316,9 +316,11 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
   }
   // The last block to finish folds every block's partials: one warp per
   // slot, lanes striding over the blocks, then a fixed shuffle tree, so the
-  // order does not depend on which block came last.  It also copies the
-  // step kernels' error word beside the sums and re-arms the counter.
+  // order does not depend on which block came last.  It writes the 16
+  // result slots (centroid divided by the red mass, the step count, the
+  // step kernels' error word) and re-arms the counter.
   __shared__ bool last;
+  __shared__ double fin[kDiagSlots];
   __syncthreads();
   const unsigned nb = gridDim.x * gridDim.y;
   if (threadIdx.x == 0) last = atomicAdd(done, 1u) == nb - 1;
@@ -332,10 +334,17 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
       v = (s == 7) ? fmax(v, p) : v + p;
     }
     v = (s == 7) ? warp_max(v) : warp_sum(v);
-    if (lane == 0) out[s] = v;
+    if (lane == 0) fin[s] = v;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    out[kDiagSlots] = (double)__ldcg(flags);
+    for (int k = 0; k < 12; ++k) out[k] = fin[k];
+    if (fin[0] > 0.0)
+      for (int k = 9; k < 12; ++k) out[k] = fin[k] / fin[0];
+    out[12] = steps;
+    out[13] = fin[12];
+    out[14] = (double)__ldcg(flags);
+    out[15] = 0.0;
     *done = 0u;
   }
 }
@@ -461,7 +470,7 @@ cudaError_t launch_footprint_t(const void* src, const StepArgs& a, int axis, int
 template <typename T>
 cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
                           int max_blocks, unsigned* done, const int* flags,
-                          double* out, cudaStream_t s) {
+                          long long steps, double* out, cudaStream_t s) {
   const long long cols = (long long)a.nx * a.ny;
   const long long cb = (cols + kDiagBlock - 1) / kDiagBlock;
   const int gx = (int)(cb < max_blocks ? cb : max_blocks);
@@ -471,7 +480,7 @@ cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
   const int zc = (a.nz + gy - 1) / gy;
   gy = (a.nz + zc - 1) / zc;
   k_diag<T><<<dim3(gx, gy), kDiagBlock, 0, s>>>((const T*)src, a, zc, part, done,
-                                                 flags, out);
+                                                 flags, (double)steps, out);
   return cudaGetLastError();
 }
 template <typename T>
@@ -527,8 +536,10 @@ cudaError_t launch_footprint(int storage, const void* src, const StepArgs& a, in
 }
 cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         double* part, int max_blocks, unsigned* done,
-                        const int* flags, double* out, cudaStream_t s) {
-  LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, done, flags, out, s)
+                        const int* flags, long long steps, double* out,
+                        cudaStream_t s) {
+  LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, done, flags, steps,
+               out, s)
 }
 int diag_capacity(int storage, int sms) {
   switch (storage) {

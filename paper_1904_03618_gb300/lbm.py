@@ -75,6 +75,10 @@ _lib.lbm_moments.argtypes = [_ctx_p, _fp, _fp, _fp]
 _lib.lbm_moments.restype = ctypes.c_int
 _lib.lbm_diagnostics.argtypes = [_ctx_p, ctypes.POINTER(ctypes.c_double)]
 _lib.lbm_diagnostics.restype = ctypes.c_int
+_lib.lbm_step_diagnostics_async.argtypes = [_ctx_p, ctypes.c_int, _fp]
+_lib.lbm_step_diagnostics_async.restype = ctypes.c_int
+_lib.lbm_sync.argtypes = [_ctx_p]
+_lib.lbm_sync.restype = ctypes.c_int
 _lib.lbm_get_f.argtypes = [_ctx_p, _fp]
 _lib.lbm_get_f.restype = ctypes.c_int
 _lib.lbm_set_f.argtypes = [_ctx_p, _fp]
@@ -141,7 +145,7 @@ _lib.lbm_last_error.argtypes = [_ctx_p]
 _lib.lbm_last_error.restype = ctypes.c_char_p
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
-            "lbm_diagnostics", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
+            "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
@@ -279,6 +283,19 @@ def lbm_diagnostics(ctx, raise_unstable=True):
     if st != LBM_OK and (raise_unstable or st != LBM_ERR_UNSTABLE):
         raise LbmError(st, lbm_last_error(ctx))
     return np.array(out[:], dtype=np.float64)
+
+
+def lbm_step_diagnostics_async(ctx, n, out):
+    """Queues n steps, the diagnostics of the state they reach and their
+    copy into ``out`` (16 float64: a pinned CPU tensor or a device tensor);
+    ``out`` is valid after :func:`lbm_sync`."""
+    if isinstance(out, torch.Tensor) and (out.dtype != torch.float64 or out.numel() < 16):
+        raise ValueError("out must hold 16 float64 values")
+    _check(ctx, _lib.lbm_step_diagnostics_async(ctx, int(n), _addr(out)))
+
+
+def lbm_sync(ctx):
+    _check(ctx, _lib.lbm_sync(ctx))
 
 
 def lbm_get_f(ctx, f):

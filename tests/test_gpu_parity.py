@@ -291,6 +291,31 @@ def test_every_diagnostics_slot_against_fp64_sums(shape, wall, storage, steps):
     assert abs(d[13] - neg.sum()) <= near.sum()
 
 
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_async_monitored_steps_match_synchronous_diagnostics(where):
+    pd = base(40, 24, 16, wall=(0, 0, 1))
+    f0 = torch.tensor(droplet_state(pd, 6.0, (0.02, 0.0, 0.0)), dtype=torch.float32,
+                      device=DEV)
+    la = lbm.Lattice(lbm.make_params(**pd), device=DEV, stream=torch.cuda.Stream(DEV))
+    lb = lbm.Lattice(lbm.make_params(**pd), device=DEV, stream=torch.cuda.Stream(DEV))
+    la.set_f(f0)
+    lb.set_f(f0)
+    K = 6
+    out = torch.zeros((K, 16), dtype=torch.float64)
+    out = out.pin_memory() if where == "pinned" else out.to(DEV)
+    for k in range(K):   # queued back to back, one host wait at the end
+        lbm.lbm_step_diagnostics_async(la.ctx, 2, out[k])
+    lbm.lbm_sync(la.ctx)
+    got = out.cpu().numpy()
+    for k in range(K):
+        lb.step(2)
+        ref = lb.diagnostics()
+        assert np.array_equal(got[k], ref), k       # same kernels, same state
+        assert got[k][12] == 2 * (k + 1) and got[k][14] == 0
+    la.close()
+    lb.close()
+
+
 def test_non_finite_state_is_reported_not_faulted():
     pd = base(16, 8, 4)
     f0 = droplet_state(pd, 3.0)
