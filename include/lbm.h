@@ -144,8 +144,8 @@ lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
    [14] error word of the step kernels' bounded waits (0: none)
    [15] 0 (reserved).
    The colour masses and the momentum are exact to about FP64 accuracy
-   (one compensated FP32 accumulator per colour and direction per thread,
-   FP64 across threads); the centroid and |u| come from the FP32 cell
+   (compensated FP32 accumulators per direction and thread, FP64 across
+   threads); the centroid and |u| come from the FP32 cell
    moments.  One kernel launch and one 128-byte copy; synchronises the
    context stream.  Returns LBM_ERR_TIMEOUT if [14] is non-zero, else
    LBM_ERR_UNSTABLE if [5] or [6] is non-zero (out is filled either way). */

@@ -162,21 +162,22 @@ __global__ void k_footprint(const T* __restrict__ src, StepArgs a, int axis, int
 }
 
 // ---------------------------------------------------------------------------
-// Diagnostics with FP64 results.  A thread walks one (x, y) column over a z
-// range (and further columns when the grid has fewer threads than the
-// lattice has columns), so the column's offsets are formed once and no cell
-// index is divided.  The colour masses and the momentum are exact to about
-// FP64 accuracy at FP32 cost (the part's FP64 rate is far below its FP32
-// rate): every thread keeps one compensated FP32 accumulator (Neumaier:
-// running sum plus running error) per colour and direction, each pulled
-// value enters its own accumulator with one compensated add (38 per cell),
-// and since the masses and the momentum are linear in the per-direction
-// sums they are formed from the 38 accumulators once per thread.  The
-// per-cell quantities (finiteness, densities, |u|, the sign of rho^N) come
-// from the plain FP32 cell macroscopics the step itself uses, and the
-// red-mass centroid moments from the plain per-cell rho_R (centroid to FP32
+// Diagnostics with FP64 results.  Work units of one block of 128 (x, y)
+// columns times one z range are taken in turn by the resident blocks; a
+// thread walks its column over the unit's z range, so the column's offsets
+// are formed once and no cell index is divided.  The colour masses and the
+// momentum are exact to about FP64 accuracy at FP32 cost (the part's FP64
+// rate is far below its FP32 rate): every thread keeps one compensated FP32
+// accumulator (Neumaier: running sum plus running error) per direction,
+// into which both colours' pulled values are added, and one for all red
+// values (57 compensated adds per cell, 40 registers of accumulators).
+// The momentum is linear in the per-direction sums, the blue mass is the
+// total minus the red mass; both are formed once per thread.  The per-cell
+// quantities (finiteness, densities, |u|, the sign of rho^N) come from the
+// plain FP32 cell macroscopics the step itself uses, and the red-mass
+// centroid moments from the plain per-cell rho_R (centroid to FP32
 // accuracy).  Per-thread sums are folded across the warp as compensated
-// pairs, across the block in FP64, and one warp per slot folds the block
+// pairs, across the block in FP64, and the last block folds the block
 // partials in a fixed order, so the result is deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kDiagBlock = 128;
@@ -224,20 +225,25 @@ struct CSum {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kDiagBlock, 3)
-    k_diag(const T* __restrict__ src, StepArgs a, int zc,
+__global__ void __launch_bounds__(kDiagBlock, 4)
+    k_diag(const T* __restrict__ src, StepArgs a, int zc, unsigned units,
            double* __restrict__ part, unsigned* __restrict__ done,
            const int* __restrict__ flags, double steps, double* __restrict__ out) {
-  CSum sR[19], sB[19];     // per-direction sums of the pulled values
+  CSum sT[19];             // per-direction sums of f_i^R + f_i^B (both added)
+  CSum sRed;               // sum of every red value
   CSum cx, cy, cz;         // red-mass moments
   unsigned n_nonfinite = 0, n_negative = 0, n_red = 0, n_colour_negative = 0;
   float u2max = 0.f;
   const unsigned nx = (unsigned)a.nx, cols = nx * (unsigned)a.ny;
-  const int z0 = blockIdx.y * zc;
-  const int z1 = min(a.nz, z0 + zc);
+  const unsigned col_blocks = (cols + kDiagBlock - 1) / kDiagBlock;
   const auto* pairs = reinterpret_cast<const typename Store<T>::Pair*>(src);
-  for (unsigned col = blockIdx.x * kDiagBlock + threadIdx.x; col < cols;
-       col += gridDim.x * kDiagBlock) {
+  // work unit = (column block, z range); the blocks of one wave take the
+  // same z range of neighbouring columns
+  for (unsigned u = blockIdx.x; u < units; u += gridDim.x) {
+    const unsigned col = (u % col_blocks) * kDiagBlock + threadIdx.x;
+    const int z0 = (int)(u / col_blocks) * zc;
+    const int z1 = min(a.nz, z0 + zc);
+    if (col >= cols) continue;
     const unsigned y = col / nx, x = col - y * nx;
     const ColOff co = col_off(a, (int)x, (int)y);
     CSum colR, colZ;
@@ -248,8 +254,9 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
       float bad = 0.f;
 #pragma unroll
       for (int i = 0; i < 19; ++i) {
-        sR[i].add(fR[i]);
-        sB[i].add(fB[i]);
+        sT[i].add(fR[i]);
+        sT[i].add(fB[i]);
+        sRed.add(fR[i]);
         bad = fmaf(fR[i], 0.f, bad);
         bad = fmaf(fB[i], 0.f, bad);
       }
@@ -268,15 +275,16 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
     cy.add_scaled((float)y, colR);
     cz.merge(colZ);
   }
-  CSum mR, mB, jx, jy, jz;
+  // blue mass = all values - red values, both as compensated pairs
+  CSum mR = sRed, mB, jx, jy, jz;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    mR.merge(sR[i]);
-    mB.merge(sB[i]);
-    if (ex(i)) { jx.merge(sR[i], (float)ex(i)); jx.merge(sB[i], (float)ex(i)); }
-    if (ey(i)) { jy.merge(sR[i], (float)ey(i)); jy.merge(sB[i], (float)ey(i)); }
-    if (ez(i)) { jz.merge(sR[i], (float)ez(i)); jz.merge(sB[i], (float)ez(i)); }
+    mB.merge(sT[i]);
+    if (ex(i)) jx.merge(sT[i], (float)ex(i));
+    if (ey(i)) jy.merge(sT[i], (float)ey(i));
+    if (ez(i)) jz.merge(sT[i], (float)ez(i));
   }
+  mB.merge(sRed, -1.f);
   CSum* sums[8] = {&mR, &mB, &jx, &jy, &jz, &cx, &cy, &cz};
 #pragma unroll
   for (int k = 0; k < 8; ++k) sums[k]->warp_fold();
@@ -311,33 +319,45 @@ __global__ void __launch_bounds__(kDiagBlock, 3)
     double v = 0.0;
     for (int w = 0; w < kDiagBlock / 32; ++w)
       v = (s == 7) ? fmax(v, sh[w][s]) : v + sh[w][s];
-    part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kDiagSlots + s] = v;
+    part[(size_t)blockIdx.x * kDiagSlots + s] = v;
     __threadfence();
   }
-  // The last block to finish folds every block's partials: one warp per
-  // slot, lanes striding over the blocks, then a fixed shuffle tree, so the
-  // order does not depend on which block came last.  It writes the 16
-  // result slots (centroid divided by the red mass, the step count, the
-  // step kernels' error word) and re-arms the counter.
+  // The last block to finish folds every block's partials: thread t takes
+  // the blocks t, t + 128, ... (all slots of a block at once, so its loads
+  // are independent), then a fixed shuffle tree and a fixed sum over the
+  // warps: the order does not depend on which block came last.  It writes
+  // the 16 result slots (centroid divided by the red mass, the step count,
+  // the step kernels' error word) and re-arms the counter.
   __shared__ bool last;
-  __shared__ double fin[kDiagSlots];
   __syncthreads();
-  const unsigned nb = gridDim.x * gridDim.y;
+  const unsigned nb = gridDim.x;
   if (threadIdx.x == 0) last = atomicAdd(done, 1u) == nb - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int s = wid; s < kDiagSlots; s += kDiagBlock / 32) {
-    double v = 0.0;
-    for (unsigned b = lane; b < nb; b += 32) {
-      const double p = __ldcg(part + (size_t)b * kDiagSlots + s);
-      v = (s == 7) ? fmax(v, p) : v + p;
-    }
-    v = (s == 7) ? warp_max(v) : warp_sum(v);
-    if (lane == 0) fin[s] = v;
+  double fold[kDiagSlots];
+#pragma unroll
+  for (int k = 0; k < kDiagSlots; ++k) fold[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < nb; b += kDiagBlock) {
+    double p[kDiagSlots];
+#pragma unroll
+    for (int k = 0; k < kDiagSlots; ++k) p[k] = __ldcg(part + (size_t)b * kDiagSlots + k);
+#pragma unroll
+    for (int k = 0; k < kDiagSlots; ++k) fold[k] = (k == 7) ? fmax(fold[k], p[k]) : fold[k] + p[k];
+  }
+#pragma unroll
+  for (int k = 0; k < kDiagSlots; ++k) {
+    const double v = (k == 7) ? warp_max(fold[k]) : warp_sum(fold[k]);
+    if (lane == 0) sh[wid][k] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    double fin[kDiagSlots];
+    for (int k = 0; k < kDiagSlots; ++k) {
+      fin[k] = 0.0;
+      for (int w = 0; w < kDiagBlock / 32; ++w)
+        fin[k] = (k == 7) ? fmax(fin[k], sh[w][k]) : fin[k] + sh[w][k];
+    }
     for (int k = 0; k < 12; ++k) out[k] = fin[k];
     if (fin[0] > 0.0)
       for (int k = 9; k < 12; ++k) out[k] = fin[k] / fin[0];
@@ -465,22 +485,36 @@ cudaError_t launch_footprint_t(const void* src, const StepArgs& a, int axis, int
   k_footprint<T><<<blocks, kAuxBlock, 0, s>>>((const T*)src, a, axis, index, count);
   return cudaGetLastError();
 }
-// Grid of the diagnostics: column blocks (x) times z ranges (y), at most
-// max_blocks blocks in all (the partials scratch holds that many).
+// Grid of the diagnostics: work units of one column block x one z range,
+// taken in turn by at most max_blocks blocks (the partials scratch holds
+// that many; max_blocks is the number resident at once).  The z split
+// minimises rounds x planes per unit, rounds = units / blocks rounded up,
+// so that no block walks a whole extra column while the others idle.
 template <typename T>
 cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
                           int max_blocks, unsigned* done, const int* flags,
                           long long steps, double* out, cudaStream_t s) {
   const long long cols = (long long)a.nx * a.ny;
   const long long cb = (cols + kDiagBlock - 1) / kDiagBlock;
-  const int gx = (int)(cb < max_blocks ? cb : max_blocks);
-  int gy = max_blocks / gx;
-  if (gy > a.nz) gy = a.nz;
-  if (gy < 1) gy = 1;
-  const int zc = (a.nz + gy - 1) / gy;
-  gy = (a.nz + zc - 1) / zc;
-  k_diag<T><<<dim3(gx, gy), kDiagBlock, 0, s>>>((const T*)src, a, zc, part, done,
-                                                 flags, (double)steps, out);
+  long long best_zs = 1;
+  double best = -1.0;
+  for (long long zs = 1; zs <= a.nz; ++zs) {
+    const long long zc = (a.nz + zs - 1) / zs;
+    if ((zs - 1) * zc >= a.nz) continue;       // same split as a smaller zs
+    const long long units = cb * zs;
+    const long long rounds = (units + max_blocks - 1) / max_blocks;
+    const double cost = (double)rounds * ((double)zc + 0.25);
+    if (best < 0.0 || cost < best) {
+      best = cost;
+      best_zs = zs;
+    }
+  }
+  const int zc = (int)((a.nz + best_zs - 1) / best_zs);
+  const long long zs = (a.nz + zc - 1) / zc;
+  const long long units = cb * zs;
+  const int blocks = (int)(units < max_blocks ? units : max_blocks);
+  k_diag<T><<<blocks, kDiagBlock, 0, s>>>((const T*)src, a, zc, (unsigned)units, part,
+                                          done, flags, (double)steps, out);
   return cudaGetLastError();
 }
 template <typename T>

@@ -255,7 +255,7 @@ _E = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1
 
 @pytest.mark.parametrize("shape,wall,storage,steps", [
     ((40, 24, 16), (0, 0, 1), "f32", 50),      # z walls, several z ranges per column
-    ((256, 256, 4), (0, 0, 0), "f32", 3),      # more columns than threads: strided
+    ((256, 256, 4), (0, 0, 0), "f32", 3),      # more work units than blocks: each block takes several
     ((36, 20, 12), (1, 1, 0), "f16", 20),      # x and y walls, 16-bit storage
 ])
 def test_every_diagnostics_slot_against_fp64_sums(shape, wall, storage, steps):
