@@ -61,7 +61,13 @@ class OracleParams(ctypes.Structure):
         ("eq18_coef", ctypes.c_double),
         ("wetting", ctypes.c_int), ("pad2_", ctypes.c_int),
         ("contact_angle_deg", ctypes.c_double),
+        ("collision", ctypes.c_int), ("pad3_", ctypes.c_int),
     ]
+
+
+# Collision operators: the MRT form (Eq. 40-44, perturbation by Eq. 53) and
+# the BGK form with the correction term (Eq. 20, perturbation divided by tau).
+COLLISION = {"mrt": 0, "bgk": 1}
 
 
 # Coefficient of the high-order term of Eq. 18.  As printed it is 3/2; the
@@ -75,7 +81,7 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
            tau_B=1.0, tau_e=1.0, tau_q=1.0, tau_pi=1.0, A_R=0.0, A_B=0.0,
            beta=0.7, delta=0.98, force=(0.0, 0.0, 0.0),
            gravity=(0.0, 0.0, 0.0), eq18_coef=EQ18_COEF, wetting=False,
-           contact_angle_deg=90.0) -> OracleParams:
+           contact_angle_deg=90.0, collision="mrt") -> OracleParams:
     p = OracleParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):
@@ -92,6 +98,7 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
     p.eq18_coef = float(eq18_coef)
     p.wetting = 1 if wetting else 0
     p.contact_angle_deg = float(contact_angle_deg)
+    p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
     return p
 
 

@@ -38,6 +38,15 @@
  *     Eq. 49 stencil a neighbour beyond a wall takes the centre-cell value.
  *   - |grad rho^N| < 1e-12: perturbation and recolouring cosine are zero;
  *     cos(phi_0) = 0 for the rest direction.
+ *   - BGK variant (collision = 1): Eq. 20 in velocity space with
+ *     tau = tau_v of Eq. 52, the correction G^k = M^-1 C^k (the paper obtains
+ *     the correction from its moments, C^k = M G^k) and the Guo force term
+ *     both under the factor (1 - 1/(2 tau)), and the perturbation of Eq. 8
+ *     divided by tau (the treatment that makes the surface tension
+ *     independent of tau, of which Eq. 53 is the MRT form).  The paper
+ *     states that Eq. 40 reduces to Eq. 20 for Lambda = I / tau; this
+ *     branch is written without M, S or Lambda so that the two check each
+ *     other.
  *   - Wetting (optional; the paper uses only the neutral wall, theta = 90
  *     degrees): at a fluid cell next to a wall the colour gradient keeps its
  *     magnitude and its direction along the wall but is turned to make the
@@ -433,16 +442,28 @@ int or_step(const or_params *p, const double *f_in, double *f_out,
             for (int a = 0; a < 3; ++a) Fk[a] = (rk[k] / rho) * Ftot[a];
             or_force_guo(Fk, u, Fi);
             matvec(M, Fi, Fhat);
-            /* Eq. 41 (with the forcing term beside the correction). */
-            for (int r = 0; r < 19; ++r)
-              mbar[r] = -s[r] * (mk[r] - meq[r]) +
-                        (1.0 - 0.5 * s[r]) * (Ck[r] + Fhat[r]);
-            matvec(Minv, mbar, om1); /* Eq. 42 */
-            /* Eq. 8 then Eq. 53: Lambda = M^-1 S M applied to Omega2. */
-            or_perturbation(Acoef[k], grad, om2);
-            matvec(M, om2, om2m);
-            for (int r = 0; r < 19; ++r) sm[r] = s[r] * om2m[r];
-            matvec(Minv, sm, om2new);
+            or_perturbation(Acoef[k], grad, om2); /* Eq. 8 */
+            if (p->collision == 1) {
+              /* Eq. 20 (BGK), velocity space: relaxation to f^eq at rate
+                 1/tau, correction and force under (1 - 1/(2 tau)); the
+                 perturbation divided by tau. */
+              double Gk[19];
+              matvec(Minv, Ck, Gk);
+              for (int i = 0; i < 19; ++i) {
+                om1[i] = -(fk[i] - feq[i]) / tv + (1.0 - 0.5 / tv) * (Gk[i] + Fi[i]);
+                om2new[i] = om2[i] / tv;
+              }
+            } else {
+              /* Eq. 41 (with the forcing term beside the correction). */
+              for (int r = 0; r < 19; ++r)
+                mbar[r] = -s[r] * (mk[r] - meq[r]) +
+                          (1.0 - 0.5 * s[r]) * (Ck[r] + Fhat[r]);
+              matvec(Minv, mbar, om1); /* Eq. 42 */
+              /* Eq. 53: Lambda = M^-1 S M applied to Omega2. */
+              matvec(M, om2, om2m);
+              for (int r = 0; r < 19; ++r) sm[r] = s[r] * om2m[r];
+              matvec(Minv, sm, om2new);
+            }
             /* Eq. 12, summed over colours. */
             for (int i = 0; i < 19; ++i) fstar[i] += fk[i] + om1[i] + om2new[i];
           }

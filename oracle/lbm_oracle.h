@@ -31,6 +31,10 @@ typedef struct {
   int wetting;               /* 1: contact-angle rule at wall-adjacent cells */
   int pad2_;
   double contact_angle_deg;  /* theta, measured through the red phase */
+  int collision;      /* 0: MRT (Eq. 40-44, 53); 1: BGK with the correction
+                         term (Eq. 20) and the perturbation scaled by 1/tau
+                         (the treatment above Eq. 53), tau = tau_v of Eq. 52 */
+  int pad3_;
 } or_params;
 
 void or_matrix_M(double *M);

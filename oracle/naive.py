@@ -11,6 +11,9 @@ the two check each other:
     collision matrix Lambda = M^-1 S M formed per cell; the correction term is
     G^k = M^-1 C^k (Eq. 45) and the perturbation uses Eq. 53 as Lambda Omega2;
   * streaming uses ``numpy.roll`` plus explicit halfway bounce-back.
+With ``collision="bgk"`` the collision matrix is Lambda = I / tau_v, which
+the paper states turns Eq. 40 into Eq. 20, and Eq. 53 into the perturbation
+divided by tau.
 
 It is vectorised over cells and intended for lattices of a few hundred cells.
 The readings it takes are the same as the C oracle's (see its header).
@@ -144,9 +147,13 @@ def step(pd: dict, f: np.ndarray, nsteps: int = 1) -> np.ndarray:
         s[5:10] = 1.0 / tv[None]
         s[10:16] = 1.0 / tau_q
         s[16:19] = 1.0 / tau_pi
-        # Lambda = M^-1 S M per cell, as (cells, 19, 19)
-        sc = s.reshape(19, -1).T
-        Lam = np.einsum("ir,cr,rj->cij", MINV, sc, M)
+        if pd.get("collision", "mrt") == "bgk":
+            # Lambda = I / tau_v per cell (Eq. 20)
+            Lam = np.einsum("c,ij->cij", 1.0 / tv.reshape(-1), np.eye(19))
+        else:
+            # Lambda = M^-1 S M per cell, as (cells, 19, 19)
+            sc = s.reshape(19, -1).T
+            Lam = np.einsum("ir,cr,rj->cij", MINV, sc, M)
         fstar = np.zeros((19,) + shp)
         for k in range(2):
             cs2 = 0.5 * (1 - alpha[k])

@@ -107,6 +107,63 @@ def test_single_phase_bgk_tau_one_is_textbook_streaming_of_equilibrium():
     assert np.all(g[1] == 0.0)
 
 
+# ---- BGK variant with the correction term (Eq. 20) -------------------------
+
+@pytest.mark.parametrize("wall", [(0, 0, 0), (1, 0, 1)])
+@pytest.mark.parametrize("improved", [True, False])
+def test_bgk_equals_mrt_with_every_rate_equal(wall, improved):
+    """The paper: Eq. 40 with Lambda = I / tau is Eq. 20, and Eq. 53 the
+    perturbation divided by tau.  The C oracle's BGK branch (velocity space,
+    no M, S or Lambda in the relaxation) against its MRT branch (moment
+    space) with tau_e = tau_q = tau_pi = tau_R = tau_B: same total f*, so the
+    same step, with force, gravity, surface tension and walls."""
+    tau = 0.87
+    pd = _pd(5, 6, 4, wall=wall, improved=improved, tau_R=tau, tau_B=tau, tau_e=tau,
+             tau_q=tau, tau_pi=tau)
+    rR, rB, u = wl.random_fields(5, 6, 4, seed=3)
+    p_mrt = oracle.params_from(pd)
+    f = oracle.init(p_mrt, rR, rB, u)
+    f = f * (1 + 0.05 * np.random.default_rng(8).uniform(-1, 1, f.shape))
+    a = oracle.step(p_mrt, f, 3)
+    b = oracle.step(oracle.params_from(dict(pd, collision="bgk")), f, 3)
+    assert np.abs(a - b).max() < 1e-13
+    # and the rates do matter: a different tau_q changes the MRT step
+    c = oracle.step(oracle.params_from(dict(pd, tau_q=1.2)), f, 3)
+    assert np.abs(a - c).max() > 1e-6
+
+
+@pytest.mark.parametrize("wall", [(0, 0, 0), (0, 1, 1), (1, 1, 1)])
+def test_bgk_c_oracle_matches_numpy_restatement(wall):
+    """Variable tau_v (Eq. 52 across the interface): the C branch against
+    the numpy one with Lambda = I / tau_v per cell."""
+    pd = _pd(5, 4, 6, wall=wall, collision="bgk")
+    p = oracle.params_from(pd)
+    rR, rB, u = wl.random_fields(5, 4, 6, seed=21)
+    f = oracle.init(p, rR, rB, u)
+    f = f * (1 + 0.05 * np.random.default_rng(6).uniform(-1, 1, f.shape))
+    assert np.abs(oracle.step(p, f, 3) - naive.step(pd, f, 3)).max() < 1e-13
+
+
+def test_bgk_tau_one_is_textbook_streaming_of_equilibrium():
+    """The BGK branch alone, at tau = 1 with one colour and alpha = 1/3:
+    f_i(x + e_i, t + 1) = rho omega_i (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u^2)."""
+    nx, ny, nz = 4, 3, 5
+    pd = _pd(nx, ny, nz, alpha_R=1 / 3, alpha_B=1 / 3, tau_R=1, tau_B=1, A_R=0, A_B=0,
+             beta=0, force=(0, 0, 0), gravity=(0, 0, 0), rho_in_R=1.0, rho_in_B=1.0,
+             collision="bgk")
+    f = wl.random_populations(nx, ny, nz, seed=12)
+    f[1] = 0.0
+    g = oracle.step(oracle.params_from(pd), f, 1)
+    rho = f[0].sum(axis=0)
+    u = np.einsum("ia,izyx->azyx", E, f[0]) / rho
+    for i in range(19):
+        eu = np.einsum("a,azyx->zyx", E[i], u)
+        feq = rho * naive.W[i] * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u ** 2).sum(0))
+        moved = np.roll(feq, shift=(int(E[i, 2]), int(E[i, 1]), int(E[i, 0])),
+                        axis=(0, 1, 2))
+        assert np.allclose(g[0, i], moved, atol=1e-15)
+
+
 def test_poiseuille_is_exact_at_the_trt_magic_parameter():
     """Single phase, halfway bounce-back walls at y = -1/2 and ny - 1/2,
     uniform force G: with (tau_v - 1/2)(tau_q - 1/2) = 3/16 and
