@@ -64,6 +64,18 @@ typedef enum {
                              flux written to a scratch field, then collision */
 } lbm_kernel;
 
+typedef enum {
+  LBM_COLLISION_MRT = 0, /* the paper's MRT operator: Eq. 40-44 with tau_e,
+                            tau_q, tau_pi and the variable tau_v of Eq. 52,
+                            perturbation by Eq. 53                           */
+  LBM_COLLISION_BGK = 1  /* BGK with the correction term, Eq. 20: every
+                            non-conserved moment relaxes at 1 / tau_v of Eq. 52
+                            (tau_e, tau_q, tau_pi unused), the correction and
+                            force under (1 - 1/(2 tau_v)), the Eq. 8
+                            perturbation divided by tau_v -- Lambda = I / tau_v
+                            in Eq. 40 and 53, as the paper notes            */
+} lbm_collision;
+
 /* Model and lattice parameters.  Defaults used by the paper are in
    brackets; see the cited equations for meaning. */
 typedef struct {
@@ -99,6 +111,8 @@ typedef struct {
                           storage (ignored for LBM_F32): colour k is stored as
                           f_i^k - ref_k * phi_i^k                            */
   double contact_angle_deg; /* theta in (0, 180) when wetting = 1            */
+  int collision;       /* lbm_collision [LBM_COLLISION_MRT]                  */
+  int reserved;        /* 0                                                  */
 } lbm_params;
 
 /* Creates a context: validates p, allocates the two population buffers and

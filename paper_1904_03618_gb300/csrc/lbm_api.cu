@@ -104,6 +104,8 @@ static lbm_status validate(const lbm_params* p) {
     return fail(nullptr, LBM_ERR_ARG, "kernel must be LBM_KERNEL_FUSED or LBM_KERNEL_TWO_PASS");
   if (p->wetting != 0 && p->wetting != 1)
     return fail(nullptr, LBM_ERR_ARG, "wetting must be 0 or 1");
+  if (p->collision != LBM_COLLISION_MRT && p->collision != LBM_COLLISION_BGK)
+    return fail(nullptr, LBM_ERR_ARG, "collision must be LBM_COLLISION_MRT or LBM_COLLISION_BGK");
   if (p->wetting && !(p->contact_angle_deg > 0 && p->contact_angle_deg < 180))
     return fail(nullptr, LBM_ERR_ARG, "contact_angle_deg must lie in (0, 180)");
   if (!(p->rho_in_R > 0) || !(p->rho_in_B > 0))
@@ -144,6 +146,7 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
   a.wz = p->wall[2];
   a.plane = plane;
   a.improved = p->improved;
+  a.bgk = p->collision == LBM_COLLISION_BGK ? 1 : 0;
   a.inv_rin_R = (float)(1.0 / p->rho_in_R);
   a.inv_rin_B = (float)(1.0 / p->rho_in_B);
   double csR = 0.5 * (1.0 - p->alpha_R), csB = 0.5 * (1.0 - p->alpha_B);
@@ -278,8 +281,10 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
       }
       return st;
     }
-    if (ps[k].storage != ps[0].storage || ps[k].kernel != ps[0].kernel)
-      return fail(nullptr, LBM_ERR_ARG, "all cases of a batch need the same storage and kernel");
+    if (ps[k].storage != ps[0].storage || ps[k].kernel != ps[0].kernel ||
+        ps[k].collision != ps[0].collision)
+      return fail(nullptr, LBM_ERR_ARG,
+                  "all cases of a batch need the same storage, kernel and collision");
   }
   if (ncases > 1 && ps[0].kernel != LBM_KERNEL_FUSED)
     return fail(nullptr, LBM_ERR_ARG, "batches run the fused kernel only");
@@ -521,8 +526,8 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
             : cudaErrorInvalidValue;
   } else if (c->ncases > 1)
     e = lbm::launch_fused_batch(c->storage, src, dst, c->d_cases, c->ncases,
-                                c->total_items, c->any_walls, c->fused, c->sms,
-                                c->stream);
+                                c->total_items, c->any_walls, c->cases[0].args.bgk != 0,
+                                c->fused, c->sms, c->stream);
   else if (c->kernel == LBM_KERNEL_TWO_PASS)
     e = lbm::launch_twopass(c->storage, src, dst, c->cases[0].args, c->phase, c->stream);
   else if (c->fused.hold == 7 || c->fused.hold == 8) {
@@ -827,6 +832,9 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
       (c->ncases > 1
            ? lbm::valid_batch_config(f) && ((hold != 7 && hold != 8) || batch_tma)
            : lbm::valid_fused_config(f, c->storage) && ((hold != 7 && hold != 8) || single_tma));
+  if (ok && c->cases[0].args.bgk && (f.tile_y != 8 || f.hold != 2))
+    return fail(c, LBM_ERR_ARG,
+                "the BGK operator runs the shared-memory-hold form only (tile_y 8, hold 2)");
   if (!ok)
     return fail(c, LBM_ERR_ARG,
                 c->ncases > 1

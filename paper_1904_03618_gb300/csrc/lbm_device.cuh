@@ -33,7 +33,7 @@ struct StepArgs {
   int wx, wy, wz;           // wall flags per axis
   long long plane;          // elements per (colour, direction) plane
   int improved;
-  int pad0;
+  int bgk;                      // 1: every non-conserved rate is 1 / tau_v (Eq. 20)
   float inv_rin_R, inv_rin_B;   // 1 / rho_k^in (below Eq. 8)
   float cs2_R, cs2_B;           // (c_s^k)^2 = (1 - alpha_k) / 2 (Eq. 13)
   float q_R, q_B;               // 1 - 3 (c_s^k)^2 (below Eq. 49)
@@ -407,6 +407,10 @@ __device__ __forceinline__ float recolour_seg(const Recolour& rc) {
 // grad = grad rho^N and Q = (d_x Qbar_x, d_y Qbar_y, d_z Qbar_z), both from
 // the Eq. 49 stencil.
 // ---------------------------------------------------------------------------
+// BGK: the operator of Eq. 20 (Lambda = I / tau_v), a compile-time choice:
+// in the MRT form the rates of rows 4 and 10-18 are launch constants, so
+// their relaxation does not wait for tau_v.
+template <bool BGK = false>
 __device__ __forceinline__ Recolour collide_total(const StepArgs& a, float* f,
                                                   const Macro& mc, float rhoN,
                                                   float Gx, float Gy, float Gz,
@@ -510,9 +514,13 @@ __device__ __forceinline__ Recolour collide_total(const StepArgs& a, float* f,
     P18 = -k19 * Gx2;
   }
 
-  // relaxation rates (Eq. 44) with the variable tau_v of Eq. 52
+  // relaxation rates (Eq. 44) with the variable tau_v of Eq. 52; the BGK
+  // operator of Eq. 20 is Lambda = I / tau_v, every rate 1 / tau_v (the
+  // conserved rows carry only F, whatever their rate)
   const float s_v = fast_rcp(tau_v_of(a, rhoN));
-  const float s_e = a.s_e, s_q = a.s_q, s_pi = a.s_pi;
+  const float s_e = BGK ? s_v : a.s_e;
+  const float s_q = BGK ? s_v : a.s_q;
+  const float s_pi = BGK ? s_v : a.s_pi;
 
   // change of moments dm = m* - m (rows 1-3: F; row 0: 0)
   float d[19];
@@ -610,6 +618,7 @@ struct RecolourAll<19> {
 // Collision + perturbation + recolouring of one cell given both colours.  On
 // entry fR, fB hold the pulled populations; on exit the post-recolouring
 // f^{k,+}.
+template <bool BGK = false>
 __device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
                                              float* fB, const Macro& mc,
                                              float rhoN, float Gx, float Gy,
@@ -618,7 +627,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, float* fR,
   float f[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) f[i] = fR[i] + fB[i];
-  const Recolour rc = collide_total(a, f, mc, rhoN, Gx, Gy, Gz, Qx, Qy, Qz);
+  const Recolour rc = collide_total<BGK>(a, f, mc, rhoN, Gx, Gy, Gz, Qx, Qy, Qz);
   RecolourAll<0>::run(rc, f, fR, fB);
 }
 

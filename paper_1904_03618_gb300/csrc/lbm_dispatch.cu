@@ -16,12 +16,12 @@ cudaError_t launch_fused(int storage, const void* src, void* dst,
 
 cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
                                const BatchCase* cases, int ncases,
-                               int total_items, bool walls,
+                               int total_items, bool walls, bool bgk,
                                const FusedConfig& cfg, int sms, cudaStream_t s) {
   switch (storage) {
-    case 0: return launch_fused_batch_storage<float>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
-    case 1: return launch_fused_batch_storage<__half>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
-    case 2: return launch_fused_batch_storage<__nv_bfloat16>(src, dst, cases, ncases, total_items, walls, cfg, sms, s);
+    case 0: return launch_fused_batch_storage<float>(src, dst, cases, ncases, total_items, walls, bgk, cfg, sms, s);
+    case 1: return launch_fused_batch_storage<__half>(src, dst, cases, ncases, total_items, walls, bgk, cfg, sms, s);
+    case 2: return launch_fused_batch_storage<__nv_bfloat16>(src, dst, cases, ncases, total_items, walls, bgk, cfg, sms, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -76,8 +76,10 @@ bool tma_config_fits(int storage, int kind, int ns) {
 // Pair bytes of a storage type (red and blue value of one direction and cell).
 static int pair_bytes(int storage) { return storage == 0 ? 8 : 4; }
 
+// The TMA forms are built for the MRT operator only (a BGK context runs the
+// shared-memory-hold form).
 bool tma_eligible(const StepArgs& a, int storage) {
-  return ((long long)a.nx * pair_bytes(storage)) % 16 == 0 && a.nz >= 3;
+  return ((long long)a.nx * pair_bytes(storage)) % 16 == 0 && a.nz >= 3 && !a.bgk;
 }
 
 // Default TMA configuration.  Tile: the one with more interior cells per

@@ -257,7 +257,7 @@ struct FusedSmem<BY, 2> {
 
 // MINB: CTAs per SM the register allocation must allow (launch bounds).
 // One work item of the fused step: tile (bx, by), planes [zb, ze).
-template <typename T, int BY, bool WALLS, int HOLD>
+template <typename T, int BY, bool WALLS, int HOLD, bool BGK = false>
 __device__ __forceinline__ void fused_work(const T* __restrict__ src,
                                            T* __restrict__ dst,
                                            const StepArgs& a, int bx, int by,
@@ -320,7 +320,7 @@ __device__ __forceinline__ void fused_work(const T* __restrict__ src,
       } else {
         m = macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4]);
       }
-      const Recolour rc = collide_total(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+      const Recolour rc = collide_total<BGK>(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
       store_recoloured<T>(dst, plane, a,
                           (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1], rc, cf);
     }
@@ -340,7 +340,7 @@ __device__ __forceinline__ void fused_work(const T* __restrict__ src,
   }
 }
 
-template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+template <typename T, int BY, bool WALLS, int HOLD, int MINB, bool BGK = false>
 __global__ void __launch_bounds__(kTileW* BY, MINB)
     k_fused(const T* __restrict__ src, T* __restrict__ dst,
             const __grid_constant__ StepArgs a, int zchunk) {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kTileW* BY, MINB)
   const int zb = blockIdx.z * zchunk;
   const int ze = min(zb + zchunk, a.nz);
   if (zb >= ze) return;
-  fused_work<T, BY, WALLS, HOLD>(src, dst, a, blockIdx.x, blockIdx.y, zb, ze, sm);
+  fused_work<T, BY, WALLS, HOLD, BGK>(src, dst, a, blockIdx.x, blockIdx.y, zb, ze, sm);
 }
 
 // Batched step: many independent lattices ("cases") in one launch.  The
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kTileW* BY, MINB)
 // so concurrently running CTAs work on neighbouring tiles of one chunk and
 // their ring re-reads hit L2.  The case's parameters are copied into shared
 // memory once per item.
-template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+template <typename T, int BY, bool WALLS, int HOLD, int MINB, bool BGK = false>
 __global__ void __launch_bounds__(kTileW* BY, MINB)
     k_fused_batch(const BatchCase* __restrict__ cases, int ncases,
                   int total_items, const T* __restrict__ src_base,
@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(kTileW* BY, MINB)
     const int zb = chunk * zchunk;
     const int ze = min(zb + zchunk, sa.nz);
     const size_t off = 2 * (size_t)bc.pair_base;
-    fused_work<T, BY, WALLS, HOLD>(src_base + off, dst_base + off, sa, bx, by, zb, ze, sm);
+    fused_work<T, BY, WALLS, HOLD, BGK>(src_base + off, dst_base + off, sa, bx, by, zb, ze,
+                                        sm);
   }
 }
 
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(kTileW * 8, 2)
     const Macro m = macro_held(a, h[19][row - 1][tx - 1], h[20][row - 1][tx - 1],
                                h[21][row - 1][tx - 1], h[22][row - 1][tx - 1],
                                h[23][row - 1][tx - 1]);
-    const Recolour rc = collide_total(a, f, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+    const Recolour rc = collide_total<false>(a, f, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
     store_recoloured<T>(dst, plane, a, (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1],
                         rc, f);
   };
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(kTileW* kAsyncBY, 2)
       for (int i = 0; i < 19; ++i) f[i] = h[i * hs];
       const Macro m = macro_held(a, h[19 * hs], h[20 * hs], h[21 * hs], h[22 * hs],
                                  h[23 * hs]);
-      const Recolour rc = collide_total(a, f, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+      const Recolour rc = collide_total<false>(a, f, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
       store_recoloured<T>(dst, plane, a,
                           (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1], rc, f);
     }
@@ -579,13 +580,13 @@ __global__ void __launch_bounds__(kTileW* kAsyncBY, 2)
 }
 
 template <typename T, int BY, bool WALLS, int HOLD,
-          int MINB = (BY == 8 && HOLD != 1) ? 2 : 1>
+          int MINB = (BY == 8 && HOLD != 1) ? 2 : 1, bool BGK = false>
 static cudaError_t launch_fused_v(const void* src, void* dst,
                                   const StepArgs& a, int zc, cudaStream_t s) {
   dim3 blk(kTileW, BY);
   dim3 grd((a.nx + kTileW - 3) / (kTileW - 2), (a.ny + BY - 3) / (BY - 2),
            (a.nz + zc - 1) / zc);
-  k_fused<T, BY, WALLS, HOLD, MINB><<<grd, blk, 0, s>>>((const T*)src, (T*)dst, a, zc);
+  k_fused<T, BY, WALLS, HOLD, MINB, BGK><<<grd, blk, 0, s>>>((const T*)src, (T*)dst, a, zc);
   return cudaGetLastError();
 }
 
@@ -653,7 +654,7 @@ static cudaError_t launch_fused_h(const void* src, void* dst,
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int BY, bool WALLS, int HOLD, int MINB>
+template <typename T, int BY, bool WALLS, int HOLD, int MINB, bool BGK = false>
 static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* cases,
                                   int ncases, int total_items, int zc, int sms,
                                   cudaStream_t s) {
@@ -661,12 +662,12 @@ static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* c
   if (per_sm == 0) {
     int q = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &q, k_fused_batch<T, BY, WALLS, HOLD, MINB>, kTileW * BY, 0);
+        &q, k_fused_batch<T, BY, WALLS, HOLD, MINB, BGK>, kTileW * BY, 0);
     if (e != cudaSuccess) return e;
     per_sm = q < 1 ? 1 : q;
   }
   const int grid = min(total_items, sms * per_sm);
-  k_fused_batch<T, BY, WALLS, HOLD, MINB><<<grid, dim3(kTileW, BY), 0, s>>>(
+  k_fused_batch<T, BY, WALLS, HOLD, MINB, BGK><<<grid, dim3(kTileW, BY), 0, s>>>(
       cases, ncases, total_items, (const T*)src, (T*)dst, zc);
   return cudaGetLastError();
 }
@@ -674,10 +675,15 @@ static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* c
 template <typename T>
 cudaError_t launch_fused_batch_storage(const void* src, void* dst,
                                        const BatchCase* cases, int ncases,
-                                       int total_items, bool walls,
+                                       int total_items, bool walls, bool bgk,
                                        const FusedConfig& cfg, int sms,
                                        cudaStream_t s) {
   const int zc = cfg.zchunk;
+  if (bgk) {  // the BGK operator runs the shared-memory-hold form only
+    if (cfg.tile_y != 8 || cfg.hold != 2) return cudaErrorInvalidValue;
+    return walls ? launch_batch_v<T, 8, true, 2, 2, true>(src, dst, cases, ncases, total_items, zc, sms, s)
+                 : launch_batch_v<T, 8, false, 2, 2, true>(src, dst, cases, ncases, total_items, zc, sms, s);
+  }
   if (cfg.tile_y == 8 && cfg.hold == 2)
     return walls ? launch_batch_v<T, 8, true, 2, 2>(src, dst, cases, ncases, total_items, zc, sms, s)
                  : launch_batch_v<T, 8, false, 2, 2>(src, dst, cases, ncases, total_items, zc, sms, s);
@@ -696,6 +702,11 @@ cudaError_t launch_fused_storage(const void* src, void* dst,
                                  cudaStream_t s) {
   const int zc = cfg.zchunk > 0 ? cfg.zchunk : a.nz;
   const bool walls = a.wx || a.wy || a.wz;
+  if (a.bgk) {  // the BGK operator runs the shared-memory-hold form only
+    if (cfg.tile_y != 8 || cfg.hold != 2) return cudaErrorInvalidValue;
+    return walls ? launch_fused_v<T, 8, true, 2, 2, true>(src, dst, a, zc, s)
+                 : launch_fused_v<T, 8, false, 2, 2, true>(src, dst, a, zc, s);
+  }
   if (cfg.tile_y == 8)
     return walls ? launch_fused_h<T, 8, true>(src, dst, a, cfg, zc, s)
                  : launch_fused_h<T, 8, false>(src, dst, a, cfg, zc, s);

@@ -9,6 +9,6 @@ template cudaError_t launch_fused_storage<__half>(const void*, void*,
                                               cudaStream_t);
 template cudaError_t launch_fused_batch_storage<__half>(const void*, void*,
                                                     const BatchCase*, int, int,
-                                                    bool, const FusedConfig&, int,
+                                                    bool, bool, const FusedConfig&, int,
                                                     cudaStream_t);
 }  // namespace lbm

@@ -365,7 +365,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
         wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
       const Macro m = HV == 24 ? macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4])
                                : macro_total(a, cf, ch[0], ch[1]);
-      const Recolour rc = collide_total(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+      const Recolour rc = collide_total<false>(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
       store_recoloured<T>(dst, plane, a, (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1],
                           rc, cf);
 #pragma unroll

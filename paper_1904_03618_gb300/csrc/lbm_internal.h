@@ -103,12 +103,13 @@ struct BatchCase {
 template <typename T>
 cudaError_t launch_fused_batch_storage(const void* src, void* dst,
                                        const BatchCase* cases, int ncases,
-                                       int total_items, bool walls,
+                                       int total_items, bool walls, bool bgk,
                                        const FusedConfig& cfg, int sms,
                                        cudaStream_t s);
+// bgk: every case uses the BGK operator (the (8, hold 2) form only)
 cudaError_t launch_fused_batch(int storage, const void* src, void* dst,
                                const BatchCase* cases, int ncases,
-                               int total_items, bool walls,
+                               int total_items, bool walls, bool bgk,
                                const FusedConfig& cfg, int sms, cudaStream_t s);
 // Batched TMA step (kind 0 or 2): maps = the device table of the source
 // buffer's tensor maps, two per case.

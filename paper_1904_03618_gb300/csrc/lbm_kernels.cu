@@ -402,7 +402,7 @@ __device__ __forceinline__ unsigned stencil_cell(const StepArgs& a, int x,
          (unsigned)wrap1(xn, a.nx);
 }
 
-template <typename T>
+template <typename T, bool BGK>
 __global__ void __launch_bounds__(256)
     k_twopass_collide(const T* __restrict__ src, T* __restrict__ dst,
                       StepArgs a, const float4* __restrict__ mom) {
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256)
     wetting_rule(a, a.wx && x == 0, a.wx && x == a.nx - 1, a.wy && y == 0,
                  a.wy && y == a.ny - 1, a.wz && z == 0, a.wz && z == a.nz - 1, Gx, Gy, Gz);
   const float rn = __ldg(&mom[c]).x;
-  collide_cell(a, fR, fB, m, rn, Gx, Gy, Gz, Qx, Qy, Qz);
+  collide_cell<BGK>(a, fR, fB, m, rn, Gx, Gy, Gz, Qx, Qy, Qz);
   store_cell<T>(dst, a, c, fR, fB);
 }
 
@@ -534,7 +534,10 @@ cudaError_t launch_twopass_t(const void* src, void* dst, const StepArgs& a,
   k_twopass_phase<T><<<grd, blk, 0, s>>>((const T*)src, a, mom);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_twopass_collide<T><<<grd, blk, 0, s>>>((const T*)src, (T*)dst, a, mom);
+  if (a.bgk)
+    k_twopass_collide<T, true><<<grd, blk, 0, s>>>((const T*)src, (T*)dst, a, mom);
+  else
+    k_twopass_collide<T, false><<<grd, blk, 0, s>>>((const T*)src, (T*)dst, a, mom);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ __device__ __forceinline__ long long neighbour(const StepArgs& a, int x, int y,
 // Collision pass: Eq. 49 gradients from the phase field, collision,
 // perturbation and recolouring, then push streaming into f_out (halfway
 // bounce-back where x + e_i lies beyond a wall).
+template <bool BGK>
 __global__ void k_noalloc_collide(const float* __restrict__ f,
                                   float* __restrict__ fout, StepArgs a,
                                   const float4* __restrict__ phase) {
@@ -102,7 +103,7 @@ __global__ void k_noalloc_collide(const float* __restrict__ f,
   if (a.wetting)
     wetting_rule(a, a.wx && x == 0, a.wx && x == a.nx - 1, a.wy && y == 0,
                  a.wy && y == a.ny - 1, a.wz && z == 0, a.wz && z == a.nz - 1, Gx, Gy, Gz);
-  collide_cell(a, fR, fB, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+  collide_cell<BGK>(a, fR, fB, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const long long d = neighbour(a, x, y, z, ex(i), ey(i), ez(i), c);
@@ -166,7 +167,10 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* f_in,
   k_noalloc_phase<<<blocks, 128, 0, s>>>(f_in, a, phase);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    k_noalloc_collide<<<blocks, 128, 0, s>>>(f_in, f_out, a, phase);
+    if (a.bgk)
+      k_noalloc_collide<true><<<blocks, 128, 0, s>>>(f_in, f_out, a, phase);
+    else
+      k_noalloc_collide<false><<<blocks, 128, 0, s>>>(f_in, f_out, a, phase);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess)

@@ -33,6 +33,8 @@ LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6
 LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2
 LBM_KERNEL_FUSED, LBM_KERNEL_TWO_PASS = 0, 1
 STORAGE = {"f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+LBM_COLLISION_MRT, LBM_COLLISION_BGK = 0, 1
+COLLISION = {"mrt": LBM_COLLISION_MRT, "bgk": LBM_COLLISION_BGK}
 
 
 class LbmParams(ctypes.Structure):
@@ -52,6 +54,7 @@ class LbmParams(ctypes.Structure):
         ("force", ctypes.c_double * 3), ("gravity", ctypes.c_double * 3),
         ("ref_R", ctypes.c_double), ("ref_B", ctypes.c_double),
         ("contact_angle_deg", ctypes.c_double),
+        ("collision", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
 
 
@@ -172,7 +175,7 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
                 alpha_B=1.0 / 3.0, tau_R=1.0, tau_B=1.0, tau_e=1.0, tau_q=1.0,
                 tau_pi=1.0, A_R=0.0, A_B=0.0, beta=0.7, delta=0.98,
                 force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), ref_R=0.0,
-                ref_B=0.0, wetting=False, contact_angle_deg=90.0,
+                ref_B=0.0, wetting=False, contact_angle_deg=90.0, collision="mrt",
                 **_ignored) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -186,6 +189,7 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
         if isinstance(kernel, str) else int(kernel)
     p.wetting = 1 if wetting else 0
     p.contact_angle_deg = float(contact_angle_deg)
+    p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
     p.rho_in_R, p.rho_in_B = float(rho_in_R), float(rho_in_B)
     p.alpha_R, p.alpha_B = float(alpha_R), float(alpha_B)
     p.tau_R, p.tau_B = float(tau_R), float(tau_B)

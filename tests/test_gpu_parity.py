@@ -247,6 +247,60 @@ def test_diagnostics_and_mass_conservation():
     assert e.nx == 40
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape,wall", [((37, 19, 9), (0, 0, 1)),    # plain fused tiles
+                                        ((64, 30, 12), (1, 1, 0)),   # TMA-staged tiles
+                                        ((40, 26, 10), (0, 0, 0))])
+def test_bgk_step_matches_oracle(kernel, shape, wall):
+    """BGK with the correction term (Eq. 20), tau_v varying across the
+    interface (Eq. 52): one step within the per-step bar, and 25 steps."""
+    pd = base(*shape, wall=wall, tau_R=0.7, tau_B=1.3, collision="bgk")
+    f0 = droplet_state(pd, min(shape) / 3.0, (0.02, 0.01, 0.0))
+    p = oracle.params_from(pd)
+    assert rel_linf(gpu_run(pd, f0, 1, kernel), oracle.step(p, f0, 1)) <= 1e-5
+    assert rel_linf(gpu_run(pd, f0, 25, kernel), oracle.step(p, f0, 25)) <= 1e-4
+
+
+def test_bgk_on_the_gpu_is_mrt_with_every_rate_equal():
+    """The BGK form against the MRT form with tau_e = tau_q = tau_pi = tau_v,
+    both in the shared-memory-hold kernel: equal to FP32 rounding (the two
+    instantiations may contract their FMAs differently)."""
+    tau = 0.9
+    pd = base(48, 20, 12, wall=(0, 0, 1), tau_R=tau, tau_B=tau, tau_e=tau, tau_q=tau,
+              tau_pi=tau)
+    f0 = torch.tensor(droplet_state(pd, 5.0, (0.02, 0.0, 0.01)), dtype=torch.float32,
+                      device=DEV)
+    out = []
+    for d in (pd, dict(pd, collision="bgk")):
+        lat = lbm.Lattice(lbm.make_params(**d), device=DEV)
+        lbm.lbm_set_fused_config(lat.ctx, 8, 12, 2)
+        lat.set_f(f0)
+        lat.step(10)
+        out.append(lat.get_f().double().cpu().numpy())
+        lat.close()
+    assert rel_linf(out[1], out[0]) <= 1e-6
+    # and a BGK context refuses the forms built for MRT only
+    lat = lbm.Lattice(lbm.make_params(**dict(pd, collision="bgk")), device=DEV)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_set_fused_config(lat.ctx, 15, 12, 7)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    lat.close()
+
+
+def test_bgk_batch_matches_single_lattices():
+    cases = [base(32, 32, 32, tau_R=0.7, tau_B=1.3, collision="bgk"),
+             base(48, 48, 48, tau_R=0.9, tau_B=0.6, collision="bgk")]
+    states = [droplet_state(c, c["nx"] / 4.0, (0.02, 0.0, 0.0)) for c in cases]
+    b = lbm.Batch([lbm.make_params(**c) for c in cases], device=DEV)
+    for k, f in enumerate(states):
+        b.set_f(k, torch.tensor(f, dtype=torch.float32, device=DEV))
+    b.step(3)
+    for k, (c, f) in enumerate(zip(cases, states)):
+        ref = oracle.step(oracle.params_from(c), f, 3)
+        assert rel_linf(b.get_f(k).double().cpu().numpy(), ref) <= 3e-5
+    b.close()
+
+
 _E = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1],
                [0, 0, -1], [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1],
                [-1, 0, -1], [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1],
