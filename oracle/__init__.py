@@ -62,6 +62,7 @@ class OracleParams(ctypes.Structure):
         ("wetting", ctypes.c_int), ("pad2_", ctypes.c_int),
         ("contact_angle_deg", ctypes.c_double),
         ("collision", ctypes.c_int), ("pad3_", ctypes.c_int),
+        ("wall_u", (ctypes.c_double * 3) * 2),
     ]
 
 
@@ -81,7 +82,8 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
            tau_B=1.0, tau_e=1.0, tau_q=1.0, tau_pi=1.0, A_R=0.0, A_B=0.0,
            beta=0.7, delta=0.98, force=(0.0, 0.0, 0.0),
            gravity=(0.0, 0.0, 0.0), eq18_coef=EQ18_COEF, wetting=False,
-           contact_angle_deg=90.0, collision="mrt") -> OracleParams:
+           contact_angle_deg=90.0, collision="mrt",
+           wall_u=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0))) -> OracleParams:
     p = OracleParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):
@@ -99,6 +101,9 @@ def params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, rho_in_R=1.0,
     p.wetting = 1 if wetting else 0
     p.contact_angle_deg = float(contact_angle_deg)
     p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    for side in range(2):
+        for a in range(3):
+            p.wall_u[side][a] = float(wall_u[side][a])
     return p
 
 

@@ -47,6 +47,16 @@
  *     states that Eq. 40 reduces to Eq. 20 for Lambda = I / tau; this
  *     branch is written without M, S or Lambda so that the two check each
  *     other.
+ *   - Moving plates (wall = 2, Sec. IV.A): Zou-He velocity nodes.  The
+ *     first and last layer of the axis lie on plates moving with wall_u;
+ *     after streaming, the populations that would enter from beyond a plate
+ *     are rebuilt per colour k from the known ones: rho_k from mass and the
+ *     plate's normal velocity, the bounce-back of the non-equilibrium part
+ *     along the normal, and transverse corrections N_t that make the
+ *     colour's momentum exactly rho_k u_w (the D3Q19 form of Hecht and
+ *     Harting).  Populations leaving through a plate are dropped.  In the
+ *     Eq. 49 stencil a plate acts as a wall.  The plate velocity carries no
+ *     forcing shift (the paper's case has no body force).
  *   - Wetting (optional; the paper uses only the neutral wall, theta = 90
  *     degrees): at a fluid cell next to a wall the colour gradient keeps its
  *     magnitude and its direction along the wall but is turned to make the
@@ -350,6 +360,53 @@ static double iso_grad(const or_params *p, const double *psi, int x, int y,
   return 3.0 * s;
 }
 
+/* Zou-He velocity nodes on both faces of axis ax (wall = 2): rebuilds, per
+   colour, the populations entering from beyond each plate. */
+static void zou_he_faces(const or_params *p, double *f, long N, int ax) {
+  const int ext[3] = {p->nx, p->ny, p->nz};
+  const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+  for (int side = 0; side < 2; ++side) {
+    const int s = side == 0 ? 1 : -1; /* inward normal along ax */
+    const double *u = p->wall_u[side];
+    const double un = s * u[ax];
+    int xyz[3];
+    xyz[ax] = side == 0 ? 0 : ext[ax] - 1;
+    for (int a = 0; a < ext[t1]; ++a) {
+      for (int b = 0; b < ext[t2]; ++b) {
+        xyz[t1] = a;
+        xyz[t2] = b;
+        long c = cell_index(p, xyz[0], xyz[1], xyz[2]);
+        for (int k = 0; k < 2; ++k) {
+          double s0 = 0.0, sout = 0.0, tang[3] = {0.0, 0.0, 0.0};
+          for (int i = 0; i < 19; ++i) {
+            const int en = s * E[i][ax];
+            const double fi = f[FIDX(k, i, c)];
+            if (en == 0) {
+              s0 += fi;
+              for (int d = 0; d < 3; ++d) tang[d] += E[i][d] * fi;
+            } else if (en < 0) {
+              sout += fi;
+            }
+          }
+          const double rho = (s0 + 2.0 * sout) / (1.0 - un);
+          double Nt[3] = {0.0, 0.0, 0.0};
+          Nt[t1] = 0.5 * tang[t1] - rho * u[t1] / 3.0;
+          Nt[t2] = 0.5 * tang[t2] - rho * u[t2] / 3.0;
+          for (int i = 0; i < 19; ++i) {
+            if (s * E[i][ax] != 1) continue;
+            double eu = 0.0, corr = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              eu += E[i][d] * u[d];
+              corr += E[i][d] * Nt[d];
+            }
+            f[FIDX(k, i, c)] = f[FIDX(k, opposite(i), c)] + 6.0 * weight(i) * rho * eu - corr;
+          }
+        }
+      }
+    }
+  }
+}
+
 int or_step(const or_params *p, const double *f_in, double *f_out,
             int nsteps) {
   long N = (long)p->nx * p->ny * p->nz;
@@ -502,6 +559,9 @@ int or_step(const or_params *p, const double *f_in, double *f_out,
         }
       }
     }
+    /* Moving plates: the populations entering from beyond them. */
+    for (int ax = 0; ax < 3; ++ax)
+      if (p->wall[ax] == 2) zou_he_faces(p, nxt, N, ax);
     double *t = cur;
     cur = nxt;
     nxt = t;

@@ -15,7 +15,10 @@
 
 typedef struct {
   int nx, ny, nz;
-  int wall[3];        /* per axis: 0 periodic, 1 halfway bounce-back walls */
+  int wall[3];        /* per axis: 0 periodic, 1 halfway bounce-back walls,
+                         2 Zou-He velocity nodes (the first and last layer
+                         lie on plates moving with wall_u; the other two
+                         axes periodic) */
   int improved;       /* 1: Eq. 18 + Eq. 45 correction; 0: Eq. 6, no correction */
   int pad_;
   double rho_in_R, rho_in_B; /* rho_k^in, below Eq. 8 */
@@ -35,6 +38,7 @@ typedef struct {
                          term (Eq. 20) and the perturbation scaled by 1/tau
                          (the treatment above Eq. 53), tau = tau_v of Eq. 52 */
   int pad3_;
+  double wall_u[2][3]; /* velocity of the low and high plate of a wall = 2 axis */
 } or_params;
 
 void or_matrix_M(double *M);

@@ -14,6 +14,13 @@ the two check each other:
 With ``collision="bgk"`` the collision matrix is Lambda = I / tau_v, which
 the paper states turns Eq. 40 into Eq. 20, and Eq. 53 into the perturbation
 divided by tau.
+Moving plates (``wall`` entry 2, Zou-He velocity nodes): the five entering
+populations of each colour and the colour density are the solution of the
+six linear conditions that define the scheme -- mass, the two tangential
+momenta equal to rho_k u_t, the normal axis population bouncing back its
+non-equilibrium part (f_n - f_-n = rho_k u_n / 3), and the same for each
+pair of diagonals (their sum) -- solved with ``numpy.linalg.solve``, not
+through the closed form the C oracle uses.
 
 It is vectorised over cells and intended for lattices of a few hundred cells.
 The readings it takes are the same as the C oracle's (see its header).
@@ -210,5 +217,51 @@ def step(pd: dict, f: np.ndarray, nsteps: int = 1) -> np.ndarray:
                 idx[3 - ax] = 0 if d > 0 else n_ax - 1
                 new[(slice(None), i) + tuple(idx[1:])] = \
                     fp[(slice(None), OPP[i]) + tuple(idx[1:])]
+        for ax in range(3):
+            if wall[ax] == 2:
+                _zou_he(new, ax, pd["wall_u"])
         f = new
     return f
+
+
+def _zou_he(f, ax, wall_u):
+    """Velocity nodes on both faces of axis ax, in place (see the header)."""
+    nax = 3 - ax                     # array axis of lattice axis ax in (k, i, z, y, x)
+    t1, t2 = (ax + 1) % 3, (ax + 2) % 3
+    for side in range(2):
+        s = 1 if side == 0 else -1
+        u = np.asarray(wall_u[side], dtype=np.float64)
+        un = s * u[ax]
+        en = s * E[:, ax]
+        unk = [i for i in range(19) if en[i] == 1]
+        axis_i = [i for i in unk if E[i, t1] == 0 and E[i, t2] == 0][0]
+        A = np.zeros((6, 6))
+        A[0, :5] = 1.0
+        A[0, 5] = -1.0                                   # mass
+        for r, t in ((1, t1), (2, t2)):                  # tangential momenta
+            A[r, :5] = [E[i, t] for i in unk]
+            A[r, 5] = -u[t]
+        A[3, unk.index(axis_i)] = 1.0
+        A[3, 5] = -un / 3.0                              # normal bounce-back
+        for r, t in ((4, t1), (5, t2)):                  # diagonal pair sums
+            for i in unk:
+                if E[i, t] != 0:
+                    A[r, unk.index(i)] = 1.0
+            A[r, 5] = -un / 3.0
+        idx = [slice(None)] * 5
+        idx[2 + (2 - ax)] = 0 if side == 0 else f.shape[2 + (2 - ax)] - 1
+        face = f[tuple(idx)]                             # (2, 19, a, b)
+        known = [i for i in range(19) if en[i] != 1]
+        for k in range(2):
+            fk = face[k]
+            b = np.zeros((6,) + fk.shape[1:])
+            b[0] = -sum(fk[i] for i in known)
+            for r, t in ((1, t1), (2, t2)):
+                b[r] = -sum(E[i, t] * fk[i] for i in known)
+            b[3] = fk[OPP[axis_i]]
+            for r, t in ((4, t1), (5, t2)):
+                b[r] = sum(fk[OPP[i]] for i in unk if E[i, t] != 0)
+            sol = np.linalg.solve(A, b.reshape(6, -1)).reshape(b.shape)
+            for j, i in enumerate(unk):
+                fk[i] = sol[j]
+        f[tuple(idx)] = face

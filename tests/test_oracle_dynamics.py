@@ -164,6 +164,85 @@ def test_bgk_tau_one_is_textbook_streaming_of_equilibrium():
         assert np.allclose(g[0, i], moved, atol=1e-15)
 
 
+# ---- moving plates: Zou-He velocity nodes (Sec. IV.A) -----------------------
+
+PLATES = ((0.03, 0.01, -0.02), (-0.01, -0.005, 0.02))   # low / high plate of the axis
+
+
+def _plates_pd(ax, **kw):
+    wall = [0, 0, 0]
+    wall[ax] = 2
+    return _pd(5, 6, 4, wall=tuple(wall), wall_u=PLATES, **kw)
+
+
+@pytest.mark.parametrize("ax", [0, 1, 2])
+@pytest.mark.parametrize("impl", ["c", "numpy"])
+def test_zou_he_nodes_carry_the_plate_velocity(ax, impl):
+    """The scheme's defining property: at every node of a plate and for each
+    colour, sum_i e_i f_i^k = rho_k u_w with rho_k = sum_i f_i^k (normal and
+    tangential components, inflow through the plate included)."""
+    pd = _plates_pd(ax)
+    p = oracle.params_from(pd)
+    rR, rB, u = wl.random_fields(5, 6, 4, seed=31)
+    f = oracle.init(p, rR, rB, u)
+    g = oracle.step(p, f, 2) if impl == "c" else naive.step(pd, f, 2)
+    for side in range(2):
+        face = [slice(None)] * 3
+        face[2 - ax] = 0 if side == 0 else g.shape[2 + 2 - ax] - 1
+        for k in range(2):
+            fk = g[(k, slice(None)) + tuple(face)]
+            rho = fk.sum(axis=0)
+            j = np.einsum("ia,i...->a...", E, fk)
+            want = rho[None] * np.asarray(PLATES[side])[(slice(None),) + (None,) * rho.ndim]
+            assert np.abs(j - want).max() < 1e-14
+
+
+@pytest.mark.parametrize("ax", [0, 1, 2])
+def test_zou_he_c_oracle_matches_numpy_restatement(ax):
+    """Closed form (C) against the linear-system statement (numpy)."""
+    pd = _plates_pd(ax)
+    p = oracle.params_from(pd)
+    rR, rB, u = wl.random_fields(5, 6, 4, seed=32)
+    f = oracle.init(p, rR, rB, u)
+    f = f * (1 + 0.05 * np.random.default_rng(4).uniform(-1, 1, f.shape))
+    assert np.abs(oracle.step(p, f, 3) - naive.step(pd, f, 3)).max() < 1e-13
+
+
+def _couette(U, tau, collision="mrt", ny=17, steps=6000):
+    pd = _pd(1, ny, 1, wall=(0, 2, 0), wall_u=((-U, 0, 0), (U, 0, 0)), alpha_R=1 / 3,
+             alpha_B=1 / 3, tau_R=tau, tau_B=tau, tau_e=1, tau_q=1, tau_pi=1, A_R=0,
+             A_B=0, beta=0, force=(0, 0, 0), gravity=(0, 0, 0), rho_in_R=1.0,
+             rho_in_B=1.0, collision=collision)
+    p = oracle.params_from(pd)
+    rR = np.ones((1, ny, 1))
+    f = oracle.init(p, rR, np.zeros_like(rR), np.zeros((3, 1, ny, 1)))
+    g = oracle.step(p, f, steps)
+    j = np.einsum("ia,kizyx->azyx", E, g)
+    ux = j[0] / g.sum(axis=(0, 1))
+    exact = U * (2 * np.arange(ny) / (ny - 1) - 1)
+    return np.abs(ux[0, :, 0] - exact).max(), np.abs(j[1:]).max(), abs(g.sum() - f.sum()) / f.sum()
+
+
+@pytest.mark.parametrize("collision", ["mrt", "bgk"])
+def test_couette_flow_between_moving_plates_is_linear(collision):
+    """Single phase between plates moving at -U and +U (the other axes
+    periodic), every rate 1: the steady velocity is exactly linear through
+    the plate nodes, u_x(y) = U (2 y / (ny - 1) - 1), v = w = 0, and no mass
+    crosses the plates."""
+    err, cross, dm = _couette(0.02, 1.0, collision)
+    assert err < 1e-14 and cross < 1e-14 and dm < 1e-13
+
+
+def test_couette_deviation_away_from_tau_one_is_third_order_in_u():
+    """At tau_v = 0.8 the steady profile departs from the line by the D3Q19
+    equilibrium's O(u^3) error, not by a boundary error: halving U divides
+    the deviation by 8."""
+    e1, _, _ = _couette(0.02, 0.8)
+    e2, _, _ = _couette(0.01, 0.8)
+    assert e1 < 1e-5 * 0.02
+    assert 7.5 < e1 / e2 < 8.5
+
+
 def test_poiseuille_is_exact_at_the_trt_magic_parameter():
     """Single phase, halfway bounce-back walls at y = -1/2 and ny - 1/2,
     uniform force G: with (tau_v - 1/2)(tau_q - 1/2) = 3/16 and
