@@ -82,7 +82,11 @@ typedef struct {
   int nx, ny, nz;      /* lattice size, each >= 1, ny and nz <= 65535,
                           nx*ny*nz < 226 million                            */
   int wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on
-                          both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D  */
+                          both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D;
+                          2 moving plates through the first and last layer
+                          (Zou-He velocity nodes, Sec. IV.A) with velocities
+                          wall_u -- at most one such axis, the other two
+                          periodic, single lattices only                    */
   int improved;        /* 1: Eq. 18 equilibrium + Eq. 45 correction (the
                           improved model); 0: Eq. 6, no correction (the
                           "original model" of Sec. IV.A)                     */
@@ -113,6 +117,15 @@ typedef struct {
   double contact_angle_deg; /* theta in (0, 180) when wetting = 1            */
   int collision;       /* lbm_collision [LBM_COLLISION_MRT]                  */
   int reserved;        /* 0                                                  */
+  double wall_u[2][3]; /* velocity of the low and the high plate of the
+                          wall = 2 axis (its normal component moves fluid
+                          through the plate).  After every step the
+                          populations of each colour entering from beyond a
+                          plate are rebuilt so that the node carries
+                          rho_k * wall_u (mass from the normal velocity,
+                          bounce-back of the non-equilibrium part along the
+                          normal, transverse momentum corrections); the plate
+                          velocity carries no forcing shift                  */
 } lbm_params;
 
 /* Creates a context: validates p, allocates the two population buffers and

@@ -51,6 +51,8 @@ struct lbm_ctx {
   CUtensorMap* d_bmaps[2][3];  // batches: [buffer][tile kind] -> device table, 2 per case
   bool batch_tma_ok[3];        // batch tables built, per tile kind
   int total_items;
+  int plate_axis;           // axis of the moving plates (wall = 2), or -1
+  double plate_u[2][3];     // their velocities (low, high)
   cudaGraphExec_t graph;    // two captured steps (buffer 0 -> 1 -> 0)
   int use_graph;
   long long steps;
@@ -94,8 +96,21 @@ static lbm_status validate(const lbm_params* p) {
   if (p->ny > 65535 || p->nz > 65535)
     return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
   for (int a = 0; a < 3; ++a)
-    if (p->wall[a] != 0 && p->wall[a] != 1)
-      return fail(nullptr, LBM_ERR_ARG, "wall[%d] must be 0 or 1", a);
+    if (p->wall[a] < 0 || p->wall[a] > 2)
+      return fail(nullptr, LBM_ERR_ARG, "wall[%d] must be 0, 1 or 2", a);
+  for (int a = 0; a < 3; ++a) {
+    if (p->wall[a] != 2) continue;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    if (p->wall[(a + 1) % 3] != 0 || p->wall[(a + 2) % 3] != 0)
+      return fail(nullptr, LBM_ERR_ARG,
+                  "moving plates (wall[%d] = 2) need the other two axes periodic", a);
+    if (n[a] < 3)
+      return fail(nullptr, LBM_ERR_ARG, "moving plates need at least 3 layers between them");
+    for (int side = 0; side < 2; ++side)
+      for (int d = 0; d < 3; ++d)
+        if (!(fabs(p->wall_u[side][d]) < 0.5))
+          return fail(nullptr, LBM_ERR_ARG, "wall_u components must be finite and below 0.5");
+  }
   if (p->improved != 0 && p->improved != 1)
     return fail(nullptr, LBM_ERR_ARG, "improved must be 0 or 1");
   if (p->storage < LBM_F32 || p->storage > LBM_BF16)
@@ -288,6 +303,11 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
   }
   if (ncases > 1 && ps[0].kernel != LBM_KERNEL_FUSED)
     return fail(nullptr, LBM_ERR_ARG, "batches run the fused kernel only");
+  if (ncases > 1)
+    for (int k = 0; k < ncases; ++k)
+      for (int a = 0; a < 3; ++a)
+        if (ps[k].wall[a] == 2)
+          return fail(nullptr, LBM_ERR_ARG, "moving plates (wall = 2) need a single lattice");
   lbm_ctx* c = new (std::nothrow) lbm_ctx;
   if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
   memset(c, 0, sizeof(*c));
@@ -299,6 +319,11 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
   c->ncases = ncases;
   c->storage = ps[0].storage;
   c->kernel = ps[0].kernel;
+  c->plate_axis = -1;
+  for (int a = 0; a < 3; ++a)
+    if (ps[0].wall[a] == 2) c->plate_axis = a;
+  for (int side = 0; side < 2; ++side)
+    for (int d = 0; d < 3; ++d) c->plate_u[side][d] = ps[0].wall_u[side][d];
   c->device = -1;
   c->stream = (cudaStream_t)cuda_stream;
   c->use_graph = 1;
@@ -541,6 +566,11 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
   else
     e = lbm::launch_fused(c->storage, src, dst, c->cases[0].args, c->fused, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  if (c->plate_axis >= 0) {
+    e = lbm::launch_plates(c->storage, dst, c->cases[0].args, c->plate_axis, c->plate_u,
+                           c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moving-plate kernel launch");
+  }
   return LBM_OK;
 }
 
@@ -863,5 +893,6 @@ extern "C" lbm_status lbm_get_fused_config(const lbm_ctx* c, int* tile_y,
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
-  return (c->ncases == 1 && c->kernel == LBM_KERNEL_TWO_PASS) ? 2 : 1;
+  return ((c->ncases == 1 && c->kernel == LBM_KERNEL_TWO_PASS) ? 2 : 1) +
+         (c->plate_axis >= 0 ? 1 : 0);
 }

@@ -41,6 +41,11 @@ cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         const int* flags, long long steps, double* out,
                         cudaStream_t s);
 int diag_capacity(int storage, int sms);
+// Moving plates on both faces of `axis` (wall = 2): rebuilds, in buf (the
+// state just written by a step), each colour's populations entering from
+// beyond a plate (Zou-He velocity nodes, velocities u[low / high]).
+cudaError_t launch_plates(int storage, void* buf, const StepArgs& a, int axis,
+                          const double u[2][3], cudaStream_t s);
 cudaError_t launch_twopass(int storage, const void* src, void* dst,
                            const StepArgs& a, float4* mom, cudaStream_t s);
 

@@ -370,6 +370,89 @@ __global__ void __launch_bounds__(kDiagBlock, 4)
 }
 
 // ---------------------------------------------------------------------------
+// Moving plates (Sec. IV.A): Zou-He velocity nodes on both faces of one
+// axis.  One thread per plate node.  The node's known populations are
+// pulled; for each colour k, rho_k = (S_0 + 2 S_out) / (1 - u_n) (S_0: the
+// populations parallel to the plate, S_out: those leaving through it, u_n
+// the plate's inward normal velocity), and each entering population
+// f_i = f_opp(i) + 6 w_i rho_k (e_i . u) - e_i . N with the transverse
+// corrections N_t = (1/2) sum_{e_j . n = 0} f_j e_jt - rho_k u_t / 3, which
+// make the colour's momentum exactly rho_k u.  f_i is written where the
+// next pull of direction i at the node looks (the node's own slot of
+// opp(i), as at a wall); no other node reads that slot.
+// ---------------------------------------------------------------------------
+struct PlateArgs {
+  float u[2][3];  // plate velocities (low, high)
+  int axis;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kAuxBlock)
+    k_plates(T* __restrict__ buf, StepArgs a, PlateArgs pl) {
+  const int ax = pl.axis, t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+  const int n[3] = {a.nx, a.ny, a.nz};
+  const int per_face = n[t1] * n[t2];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * per_face) return;
+  const int side = e / per_face, r = e - side * per_face;
+  int xyz[3];
+  xyz[ax] = side == 0 ? 0 : n[ax] - 1;
+  xyz[t1] = r % n[t1];
+  xyz[t2] = r / n[t1];
+  const int sgn = side == 0 ? 1 : -1;  // inward normal along ax
+  const float ux = pl.u[side][0], uy = pl.u[side][1], uz = pl.u[side][2];
+  const float uu[3] = {ux, uy, uz};
+  const float un = sgn * uu[ax];
+  float fR[19], fB[19];
+  pull_pairs<T>(buf, a, xyz[0], xyz[1], xyz[2], fR, fB);
+  const unsigned c =
+      ((unsigned)xyz[2] * (unsigned)a.ny + (unsigned)xyz[1]) * (unsigned)a.nx + (unsigned)xyz[0];
+  auto en = [&](int i) { return sgn * (ax == 0 ? ex(i) : (ax == 1 ? ey(i) : ez(i))); };
+  auto et = [&](int i, int d) { return d == 0 ? ex(i) : (d == 1 ? ey(i) : ez(i)); };
+  float* fk[2] = {fR, fB};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float s0 = 0.f, sout = 0.f, tg[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      const int ni = en(i);
+      if (ni == 0) {
+        s0 += fk[k][i];
+        tg[0] += ex(i) * fk[k][i];
+        tg[1] += ey(i) * fk[k][i];
+        tg[2] += ez(i) * fk[k][i];
+      } else if (ni < 0) {
+        sout += fk[k][i];
+      }
+    }
+    const float rho = (s0 + 2.f * sout) / (1.f - un);
+    float N[3] = {0.f, 0.f, 0.f};
+    N[t1] = 0.5f * tg[t1] - rho * uu[t1] * (1.0f / 3.0f);
+    N[t2] = 0.5f * tg[t2] - rho * uu[t2] * (1.0f / 3.0f);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      if (en(i) != 1) continue;
+      const float eu = ex(i) * ux + ey(i) * uy + ez(i) * uz;
+      const float corr = et(i, 0) * N[0] + et(i, 1) * N[1] + et(i, 2) * N[2];
+      const float w = shell(i) == 1 ? (1.0f / 18.0f) : (1.0f / 36.0f);
+      fk[k][i] = fk[k][opp(i)] + 6.f * w * rho * eu - corr;
+    }
+  }
+  // write the entering populations (both colours) to their pull slots
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    if (en(i) != 1) continue;
+    float rv = fR[i], bv = fB[i];
+    if (Store<T>::kDeviation) {
+      const int sh = shell(i);
+      rv -= sh == 1 ? a.offR1 : a.offR2;
+      bv -= sh == 1 ? a.offB1 : a.offB2;
+    }
+    Store<T>::store2(buf + 2 * ((size_t)opp(i) * (unsigned)a.plane + c), rv, bv);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Two-pass step.  Pass 1 writes, per cell, (rho^N, Qbar_x, Qbar_y, Qbar_z)
 // to a scratch field; pass 2 pulls the populations again, forms the Eq. 49
 // gradients from the neighbours' scratch entries and collides.
@@ -518,6 +601,19 @@ cudaError_t launch_diag_t(const void* src, const StepArgs& a, double* part,
   return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_plates_t(void* buf, const StepArgs& a, int axis, const double u[2][3],
+                            cudaStream_t s) {
+  PlateArgs pl;
+  pl.axis = axis;
+  for (int side = 0; side < 2; ++side)
+    for (int d = 0; d < 3; ++d) pl.u[side][d] = (float)u[side][d];
+  const int n[3] = {a.nx, a.ny, a.nz};
+  const long long nodes = 2LL * n[(axis + 1) % 3] * n[(axis + 2) % 3];
+  const unsigned blocks = (unsigned)((nodes + kAuxBlock - 1) / kAuxBlock);
+  k_plates<T><<<blocks, kAuxBlock, 0, s>>>((T*)buf, a, pl);
+  return cudaGetLastError();
+}
+template <typename T>
 int diag_capacity_t(int sms) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag<T>,
@@ -577,6 +673,11 @@ cudaError_t launch_diag(int storage, const void* src, const StepArgs& a,
                         cudaStream_t s) {
   LBM_DISPATCH(storage, launch_diag_t, src, a, part, max_blocks, done, flags, steps,
                out, s)
+}
+cudaError_t launch_plates(int storage, void* buf, const StepArgs& a, int axis,
+                          const double u[2][3], cudaStream_t s) {
+  if (axis < 0 || axis > 2) return cudaErrorInvalidValue;
+  LBM_DISPATCH(storage, launch_plates_t, buf, a, axis, u, s)
 }
 int diag_capacity(int storage, int sms) {
   switch (storage) {

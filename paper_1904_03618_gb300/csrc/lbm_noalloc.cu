@@ -123,6 +123,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* f_in,
   clear_thread_error();
   lbm_status st = validate_params(p);
   if (st != LBM_OK) return st;
+  if (p->wall[0] == 2 || p->wall[1] == 2 || p->wall[2] == 2)
+    return fail_without_context(LBM_ERR_ARG,
+                                "lbm_step_noalloc: moving plates (wall = 2) are not supported");
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > kNoAllocMaxCells)
     return fail_without_context(

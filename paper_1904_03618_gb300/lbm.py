@@ -55,6 +55,7 @@ class LbmParams(ctypes.Structure):
         ("ref_R", ctypes.c_double), ("ref_B", ctypes.c_double),
         ("contact_angle_deg", ctypes.c_double),
         ("collision", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("wall_u", (ctypes.c_double * 3) * 2),
     ]
 
 
@@ -176,7 +177,7 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
                 tau_pi=1.0, A_R=0.0, A_B=0.0, beta=0.7, delta=0.98,
                 force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0), ref_R=0.0,
                 ref_B=0.0, wetting=False, contact_angle_deg=90.0, collision="mrt",
-                **_ignored) -> LbmParams:
+                wall_u=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), **_ignored) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):
@@ -190,6 +191,9 @@ def make_params(nx, ny, nz, *, wall=(0, 0, 0), improved=True, storage="f32",
     p.wetting = 1 if wetting else 0
     p.contact_angle_deg = float(contact_angle_deg)
     p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    for side in range(2):
+        for a in range(3):
+            p.wall_u[side][a] = float(wall_u[side][a])
     p.rho_in_R, p.rho_in_B = float(rho_in_R), float(rho_in_B)
     p.alpha_R, p.alpha_B = float(alpha_R), float(alpha_B)
     p.tau_R, p.tau_B = float(tau_R), float(tau_B)
