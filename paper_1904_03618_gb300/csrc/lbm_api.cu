@@ -48,6 +48,8 @@ struct lbm_ctx {
   int* d_flags;             // device error word of the kernels' bounded waits
   bool tma_ok[3];           // tensor maps built, per tile kind (single lattice)
   CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
+  CUtensorMap smaps[2][2][6];  // [tile: 0 = 34 x 15, 1 = 34 x 12][buffer][map]: SEAM forms
+  bool seam_ok;                // smaps built (FP32, periodic in x and y)
   CUtensorMap* d_bmaps[2][3];  // batches: [buffer][tile kind] -> device table, 2 per case
   bool batch_tma_ok[3];        // batch tables built, per tile kind
   int total_items;
@@ -382,10 +384,24 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
         c->tma_ok[w] = lbm::tma_build_maps(c->storage, c->pop[b], c->cases[0].args, w,
                                            c->tmaps[b][w]) == cudaSuccess;
     }
+    if (c->tma_ok[2] && lbm::seam_eligible(c->cases[0].args, c->storage)) {
+      c->seam_ok = true;
+      for (int t = 0; t < 2 && c->seam_ok; ++t)
+        for (int b = 0; b < 2 && c->seam_ok; ++b)
+          c->seam_ok = lbm::tma_build_seam_maps(c->pop[b], c->cases[0].args, t == 0 ? 15 : 12,
+                                                c->smaps[t][b]) == cudaSuccess;
+    }
     cudaGetLastError();
     lbm::FusedConfig t;
     if (lbm::tma_default_config(c->cases[0].args, c->storage, c->sms, c->tma_ok, &t))
       c->fused = t;
+    if (c->seam_ok) {
+      // periodic FP32 lattices: the 34 x 12 tile with two stages and the
+      // seams staged by tensor copies
+      c->fused.tile_y = 12;
+      c->fused.hold = 7;
+      c->fused.zchunk = lbm::seam12_zchunk(c->cases[0].args, c->sms);
+    }
   }
   if (st == LBM_OK && ncases > 1) {
     // tensor maps of every case for the batched TMA step (tile kinds 0, 2)
@@ -555,6 +571,11 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
                                 c->fused, c->sms, c->stream);
   else if (c->kernel == LBM_KERNEL_TWO_PASS)
     e = lbm::launch_twopass(c->storage, src, dst, c->cases[0].args, c->phase, c->stream);
+  else if (c->seam_ok && ((c->fused.hold == 8 && c->fused.tile_y == 15) ||
+                           (c->fused.hold == 7 && c->fused.tile_y == 12)))
+    e = lbm::launch_fused_tma_seam(src, dst, c->cases[0].args, c->fused.tile_y,
+                                   c->smaps[c->fused.tile_y == 15 ? 0 : 1][from],
+                                   c->fused.zchunk, c->d_flags, c->stream);
   else if (c->fused.hold == 7 || c->fused.hold == 8) {
     const int w = lbm::tma_kind(c->fused.tile_y);
     e = w >= 0 && c->tma_ok[w]
@@ -862,6 +883,17 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
       (c->ncases > 1
            ? lbm::valid_batch_config(f) && ((hold != 7 && hold != 8) || batch_tma)
            : lbm::valid_fused_config(f, c->storage) && ((hold != 7 && hold != 8) || single_tma));
+  if (tile_y == 12) {  // the two-stage SEAM form only
+    if (!(c->ncases == 1 && c->seam_ok && hold == 7 && zchunk >= 0))
+      return fail(c, LBM_ERR_ARG,
+                  "tile_y 12 is the two-stage seam form (hold 7) of single periodic FP32 "
+                  "lattices with nx a multiple of 2, nx >= 34 and ny >= 15");
+    if (zchunk == 0) f.zchunk = lbm::seam12_zchunk(c->cases[0].args, c->sms);
+    c->fused = f;
+    drop_graph(c);
+    c->err[0] = 0;
+    return LBM_OK;
+  }
   if (ok && c->cases[0].args.bgk && (f.tile_y != 8 || f.hold != 2))
     return fail(c, LBM_ERR_ARG,
                 "the BGK operator runs the shared-memory-hold form only (tile_y 8, hold 2)");

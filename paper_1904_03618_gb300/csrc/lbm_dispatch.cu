@@ -136,10 +136,10 @@ bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind
 // (tw + 2)-pair boxes; 16-bit storage uses tw + 4 pairs rounded up to a
 // multiple of 4 (map 1 = map 0).  Boxes are by rows by one plane by one direction, no swizzle; cells
 // beyond the array read as zero.
-cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
-                           CUtensorMap maps[2]) {
-  if (kind < 0 || kind > 2) return cudaErrorInvalidValue;
-  const int tw = kTmaTW[kind], by = kTmaBY[kind];
+// One tensor map over a population buffer seen as [direction][z][y][x]
+// pairs, with a box of w x h pairs (one plane, one direction).
+static cudaError_t encode_box(int storage, const void* base, const StepArgs& a, unsigned w,
+                              unsigned h, CUtensorMap* map) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -154,22 +154,62 @@ cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int
       return e != cudaSuccess ? e : cudaErrorNotSupported;
     encode = (EncodeFn)fn;
   }
-  if (!tma_eligible(a, storage)) return cudaErrorInvalidValue;
   const cuuint64_t E = (cuuint64_t)pair_bytes(storage);
   const cuuint64_t dims[4] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz, 19};
   const cuuint64_t strides[3] = {E * a.nx, E * a.nx * a.ny, E * (cuuint64_t)a.plane};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       storage == 0 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  const cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)h, 1, 1};
+  const CUresult r = encode(map, dt, 4, const_cast<void*>(base), dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
+                           CUtensorMap maps[2]) {
+  if (kind < 0 || kind > 2) return cudaErrorInvalidValue;
+  if (!tma_eligible(a, storage)) return cudaErrorInvalidValue;
+  const int tw = kTmaTW[kind], by = kTmaBY[kind];
   for (int m = 0; m < 2; ++m) {
-    const cuuint32_t w =
-        (cuuint32_t)(storage == 0 ? (m == 0 ? tw : tw + 2) : (tw + 4 + 3) / 4 * 4);
-    const cuuint32_t box[4] = {w, (cuuint32_t)by, 1, 1};
-    const CUresult r = encode(&maps[m], dt, 4, const_cast<void*>(base), dims, strides, box, es,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const unsigned w = (unsigned)(storage == 0 ? (m == 0 ? tw : tw + 2) : (tw + 4 + 3) / 4 * 4);
+    cudaError_t e = encode_box(storage, base, a, w, (unsigned)by, &maps[m]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int seam12_zchunk(const StepArgs& a, int sms) {
+  const long long cols = (long long)((a.nx + 31) / 32) * ((a.ny + 9) / 10);
+  const long long slots = sms > 0 ? sms : 152;
+  int best_zc = 12;
+  double best_cost = 1e300;
+  for (int zc = 6; zc <= 24; ++zc) {
+    const long long ctas = cols * ((a.nz + zc - 1) / zc);
+    const double cost = (double)((ctas + slots - 1) / slots) * (zc + 1.5);
+    if (cost <= best_cost + 1e-9) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  return best_zc < a.nz ? best_zc : a.nz;
+}
+
+bool seam_eligible(const StepArgs& a, int storage) {
+  return storage == 0 && tma_eligible(a, storage) && !a.wx && !a.wy && !a.wz &&
+         a.nx >= kTmaTW[2] && a.ny >= kTmaBY[2];
+}
+
+cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
+                                CUtensorMap maps[6]) {
+  if (!seam_eligible(a, 0) || (tile_y != 15 && tile_y != 12)) return cudaErrorInvalidValue;
+  const unsigned tw = (unsigned)kTmaTW[2], by = (unsigned)tile_y;
+  const unsigned shape[6][2] = {{tw, by}, {tw + 2, by}, {2, by}, {tw, 2}, {tw + 2, 2}, {2, 2}};
+  for (int m = 0; m < 6; ++m) {
+    cudaError_t e = encode_box(0, base, a, shape[m][0], shape[m][1], &maps[m]);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

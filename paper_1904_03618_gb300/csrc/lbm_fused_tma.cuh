@@ -33,6 +33,16 @@
 // do the first and last plane of a lattice with walls in z (they get no
 // copies).
 //
+// Periodic seams (SEAM form: FP32, lattices periodic in x and y; a 34 x 15
+// tile with one stage or a 34 x 12 tile with two).  A tensor copy cannot wrap around a periodic axis, so a tile on a
+// seam gets, per direction, up to three more copies into its stage: the two
+// columns beyond the x seam (a 2 x BY box read from the other side of the
+// lattice), the two rows beyond the y seam (a W x 2 box) and the 2 x 2
+// corner.  A direction's main box and its strips share one block of the
+// stage; each lane looks up its 19 pairs through nine byte offsets, one per
+// (e_x, e_y), fixed per chunk, so a seam tile reads shared memory exactly
+// like an inner one and no lane pulls from global memory.
+//
 // Waits on the stage mbarriers are bounded (kTmaWaitNs); a wait that
 // gives up sets *err, waits (bounded) for the CTA's copies still in flight
 // and leaves the CTA.
@@ -69,9 +79,33 @@ __host__ __device__ constexpr int tma_box_off(int i) {
   for (int j = 0; j < i; ++j) o += tma_box_bytes<T, TW, BY>(j);
   return o;
 }
-template <typename T, int TW, int BY>
+// SEAM form: per direction one block = main box (up to TW + 2 pairs wide) |
+// x strip (2 x BY) | y strip (up to (TW + 2) x 2) | corner (2 x 2), each part
+// 128-byte aligned; the main box of a TW-wide direction leaves its block's
+// tail unused.
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_main_bytes(int w) {
+  return (w * BY * 8 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_xs_off(int w) {
+  return seam_main_bytes<TW, BY>(w);
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_ys_off(int w) {
+  return seam_xs_off<TW, BY>(w) + (2 * BY * 8 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_cs_off(int w) {
+  return seam_ys_off<TW, BY>(w) + ((TW + 2) * 2 * 8 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_block_bytes() {
+  return seam_cs_off<TW, BY>(TW + 2) + 128;
+}
+template <typename T, int TW, int BY, bool SEAM = false>
 __host__ __device__ constexpr int tma_stage_bytes() {
-  return tma_box_off<T, TW, BY>(19);
+  return SEAM ? 19 * seam_block_bytes<TW, BY>() : tma_box_off<T, TW, BY>(19);
 }
 // Bytes the 19 copies of a plane deliver (the boxes without their padding):
 // the transaction count the stage's mbarrier expects.
@@ -99,27 +133,27 @@ __host__ __device__ constexpr int tma_hold_bytes(int vals) {
 }
 // Values a cell holds between its pull and its collision: f (19), rho_R,
 // rho_B and, where shared memory allows, u (recomputed from f otherwise).
-template <typename T, int TW, int BY, int NS>
+template <typename T, int TW, int BY, int NS, bool SEAM = false>
 __host__ __device__ constexpr int tma_hold_vals() {
-  return NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
+  return NS * tma_stage_bytes<T, TW, BY, SEAM>() + tma_win_bytes<TW, BY>() +
                      tma_hold_bytes<TW, BY>(24) + 16 <=
                  (TW * BY > 256 ? kTmaSmemLimit : 113 * 1024)
              ? 24
              : 21;
 }
-template <typename T, int TW, int BY, int NS>
+template <typename T, int TW, int BY, int NS, bool SEAM = false>
 __host__ __device__ constexpr int tma_smem_bytes() {
-  return NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
-         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS>()) + 16;
+  return NS * tma_stage_bytes<T, TW, BY, SEAM>() + tma_win_bytes<TW, BY>() +
+         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS, SEAM>()) + 16;
 }
 // Resident CTAs per SM the configuration is laid out for.
 template <int TW, int BY>
 __host__ __device__ constexpr int tma_ctas_per_sm() {
   return TW * BY > 256 ? 1 : 2;
 }
-template <typename T, int TW, int BY, int NS>
+template <typename T, int TW, int BY, int NS, bool SEAM = false>
 __host__ __device__ constexpr bool tma_fits() {
-  return tma_smem_bytes<T, TW, BY, NS>() <=
+  return tma_smem_bytes<T, TW, BY, NS, SEAM>() <=
          (tma_ctas_per_sm<TW, BY>() == 1 ? kTmaSmemLimit : 113 * 1024);
 }
 
@@ -184,6 +218,102 @@ struct TmaIssue<T, TW, BY, 19> {
                                              int, int, int, int, unsigned) {}
 };
 
+// SEAM form: the strip maps (x strip 2 x BY, y strips TW x 2 and (TW + 2) x 2,
+// corner 2 x 2) of the source buffer.
+struct SeamStripMaps {
+  const CUtensorMap *xs, *ys0, *ys1, *cs;
+};
+// SEAM form, one thread: the main boxes of a plane into their blocks (as
+// TmaIssue, compile-time direction and map) ...
+template <int TW, int BY, int I>
+struct TmaIssueSeamMain {
+  __device__ __forceinline__ static void run(unsigned block0, const CUtensorMap* m0,
+                                             const CUtensorMap* m1, int x0, int y0, int zz,
+                                             int nz, unsigned mbar) {
+    tma_load_4d(block0 + (unsigned)(I * seam_block_bytes<TW, BY>()), ex(I) == 0 ? m1 : m0,
+                ex(I) < 0 ? x0 : x0 - 2, y0 - 1 - ey(I), wrap1(zz - ez(I), nz), I, mbar);
+    TmaIssueSeamMain<TW, BY, I + 1>::run(block0, m0, m1, x0, y0, zz, nz, mbar);
+  }
+};
+template <int TW, int BY>
+struct TmaIssueSeamMain<TW, BY, 19> {
+  __device__ __forceinline__ static void run(unsigned, const CUtensorMap*, const CUtensorMap*,
+                                             int, int, int, int, unsigned) {}
+};
+// ... and, on a seam tile only, the strips: x strip from source x = xs, y
+// strip from source y = ys, corner (xs or ys < 0: none).
+template <int TW, int BY, int I>
+struct TmaIssueStrips {
+  __device__ __forceinline__ static void run(unsigned block0, const SeamStripMaps& sm, int x0,
+                                             int y0, int zz, int nz, int xs, int ys,
+                                             unsigned mbar) {
+    constexpr int w = ex(I) == 0 ? TW + 2 : TW;
+    const unsigned blk = block0 + (unsigned)(I * seam_block_bytes<TW, BY>());
+    const int x = ex(I) < 0 ? x0 : x0 - 2;
+    const int y = y0 - 1 - ey(I);
+    const int z = wrap1(zz - ez(I), nz);
+    if (xs >= 0) tma_load_4d(blk + seam_xs_off<TW, BY>(w), sm.xs, xs, y, z, I, mbar);
+    if (ys >= 0)
+      tma_load_4d(blk + seam_ys_off<TW, BY>(w), ex(I) == 0 ? sm.ys1 : sm.ys0, x, ys, z, I, mbar);
+    if (xs >= 0 && ys >= 0) tma_load_4d(blk + seam_cs_off<TW, BY>(w), sm.cs, xs, ys, z, I, mbar);
+    TmaIssueStrips<TW, BY, I + 1>::run(block0, sm, x0, y0, zz, nz, xs, ys, mbar);
+  }
+};
+template <int TW, int BY>
+struct TmaIssueStrips<TW, BY, 19> {
+  __device__ __forceinline__ static void run(unsigned, const SeamStripMaps&, int, int, int, int,
+                                             int, int, unsigned) {}
+};
+// Bytes one plane's copies deliver on a tile with or without x / y strips.
+template <int TW, int BY>
+__host__ __device__ constexpr int seam_tx_bytes(bool xstrip, bool ystrip) {
+  int b = 0;
+  for (int i = 0; i < 19; ++i) {
+    const int w = ex(i) == 0 ? TW + 2 : TW;
+    b += w * BY * 8;
+    if (xstrip) b += 2 * BY * 8;
+    if (ystrip) b += w * 2 * 8;
+    if (xstrip && ystrip) b += 2 * 2 * 8;
+  }
+  return b;
+}
+// Byte offset, within a direction's block, of the pair a lane reads for a
+// direction (ex, ey): its source cell (cx - ex, cy - ey) in the main box, or
+// beyond a periodic seam in the x strip, the y strip or the corner.  Lanes
+// whose source lies further out (beyond the ring, unused) read the main box.
+template <int TW, int BY>
+__device__ __forceinline__ unsigned seam_lane_off(int tx, int ty, int cx, int cy, int ex_,
+                                                  int ey_, int nx, int ny) {
+  const int w = ex_ == 0 ? TW + 2 : TW;
+  const int col = tx + (ex_ == 0 ? 1 : 0);
+  const int sx = cx - ex_, sy = cy - ey_;
+  const bool xin = sx >= 0 && sx < nx, yin = sy >= 0 && sy < ny;
+  const int xc = sx < 0 ? sx + 2 : sx - nx, yc = sy < 0 ? sy + 2 : sy - ny;
+  const bool xok = xc >= 0 && xc < 2, yok = yc >= 0 && yc < 2;
+  int off = (ty * w + col) * 8;
+  if (!xin && yin && xok) off = seam_xs_off<TW, BY>(w) + (ty * 2 + xc) * 8;
+  if (xin && !yin && yok) off = seam_ys_off<TW, BY>(w) + (yc * w + col) * 8;
+  if (!xin && !yin && xok && yok) off = seam_cs_off<TW, BY>(w) + (yc * 2 + xc) * 8;
+  return (unsigned)off;
+}
+// SEAM form of StageReduce: the pair of direction I at its lane offset.
+template <int TW, int BY, int I>
+struct StageReduceSeam {
+  __device__ __forceinline__ static void run(const unsigned char* stage, const unsigned* loff,
+                                             float* f, float2& rho) {
+    const float2 v = *reinterpret_cast<const float2*>(
+        stage + I * seam_block_bytes<TW, BY>() + loff[(ex(I) + 1) * 3 + (ey(I) + 1)]);
+    rho = __fadd2_rn(rho, v);
+    f[I] = v.x + v.y;
+    StageReduceSeam<TW, BY, I + 1>::run(stage, loff, f, rho);
+  }
+};
+template <int TW, int BY>
+struct StageReduceSeam<TW, BY, 19> {
+  __device__ __forceinline__ static void run(const unsigned char*, const unsigned*, float*,
+                                             float2&) {}
+};
+
 // Reads the 19 pairs of one cell from a stage, reduced on the fly to
 // (f_i = fR_i + fB_i, rho_R, rho_B).  col0 = tx (FP32) or tx + 1 + o (16-bit).
 template <typename T, int TW, int BY, int I>
@@ -216,15 +346,17 @@ struct StageReduce<T, TW, BY, 19> {
 // stages and mbarrier phases continue across items.  map0 / map1: the
 // source buffer's tensor maps (param or global space).  Returns false after
 // a wait gave up (*err set, the CTA's copies drained).
-template <typename T, bool WALLS, int TW, int BY, int NS>
+template <typename T, bool WALLS, int TW, int BY, int NS, bool SEAM = false>
 __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restrict__ dst,
                                           const StepArgs& a, const CUtensorMap* map0,
                                           const CUtensorMap* map1, int bx, int by, int zb,
                                           int ze, unsigned char* smem, unsigned G0,
-                                          int* __restrict__ err) {
-  constexpr int SB = tma_stage_bytes<T, TW, BY>();
-  constexpr int TX = tma_stage_tx_bytes<T, TW, BY>();
-  constexpr int HV = tma_hold_vals<T, TW, BY, NS>();
+                                          int* __restrict__ err,
+                                          const SeamStripMaps* strips = nullptr) {
+  static_assert(!SEAM || (tma_pair_bytes<T>() == 8 && !WALLS),
+                "the SEAM form is FP32 and periodic in x and y");
+  constexpr int SB = tma_stage_bytes<T, TW, BY, SEAM>();
+  constexpr int HV = tma_hold_vals<T, TW, BY, NS, SEAM>();
   using Pair = typename Store<T>::Pair;
   unsigned char* stage0 = smem;
   float4(*win)[BY][TW] = reinterpret_cast<float4(*)[BY][TW]>(smem + NS * SB);
@@ -240,6 +372,22 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   const int x0 = bx * (TW - 2), y0 = by * (BY - 2);
   // every source x - e_i, y - e_i of this column lies inside the lattice
   const bool col_fast = g.cx >= 1 && g.cx <= a.nx - 2 && g.cy >= 1 && g.cy <= a.ny - 2;
+  // SEAM form: strip sources of this tile (< 0: none) and the lane's nine
+  // offsets; the copies deliver TX bytes per plane
+  int TX = tma_stage_tx_bytes<T, TW, BY>();
+  int seam_xs = -1, seam_ys = -1;
+  unsigned loff[9];
+  if constexpr (SEAM) {
+    const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
+    if (x0 < 2) seam_xs = a.nx - 2;
+    else if (x0 + TW - 2 >= a.nx - 1) seam_xs = 0;
+    if (y0 < 2) seam_ys = a.ny - 2;
+    else if (y0 + BY - 2 >= a.ny - 1) seam_ys = 0;
+    TX = seam_tx_bytes<TW, BY>(seam_xs >= 0, seam_ys >= 0);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      loff[e] = seam_lane_off<TW, BY>(tx, ty, cx, cy, e / 3 - 1, e % 3 - 1, a.nx, a.ny);
+  }
   int col0 = tx;
   if constexpr (tma_pair_bytes<T>() != 8) col0 = tx + 1 + ((x0 - 2) - ((x0 - 2) & ~3));
   const unsigned st_base = smem_addr(stage0), mb_base = smem_addr(mbar);
@@ -260,24 +408,40 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     if (!(WALLS && a.wz)) return true;
     return zl >= 1 && zl <= a.nz - 2;
   };
-  auto issue = [&](int k) {  // one thread
+  auto issue_one = [&](int k) {  // one thread
     const int zl = zb - 1 + k;
     const unsigned m = mb(k);
     if (staged(zl)) {
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m),
                    "r"(TX)
                    : "memory");
-      TmaIssue<T, TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
+      if constexpr (SEAM) {
+        TmaIssueSeamMain<TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz,
+                                         m);
+        if (seam_xs >= 0 || seam_ys >= 0)
+          TmaIssueStrips<TW, BY, 0>::run(st_addr(k), *strips, x0, y0, wrap1(zl, a.nz), a.nz,
+                                         seam_xs, seam_ys, m);
+      } else {
+        TmaIssue<T, TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
+      }
     } else {
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(m) : "memory");
     }
+  };
+  auto issue = [&](int k) {
+    if (tid == 0) issue_one(k);
   };
   // Pulls plane zl: window slot and reduced state (f, rho_R, rho_B, u).
   auto fill = [&](int k, float* f, float* hu) {
     const int zl = zb - 1 + k;
     if (!g.plane_ok(a, zl)) return;
     float rR = 0.f, rB = 0.f;
-    if (col_fast && staged(zl)) {
+    if constexpr (SEAM) {
+      float2 rho = make_float2(0.f, 0.f);
+      StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
+      rR = rho.x;
+      rB = rho.y;
+    } else if (col_fast && staged(zl)) {
       float2 rho = make_float2(0.f, 0.f);
       StageReduce<T, TW, BY, 0>::run(stage0 + stage_of(k) * SB, ty, col0, a, f, rho);
       rR = rho.x;
@@ -301,10 +465,8 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
 
   float cf[19], ch[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if constexpr (NS == 2) {
-    if (tid == 0) {
-      issue(0);
-      issue(1);
-    }
+    issue(0);
+    issue(1);
     float tf[19], th[5];
     bool ok = tma_wait(mb(0), par(0));
     if (ok) fill(0, tf, th);
@@ -314,12 +476,10 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
       drain(0);
       return false;
     }
-    if (tid == 0) {
-      if (K > 2) issue(2);
-      if (K > 3) issue(3);
-    }
+    if (K > 2) issue(2);
+    if (K > 3) issue(3);
   } else {
-    if (tid == 0) issue(0);
+    issue(0);
     float tf[19], th[5];
     bool ok = tma_wait(mb(0), par(0));
     if (ok) fill(0, tf, th);
@@ -327,14 +487,14 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
       drain(0);
       return false;
     }
-    if (tid == 0) issue(1);
+    issue(1);
     ok = tma_wait(mb(1), par(1));
     if (ok) fill(1, cf, ch);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(1);
       return false;
     }
-    if (tid == 0 && K > 2) issue(2);
+    if (K > 2) issue(2);
   }
   for (int k = 2; k < K; ++k) {
     const int z = zb + k - 2;  // plane that collides; plane z + 1 is filled
@@ -354,7 +514,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
       return false;
     }
     // the stage of fill k is consumed by every thread: refill it
-    if (tid == 0 && k + NS < K) issue(k + NS);
+    if (k + NS < K) issue(k + NS);
     if (g.interior) {
       const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
       float4 ctr;
@@ -386,10 +546,10 @@ __device__ __forceinline__ void tma_init_barriers(unsigned char* mbar_bytes, int
   }
 }
 
-template <typename T, int TW, int BY, int NS>
+template <typename T, int TW, int BY, int NS, bool SEAM = false>
 __device__ __forceinline__ unsigned char* tma_mbar_bytes(unsigned char* smem) {
-  return smem + NS * tma_stage_bytes<T, TW, BY>() + tma_win_bytes<TW, BY>() +
-         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS>());
+  return smem + NS * tma_stage_bytes<T, TW, BY, SEAM>() + tma_win_bytes<TW, BY>() +
+         tma_hold_bytes<TW, BY>(tma_hold_vals<T, TW, BY, NS, SEAM>());
 }
 
 template <typename T, bool WALLS, int TW, int BY, int NS>
@@ -409,6 +569,56 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
   __syncthreads();
   tma_chunk<T, WALLS, TW, BY, NS>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y, zb, ze,
                                   smem, 0u, err);
+}
+
+// SEAM form (FP32, periodic in x and y, one stage): the source buffer's six
+// tensor maps (main TW, main TW + 2, x strip, y strip TW, y strip TW + 2,
+// corner), each a kernel parameter of its own like the other forms' maps.
+template <int TW, int BY, int NS>
+__global__ void __launch_bounds__(TW* BY, 1)
+    k_fused_tma_seam(const float* __restrict__ src, float* __restrict__ dst,
+                     const __grid_constant__ StepArgs a,
+                     const __grid_constant__ CUtensorMap map0,
+                     const __grid_constant__ CUtensorMap map1,
+                     const __grid_constant__ CUtensorMap mxs,
+                     const __grid_constant__ CUtensorMap mys0,
+                     const __grid_constant__ CUtensorMap mys1,
+                     const __grid_constant__ CUtensorMap mcs, int zchunk,
+                     int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, a.nz);
+  if (zb >= ze) return;
+  if (smem_addr(smem) & 127u) {  // the copies need 128-byte aligned blocks
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
+    return;
+  }
+  tma_init_barriers(tma_mbar_bytes<float, TW, BY, NS, true>(smem), NS);
+  __syncthreads();
+  const SeamStripMaps strips = {&mxs, &mys0, &mys1, &mcs};
+  tma_chunk<float, false, TW, BY, NS, true>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y,
+                                            zb, ze, smem, 0u, err, &strips);
+}
+
+template <int TW, int BY, int NS>
+static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs& a,
+                                     const CUtensorMap* maps6, int zc, int* err,
+                                     cudaStream_t s) {
+  static_assert(tma_fits<float, TW, BY, NS, true>(), "SEAM stages do not fit");
+  static bool attr_set = false;
+  constexpr int bytes = tma_smem_bytes<float, TW, BY, NS, true>();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 blk(TW, BY);
+  dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
+  k_fused_tma_seam<TW, BY, NS><<<grd, blk, bytes, s>>>((const float*)src, (float*)dst, a, maps6[0],
+                                                   maps6[1], maps6[2], maps6[3], maps6[4],
+                                                   maps6[5], zc, err);
+  return cudaGetLastError();
 }
 
 // Batched TMA step: persistent CTAs take the work items (case, z chunk,

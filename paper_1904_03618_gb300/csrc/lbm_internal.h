@@ -80,6 +80,20 @@ bool tma_eligible(const StepArgs& a, int storage);
 int tma_kind(int tile_y);  // -1 for a tile_y without a TMA form
 cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
                            CUtensorMap maps[2]);
+// SEAM forms of the TMA step (34 x 15 threads with one stage, 34 x 12 with
+// two; tile_y 15 or 12): FP32 storage, periodic in x and y, nx >= 34 and
+// ny >= 15 (no tile on both seams of an axis), TMA eligible.  Their six maps
+// (main 34 and 36 wide, x strip 2 wide, y strips 34 and 36 x 2, corner
+// 2 x 2; main and x strip tile_y rows) over the source buffer.
+bool seam_eligible(const StepArgs& a, int storage);
+cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
+                                CUtensorMap maps[6]);
+cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
+                                  const CUtensorMap* maps6, int zchunk, int* err,
+                                  cudaStream_t s);
+// z chunk of the 34 x 12 two-stage SEAM form (the rounds-of-CTAs model of
+// tma_default_config over its tile columns).
+int seam12_zchunk(const StepArgs& a, int sms);
 bool tma_config_fits(int storage, int kind, int ns);
 // Interior width of a tile (30, or 32 for the 34 x 15 tile, tile_y 15).
 inline int tile_interior_x(int tile_y) { return tile_y == 15 ? 32 : 30; }

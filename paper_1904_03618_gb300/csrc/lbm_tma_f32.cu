@@ -10,4 +10,15 @@ template cudaError_t launch_fused_tma_batch_storage<float>(
     const void*, void*, const BatchCase*, int, int, bool, const CUtensorMap*, int, int, int, int*,
     int, cudaStream_t);
 template bool tma_config_fits_storage<float>(int, int);
+
+// SEAM forms (FP32, periodic in x and y): 34 x 15 with one stage, 34 x 12
+// with two.
+cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
+                                  const CUtensorMap* maps6, int zchunk, int* err,
+                                  cudaStream_t s) {
+  const int zc = zchunk > 0 ? zchunk : a.nz;
+  if (tile_y == 15) return launch_tma_seam_v<34, 15, 1>(src, dst, a, maps6, zc, err, s);
+  if (tile_y == 12) return launch_tma_seam_v<34, 12, 2>(src, dst, a, maps6, zc, err, s);
+  return cudaErrorInvalidValue;
+}
 }  // namespace lbm

@@ -73,6 +73,37 @@ def test_tma_matches_oracle_and_hold2(name, zchunk, tile_y, hold):
     assert diag[5] == 0
 
 
+SEAM_CASES = [(72, 37, 19), (34, 15, 6), (36, 16, 5), (130, 44, 11), (64, 28, 9)]
+
+
+@pytest.mark.parametrize("tile_y,hold", [(15, 8), (12, 7)])
+@pytest.mark.parametrize("nx,ny,nz", SEAM_CASES)
+def test_seam_form_matches_oracle_across_the_periodic_seams(nx, ny, nz, tile_y, hold):
+    """On a periodic FP32 lattice the 34 x 15 one-stage form and the 34 x 12
+    two-stage form (the library default there) stage the cells beyond the x
+    and y seams by tensor copies of the lattice's far side.  A drop centred
+    on the corner (0, 0) puts the interface across both seams and their
+    corner."""
+    pd = base(nx, ny, nz)
+    rR, rB, u = wl.droplet(nx, ny, nz, 6.0, pd["rho_in_R"], pd["rho_in_B"],
+                           velocity=(0.02, -0.01, 0.005), center=(0.5, 0.5, nz / 2.0),
+                           noise=1e-3, seed=3)
+    f0 = np.asarray(oracle.init(oracle.params_from(pd), rR, rB, u),
+                    dtype=np.float32).astype(np.float64)
+    got, diag = run(pd, f0, 3, hold, 0, tile_y=tile_y)
+    ref_gpu, _ = run(pd, f0, 3, 2, 0)
+    ref = oracle.step(oracle.params_from(pd), f0, 3)
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= 1e-5
+    assert np.abs(got - ref_gpu).max() / np.abs(ref_gpu).max() <= 1e-6
+    assert diag[5] == 0
+
+
+def test_seam_form_is_the_default_on_a_periodic_fp32_cube():
+    lat = lbm.Lattice(lbm.make_params(**base(128, 128, 128)), device=DEV)
+    assert tuple(lbm.lbm_get_fused_config(lat.ctx))[::2] == (12, 7)
+    lat.close()
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("tile_y,hold", TMA)
 def test_tma_reduced_precision(storage, tile_y, hold):
