@@ -240,40 +240,51 @@ struct TmaIssueSeamMain<TW, BY, 19> {
   __device__ __forceinline__ static void run(unsigned, const CUtensorMap*, const CUtensorMap*,
                                              int, int, int, int, unsigned) {}
 };
-// ... and, on a seam tile only, the strips: x strip from source x = xs, y
-// strip from source y = ys, corner (xs or ys < 0: none).
+// ... and, on a seam tile only, the strips a lane can read: x strip from
+// source x = xs for the directions whose sources cross that seam (e_x >= 0
+// at the low seam, xlo; e_x <= 0 at the high one), y strip from source y =
+// ys likewise, the corner where both cross (xs or ys < 0: none).
+template <int I>
+__device__ __forceinline__ bool seam_crosses(int e, bool lo) {
+  return lo ? e >= 0 : e <= 0;
+}
 template <int TW, int BY, int I>
 struct TmaIssueStrips {
   __device__ __forceinline__ static void run(unsigned block0, const SeamStripMaps& sm, int x0,
-                                             int y0, int zz, int nz, int xs, int ys,
-                                             unsigned mbar) {
+                                             int y0, int zz, int nz, int xs, int ys, bool xlo,
+                                             bool ylo, unsigned mbar) {
     constexpr int w = ex(I) == 0 ? TW + 2 : TW;
     const unsigned blk = block0 + (unsigned)(I * seam_block_bytes<TW, BY>());
     const int x = ex(I) < 0 ? x0 : x0 - 2;
     const int y = y0 - 1 - ey(I);
     const int z = wrap1(zz - ez(I), nz);
-    if (xs >= 0) tma_load_4d(blk + seam_xs_off<TW, BY>(w), sm.xs, xs, y, z, I, mbar);
-    if (ys >= 0)
+    const bool cx = xs >= 0 && seam_crosses<I>(ex(I), xlo);
+    const bool cy = ys >= 0 && seam_crosses<I>(ey(I), ylo);
+    if (cx) tma_load_4d(blk + seam_xs_off<TW, BY>(w), sm.xs, xs, y, z, I, mbar);
+    if (cy)
       tma_load_4d(blk + seam_ys_off<TW, BY>(w), ex(I) == 0 ? sm.ys1 : sm.ys0, x, ys, z, I, mbar);
-    if (xs >= 0 && ys >= 0) tma_load_4d(blk + seam_cs_off<TW, BY>(w), sm.cs, xs, ys, z, I, mbar);
-    TmaIssueStrips<TW, BY, I + 1>::run(block0, sm, x0, y0, zz, nz, xs, ys, mbar);
+    if (cx && cy) tma_load_4d(blk + seam_cs_off<TW, BY>(w), sm.cs, xs, ys, z, I, mbar);
+    TmaIssueStrips<TW, BY, I + 1>::run(block0, sm, x0, y0, zz, nz, xs, ys, xlo, ylo, mbar);
   }
 };
 template <int TW, int BY>
 struct TmaIssueStrips<TW, BY, 19> {
   __device__ __forceinline__ static void run(unsigned, const SeamStripMaps&, int, int, int, int,
-                                             int, int, unsigned) {}
+                                             int, int, bool, bool, unsigned) {}
 };
-// Bytes one plane's copies deliver on a tile with or without x / y strips.
+// Bytes one plane's copies deliver on a tile with or without x / y strips
+// (xlo / ylo: the tile's seam is the low one of its axis).
 template <int TW, int BY>
-__host__ __device__ constexpr int seam_tx_bytes(bool xstrip, bool ystrip) {
+__host__ __device__ constexpr int seam_tx_bytes(bool xstrip, bool ystrip, bool xlo, bool ylo) {
   int b = 0;
   for (int i = 0; i < 19; ++i) {
     const int w = ex(i) == 0 ? TW + 2 : TW;
+    const bool cx = xstrip && (xlo ? ex(i) >= 0 : ex(i) <= 0);
+    const bool cy = ystrip && (ylo ? ey(i) >= 0 : ey(i) <= 0);
     b += w * BY * 8;
-    if (xstrip) b += 2 * BY * 8;
-    if (ystrip) b += w * 2 * 8;
-    if (xstrip && ystrip) b += 2 * 2 * 8;
+    if (cx) b += 2 * BY * 8;
+    if (cy) b += w * 2 * 8;
+    if (cx && cy) b += 2 * 2 * 8;
   }
   return b;
 }
@@ -289,7 +300,10 @@ __device__ __forceinline__ unsigned seam_lane_off(int tx, int ty, int cx, int cy
   const int sx = cx - ex_, sy = cy - ey_;
   const bool xin = sx >= 0 && sx < nx, yin = sy >= 0 && sy < ny;
   const int xc = sx < 0 ? sx + 2 : sx - nx, yc = sy < 0 ? sy + 2 : sy - ny;
-  const bool xok = xc >= 0 && xc < 2, yok = yc >= 0 && yc < 2;
+  // only lanes of the ring and the interior (whose moments are used) look
+  // beyond a seam; the strips copied are the ones those lanes need
+  const bool used = cx >= -1 && cx <= nx && cy >= -1 && cy <= ny;
+  const bool xok = used && xc >= 0 && xc < 2, yok = used && yc >= 0 && yc < 2;
   int off = (ty * w + col) * 8;
   if (!xin && yin && xok) off = seam_xs_off<TW, BY>(w) + (ty * 2 + xc) * 8;
   if (xin && !yin && yok) off = seam_ys_off<TW, BY>(w) + (yc * w + col) * 8;
@@ -383,7 +397,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     else if (x0 + TW - 2 >= a.nx - 1) seam_xs = 0;
     if (y0 < 2) seam_ys = a.ny - 2;
     else if (y0 + BY - 2 >= a.ny - 1) seam_ys = 0;
-    TX = seam_tx_bytes<TW, BY>(seam_xs >= 0, seam_ys >= 0);
+    TX = seam_tx_bytes<TW, BY>(seam_xs >= 0, seam_ys >= 0, x0 < 2, y0 < 2);
 #pragma unroll
     for (int e = 0; e < 9; ++e)
       loff[e] = seam_lane_off<TW, BY>(tx, ty, cx, cy, e / 3 - 1, e % 3 - 1, a.nx, a.ny);
@@ -420,7 +434,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
                                          m);
         if (seam_xs >= 0 || seam_ys >= 0)
           TmaIssueStrips<TW, BY, 0>::run(st_addr(k), *strips, x0, y0, wrap1(zl, a.nz), a.nz,
-                                         seam_xs, seam_ys, m);
+                                         seam_xs, seam_ys, x0 < 2, y0 < 2, m);
       } else {
         TmaIssue<T, TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
       }
