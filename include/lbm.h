@@ -179,17 +179,20 @@ lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
 lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[16]);
 
 /* Monitored stepping without host waits: advances n >= 0 steps (as
-   lbm_step) and queues the diagnostics of the state they reach (case 0 of
-   a batch) and an asynchronous copy of their 16 slots (as lbm_diagnostics)
-   into out, which may be pinned host memory or device memory (pageable
-   host memory makes the copy synchronous).  Returns after queueing: out is
-   valid once the context stream has passed the copy (lbm_sync).  State
-   errors are reported in the slots ([5], [6], [14]), not by the return
-   value.  Errors: LBM_ERR_ARG (out NULL, n < 0), LBM_ERR_STATE,
-   LBM_ERR_CUDA. */
+   lbm_step, on the context stream) and queues the diagnostics of the state
+   they reach (case 0 of a batch) and an asynchronous copy of their 16 slots
+   (as lbm_diagnostics) into out, which may be pinned host memory or device
+   memory (pageable host memory makes the copy synchronous).  The
+   diagnostics run on a stream of the library's own (created on first use)
+   after the step, so that they overlap the next step, which only reads the
+   buffer they read; a later launch that writes that buffer waits for them.
+   Returns after queueing: out is valid after lbm_sync.  State errors are
+   reported in the slots ([5], [6], [14]), not by the return value.
+   Errors: LBM_ERR_ARG (out NULL, n < 0), LBM_ERR_STATE, LBM_ERR_CUDA. */
 lbm_status lbm_step_diagnostics_async(lbm_ctx *ctx, int n, double *out);
 
-/* Waits until all work queued on the context stream has finished. */
+/* Waits until all work queued by the context (its stream and the stream of
+   the asynchronous diagnostics) has finished. */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Copies f_i^k(x, t) -- the populations after streaming at the current

@@ -40,6 +40,13 @@ struct lbm_ctx {
   double* diag_out;         // folded sums and the error word (device)
   unsigned* diag_done;      // block counter of the diagnostics kernel
   double* diag_host;        // pinned host copy of diag_out
+  // lbm_step_diagnostics_async runs the diagnostics on a stream of their own
+  // (created on first use), so that they overlap the next step, which only
+  // reads the buffer they read; a launch that writes a buffer first waits
+  // for the last diagnostics that read it (diag_ev[b], pending diag_pend[b]).
+  cudaStream_t dstream;
+  cudaEvent_t step_ev, diag_ev[2];
+  bool diag_pend[2];
   int diag_blocks;
   float* staging;           // device staging for host-pointer transfers
   size_t staging_floats;
@@ -469,6 +476,13 @@ extern "C" lbm_status lbm_create_batch(const lbm_params* cases, int ncases,
 
 extern "C" void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
+  if (c->dstream) {
+    cudaStreamSynchronize(c->dstream);
+    cudaStreamDestroy(c->dstream);
+    cudaEventDestroy(c->step_ev);
+    cudaEventDestroy(c->diag_ev[0]);
+    cudaEventDestroy(c->diag_ev[1]);
+  }
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   release(c);
@@ -521,12 +535,24 @@ static lbm_status check_case(lbm_ctx* c, int k) {
   return LBM_OK;
 }
 
+// The context stream waits for the asynchronous diagnostics that still read
+// buffer b (b < 0: both buffers, and the diagnostics scratch).
+static lbm_status settle_diag(lbm_ctx* c, int b) {
+  for (int q = 0; q < 2; ++q) {
+    if ((b >= 0 && q != b) || !c->diag_pend[q]) continue;
+    LBM_CUDA(c, cudaStreamWaitEvent(c->stream, c->diag_ev[q], 0), "cudaStreamWaitEvent");
+    c->diag_pend[q] = false;
+  }
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_R,
                                             const float* rho_B, const float* u) {
   if (!c) return LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
   if (!rho_R || !rho_B || !u) return fail(c, LBM_ERR_ARG, "NULL field pointer");
+  if ((st = settle_diag(c, -1)) != LBM_OK) return st;
   CaseRec& r = c->cases[k];
   const size_t N = (size_t)r.N;
   const bool all_dev = is_device_ptr(rho_R) && is_device_ptr(rho_B) && is_device_ptr(u);
@@ -624,6 +650,10 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
   for (int k = 0; k < c->ncases; ++k)
     if (!c->cases[k].initialized)
       return fail(c, LBM_ERR_STATE, "lbm_step before every case was initialised (case %d)", k);
+  {  // one step writes the other buffer only; more steps write both
+    lbm_status sd = settle_diag(c, n == 1 ? (c->cur ^ 1) : -1);
+    if (sd != LBM_OK) return sd;
+  }
   // CUDA graphs need a capturable stream (not the legacy default stream).
   const bool graphs = c->use_graph && c->stream != nullptr && n >= 4;
   lbm_status st;
@@ -701,11 +731,11 @@ extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
   return lbm_batch_moments(c, 0, rho_R, rho_B, u);
 }
 
-static lbm_status enqueue_diag(lbm_ctx* c, int k) {
+static lbm_status enqueue_diag(lbm_ctx* c, int k, cudaStream_t s) {
   const CaseRec& r = c->cases[k];
   LBM_CUDA(c, lbm::launch_diag(c->storage, case_buffer(c, c->cur, k), r.args,
                                c->diag_part, c->diag_blocks, c->diag_done, c->d_flags,
-                               c->steps, c->diag_out, c->stream),
+                               c->steps, c->diag_out, s),
            "diagnostics kernel");
   return LBM_OK;
 }
@@ -715,7 +745,8 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
   if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "diagnostics before init");
-  if ((st = enqueue_diag(c, k)) != LBM_OK) return st;
+  if ((st = settle_diag(c, -1)) != LBM_OK) return st;  // shares the scratch
+  if ((st = enqueue_diag(c, k, c->stream)) != LBM_OK) return st;
   LBM_CUDA(c, cudaMemcpyAsync(c->diag_host, c->diag_out, sizeof(double) * 16,
                               cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync D2H");
@@ -735,18 +766,35 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
 
 extern "C" lbm_status lbm_step_diagnostics_async(lbm_ctx* c, int n, double* out) {
   if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
+  if (!c->dstream) {
+    LBM_CUDA(c, cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking),
+             "cudaStreamCreateWithFlags");
+    LBM_CUDA(c, cudaEventCreateWithFlags(&c->step_ev, cudaEventDisableTiming),
+             "cudaEventCreateWithFlags");
+    for (int q = 0; q < 2; ++q)
+      LBM_CUDA(c, cudaEventCreateWithFlags(&c->diag_ev[q], cudaEventDisableTiming),
+               "cudaEventCreateWithFlags");
+  }
   lbm_status st = lbm_step(c, n);
   if (st != LBM_OK) return st;
-  if ((st = enqueue_diag(c, 0)) != LBM_OK) return st;
+  // the diagnostics of the state just reached, on their own stream after
+  // the step; they read buffer cur, which the next step only reads
+  LBM_CUDA(c, cudaEventRecord(c->step_ev, c->stream), "cudaEventRecord");
+  LBM_CUDA(c, cudaStreamWaitEvent(c->dstream, c->step_ev, 0), "cudaStreamWaitEvent");
+  if ((st = enqueue_diag(c, 0, c->dstream)) != LBM_OK) return st;
   LBM_CUDA(c, cudaMemcpyAsync(out, c->diag_out, sizeof(double) * 16, cudaMemcpyDefault,
-                              c->stream),
+                              c->dstream),
            "cudaMemcpyAsync of the diagnostics");
+  LBM_CUDA(c, cudaEventRecord(c->diag_ev[c->cur], c->dstream), "cudaEventRecord");
+  c->diag_pend[c->cur] = true;
   c->err[0] = 0;
   return LBM_OK;
 }
 
 extern "C" lbm_status lbm_sync(lbm_ctx* c) {
   if (!c) return LBM_ERR_ARG;
+  if (c->dstream) LBM_CUDA(c, cudaStreamSynchronize(c->dstream), "stream sync");
+  for (int q = 0; q < 2; ++q) c->diag_pend[q] = false;
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   c->err[0] = 0;
   return LBM_OK;
@@ -814,6 +862,7 @@ extern "C" lbm_status lbm_batch_set_f(lbm_ctx* c, int k, const float* f) {
   if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
+  if ((st = settle_diag(c, -1)) != LBM_OK) return st;
   CaseRec& r = c->cases[k];
   const size_t n = 38 * (size_t)r.N;
   const float* src = f;
@@ -853,6 +902,10 @@ extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
 
 extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
   if (!c || !src) return c ? fail(c, LBM_ERR_ARG, "src is NULL") : LBM_ERR_ARG;
+  {
+    lbm_status st = settle_diag(c, -1);
+    if (st != LBM_OK) return st;
+  }
   LBM_CUDA(c, cudaMemcpyAsync(c->pop[c->cur], src, lbm_population_bytes(c),
                               cudaMemcpyDefault, c->stream),
            "cudaMemcpyAsync");

@@ -379,8 +379,9 @@ def test_every_diagnostics_slot_against_fp64_sums(shape, wall, storage, steps):
     assert abs(d[13] - neg.sum()) <= near.sum()
 
 
+@pytest.mark.parametrize("nstep", [1, 2])
 @pytest.mark.parametrize("where", ["pinned", "device"])
-def test_async_monitored_steps_match_synchronous_diagnostics(where):
+def test_async_monitored_steps_match_synchronous_diagnostics(where, nstep):
     pd = base(40, 24, 16, wall=(0, 0, 1))
     f0 = torch.tensor(droplet_state(pd, 6.0, (0.02, 0.0, 0.0)), dtype=torch.float32,
                       device=DEV)
@@ -388,18 +389,24 @@ def test_async_monitored_steps_match_synchronous_diagnostics(where):
     lb = lbm.Lattice(lbm.make_params(**pd), device=DEV, stream=torch.cuda.Stream(DEV))
     la.set_f(f0)
     lb.set_f(f0)
-    K = 6
+    K = 9
     out = torch.zeros((K, 16), dtype=torch.float64)
     out = out.pin_memory() if where == "pinned" else out.to(DEV)
-    for k in range(K):   # queued back to back, one host wait at the end
-        lbm.lbm_step_diagnostics_async(la.ctx, 2, out[k])
+    # queued back to back, one host wait at the end; with one step per call
+    # the diagnostics of a state overlap the next step (their own stream)
+    for k in range(K):
+        lbm.lbm_step_diagnostics_async(la.ctx, nstep, out[k])
     lbm.lbm_sync(la.ctx)
     got = out.cpu().numpy()
     for k in range(K):
-        lb.step(2)
+        lb.step(nstep)
         ref = lb.diagnostics()
         assert np.array_equal(got[k], ref), k       # same kernels, same state
-        assert got[k][12] == 2 * (k + 1) and got[k][14] == 0
+        assert got[k][12] == nstep * (k + 1) and got[k][14] == 0
+    # the states themselves agree, and a synchronous call after asynchronous
+    # ones sees the same scratch
+    assert np.array_equal(la.get_f().cpu().numpy(), lb.get_f().cpu().numpy())
+    assert np.array_equal(la.diagnostics(), lb.diagnostics())
     la.close()
     lb.close()
 
