@@ -198,8 +198,8 @@ int seam12_zchunk(const StepArgs& a, int sms) {
 }
 
 bool seam_eligible(const StepArgs& a, int storage) {
-  return storage == 0 && tma_eligible(a, storage) && !a.wx && !a.wy && !a.wz &&
-         a.nx >= kTmaTW[2] && a.ny >= kTmaBY[2];
+  return storage == 0 && tma_eligible(a, storage) && !a.wx && !a.wy && a.nx >= kTmaTW[2] &&
+         a.ny >= kTmaBY[2];
 }
 
 cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,

@@ -33,7 +33,8 @@
 // do the first and last plane of a lattice with walls in z (they get no
 // copies).
 //
-// Periodic seams (SEAM form: FP32, lattices periodic in x and y; a 34 x 15
+// Periodic seams (SEAM form: FP32, lattices periodic in x and y -- walls in
+// z allowed, their first and last plane pulled from global memory; a 34 x 15
 // tile with one stage or a 34 x 12 tile with two).  A tensor copy cannot wrap around a periodic axis, so a tile on a
 // seam gets, per direction, up to three more copies into its stage: the two
 // columns beyond the x seam (a 2 x BY box read from the other side of the
@@ -367,8 +368,8 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
                                           int ze, unsigned char* smem, unsigned G0,
                                           int* __restrict__ err,
                                           const SeamStripMaps* strips = nullptr) {
-  static_assert(!SEAM || (tma_pair_bytes<T>() == 8 && !WALLS),
-                "the SEAM form is FP32 and periodic in x and y");
+  static_assert(!SEAM || tma_pair_bytes<T>() == 8,
+                "the SEAM form is FP32, periodic in x and y (walls in z allowed)");
   constexpr int SB = tma_stage_bytes<T, TW, BY, SEAM>();
   constexpr int HV = tma_hold_vals<T, TW, BY, NS, SEAM>();
   using Pair = typename Store<T>::Pair;
@@ -450,19 +451,26 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     const int zl = zb - 1 + k;
     if (!g.plane_ok(a, zl)) return;
     float rR = 0.f, rB = 0.f;
+    bool from_stage = false;
     if constexpr (SEAM) {
-      float2 rho = make_float2(0.f, 0.f);
-      StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
-      rR = rho.x;
-      rB = rho.y;
-    } else if (col_fast && staged(zl)) {
-      float2 rho = make_float2(0.f, 0.f);
-      StageReduce<T, TW, BY, 0>::run(stage0 + stage_of(k) * SB, ty, col0, a, f, rho);
-      rR = rho.x;
-      rB = rho.y;
+      if (staged(zl)) {  // every lane (the first and last plane of z walls: global)
+        float2 rho = make_float2(0.f, 0.f);
+        StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
+        rR = rho.x;
+        rB = rho.y;
+        from_stage = true;
+      }
     } else {
-      pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f, rR, rB);
+      if (col_fast && staged(zl)) {
+        float2 rho = make_float2(0.f, 0.f);
+        StageReduce<T, TW, BY, 0>::run(stage0 + stage_of(k) * SB, ty, col0, a, f, rho);
+        rR = rho.x;
+        rB = rho.y;
+        from_stage = true;
+      }
     }
+    if (!from_stage)
+      pull_reduce<T, WALLS>(srcp, plane, a, g.co, g.plane(a, wrap1(zl, a.nz)), f, rR, rB);
     const Macro m = macro_total(a, f, rR, rB);
     hu[0] = rR;
     hu[1] = rB;
@@ -588,7 +596,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
 // SEAM form (FP32, periodic in x and y, one stage): the source buffer's six
 // tensor maps (main TW, main TW + 2, x strip, y strip TW, y strip TW + 2,
 // corner), each a kernel parameter of its own like the other forms' maps.
-template <int TW, int BY, int NS>
+template <int TW, int BY, int NS, bool WALLS>
 __global__ void __launch_bounds__(TW* BY, 1)
     k_fused_tma_seam(const float* __restrict__ src, float* __restrict__ dst,
                      const __grid_constant__ StepArgs a,
@@ -610,11 +618,11 @@ __global__ void __launch_bounds__(TW* BY, 1)
   tma_init_barriers(tma_mbar_bytes<float, TW, BY, NS, true>(smem), NS);
   __syncthreads();
   const SeamStripMaps strips = {&mxs, &mys0, &mys1, &mcs};
-  tma_chunk<float, false, TW, BY, NS, true>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y,
+  tma_chunk<float, WALLS, TW, BY, NS, true>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y,
                                             zb, ze, smem, 0u, err, &strips);
 }
 
-template <int TW, int BY, int NS>
+template <int TW, int BY, int NS, bool WALLS>
 static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs& a,
                                      const CUtensorMap* maps6, int zc, int* err,
                                      cudaStream_t s) {
@@ -622,14 +630,14 @@ static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs&
   static bool attr_set = false;
   constexpr int bytes = tma_smem_bytes<float, TW, BY, NS, true>();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS>,
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS, WALLS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 blk(TW, BY);
   dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
-  k_fused_tma_seam<TW, BY, NS><<<grd, blk, bytes, s>>>((const float*)src, (float*)dst, a, maps6[0],
+  k_fused_tma_seam<TW, BY, NS, WALLS><<<grd, blk, bytes, s>>>((const float*)src, (float*)dst, a, maps6[0],
                                                    maps6[1], maps6[2], maps6[3], maps6[4],
                                                    maps6[5], zc, err);
   return cudaGetLastError();

@@ -81,7 +81,8 @@ int tma_kind(int tile_y);  // -1 for a tile_y without a TMA form
 cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
                            CUtensorMap maps[2]);
 // SEAM forms of the TMA step (34 x 15 threads with one stage, 34 x 12 with
-// two; tile_y 15 or 12): FP32 storage, periodic in x and y, nx >= 34 and
+// two; tile_y 15 or 12): FP32 storage, periodic in x and y (walls in z
+// allowed), nx >= 34 and
 // ny >= 15 (no tile on both seams of an axis), TMA eligible.  Their six maps
 // (main 34 and 36 wide, x strip 2 wide, y strips 34 and 36 x 2, corner
 // 2 x 2; main and x strip tile_y rows) over the source buffer.

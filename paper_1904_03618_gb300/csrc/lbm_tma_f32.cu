@@ -11,14 +11,19 @@ template cudaError_t launch_fused_tma_batch_storage<float>(
     int, cudaStream_t);
 template bool tma_config_fits_storage<float>(int, int);
 
-// SEAM forms (FP32, periodic in x and y): 34 x 15 with one stage, 34 x 12
-// with two.
+// SEAM forms (FP32, periodic in x and y, walls in z allowed): 34 x 15 with
+// one stage, 34 x 12 with two.
 cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
                                   const CUtensorMap* maps6, int zchunk, int* err,
                                   cudaStream_t s) {
   const int zc = zchunk > 0 ? zchunk : a.nz;
-  if (tile_y == 15) return launch_tma_seam_v<34, 15, 1>(src, dst, a, maps6, zc, err, s);
-  if (tile_y == 12) return launch_tma_seam_v<34, 12, 2>(src, dst, a, maps6, zc, err, s);
+  const bool zwalls = a.wz != 0;  // x and y are periodic (seam_eligible)
+  if (tile_y == 15)
+    return zwalls ? launch_tma_seam_v<34, 15, 1, true>(src, dst, a, maps6, zc, err, s)
+                  : launch_tma_seam_v<34, 15, 1, false>(src, dst, a, maps6, zc, err, s);
+  if (tile_y == 12)
+    return zwalls ? launch_tma_seam_v<34, 12, 2, true>(src, dst, a, maps6, zc, err, s)
+                  : launch_tma_seam_v<34, 12, 2, false>(src, dst, a, maps6, zc, err, s);
   return cudaErrorInvalidValue;
 }
 }  // namespace lbm

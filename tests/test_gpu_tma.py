@@ -76,15 +76,17 @@ def test_tma_matches_oracle_and_hold2(name, zchunk, tile_y, hold):
 SEAM_CASES = [(72, 37, 19), (34, 15, 6), (36, 16, 5), (130, 44, 11), (64, 28, 9)]
 
 
+@pytest.mark.parametrize("zwall", [0, 1])
 @pytest.mark.parametrize("tile_y,hold", [(15, 8), (12, 7)])
 @pytest.mark.parametrize("nx,ny,nz", SEAM_CASES)
-def test_seam_form_matches_oracle_across_the_periodic_seams(nx, ny, nz, tile_y, hold):
+def test_seam_form_matches_oracle_across_the_periodic_seams(nx, ny, nz, tile_y, hold, zwall):
     """On a periodic FP32 lattice the 34 x 15 one-stage form and the 34 x 12
     two-stage form (the library default there) stage the cells beyond the x
     and y seams by tensor copies of the lattice's far side.  A drop centred
     on the corner (0, 0) puts the interface across both seams and their
-    corner."""
-    pd = base(nx, ny, nz)
+    corner.  With walls in z (zwall = 1) the first and last plane are pulled
+    from global memory, the rest staged."""
+    pd = base(nx, ny, nz, wall=(0, 0, zwall))
     rR, rB, u = wl.droplet(nx, ny, nz, 6.0, pd["rho_in_R"], pd["rho_in_B"],
                            velocity=(0.02, -0.01, 0.005), center=(0.5, 0.5, nz / 2.0),
                            noise=1e-3, seed=3)
