@@ -238,7 +238,13 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
    tile_y = 8 is a 32 x 8 thread tile, tile_y = 16 a 16 x 16 thread tile
    (interior 14 x 14; with hold 7 for 16-bit storage only) and tile_y = 15
    (hold 7 and 8 only) a 34 x 15 thread tile (interior 32 x 13, one CTA per
-   SM).  The TMA waits are bounded and report LBM_ERR_TIMEOUT through
+   SM).  On FP32 single lattices periodic in x and y (walls in z allowed)
+   with nx >= 34 and ny >= 15, the TMA forms stage the cells beyond the
+   periodic x / y seams by tensor copies of the lattice's far side instead
+   of pulling them from global memory (the seam forms): tile_y = 15 with
+   hold 8 (one stage), and tile_y = 12 with hold 7 -- a 34 x 12 thread tile
+   (interior 32 x 10) with two stages, accepted only there and the default
+   there.  The TMA waits are bounded and report LBM_ERR_TIMEOUT through
    lbm_diagnostics.
    Errors: LBM_ERR_ARG. */
 lbm_status lbm_set_fused_config(lbm_ctx *ctx, int tile_y, int zchunk, int hold);

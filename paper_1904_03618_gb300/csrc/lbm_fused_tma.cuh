@@ -27,10 +27,11 @@
 //   Rows y0 - 1 - e_iy ... (BY rows); plane z - e_iz, wrapped periodically
 //   in z.  Each box is padded to a multiple of 128 bytes in the stage.
 // A copy whose box reaches beyond the lattice in x or y fills zeros there
-// (TMA bounds handling); the cells whose sources lie beyond the lattice in x
-// or y -- the periodic wrap and bounce-back links, i.e. cells on the first
-// and last row and column -- pull from global memory as k_fused does, and so
-// do the first and last plane of a lattice with walls in z (they get no
+// (TMA bounds handling); in the plain form the cells whose sources lie
+// beyond the lattice in x or y -- the periodic wrap and bounce-back links,
+// i.e. cells on the first and last row and column -- pull from global memory
+// as k_fused does (the SEAM form below stages the periodic ones), and so do
+// the first and last plane of a lattice with walls in z (they get no
 // copies).
 //
 // Periodic seams (SEAM form: FP32, lattices periodic in x and y -- walls in

@@ -100,6 +100,27 @@ def test_seam_form_matches_oracle_across_the_periodic_seams(nx, ny, nz, tile_y, 
     assert diag[5] == 0
 
 
+def test_two_stage_seam_tile_is_accepted_only_where_it_applies():
+    ok = lbm.Lattice(lbm.make_params(**base(64, 30, 9, wall=(0, 0, 1))), device=DEV)
+    lbm.lbm_set_fused_config(ok.ctx, 12, 0, 7)
+    assert lbm.lbm_get_fused_config(ok.ctx)[0] == 12
+    ok.close()
+    refused = [dict(base(64, 30, 9, wall=(1, 0, 0))),            # x walls
+               dict(base(64, 30, 9), collision="bgk"),           # BGK: shared-memory hold
+               dict(base(30, 30, 9)),                            # nx < 34
+               dict(base(64, 30, 9), storage="f16")]             # 16-bit storage
+    for d in refused:
+        storage = d.pop("storage", "f32")
+        lat = lbm.Lattice(lbm.make_params(storage=storage, **d), device=DEV)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_set_fused_config(lat.ctx, 12, 0, 7)
+        assert ei.value.status == lbm.LBM_ERR_ARG
+        for hold in (2, 8):
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_set_fused_config(lat.ctx, 12, 0, hold)
+        lat.close()
+
+
 def test_seam_form_is_the_default_on_a_periodic_fp32_cube():
     lat = lbm.Lattice(lbm.make_params(**base(128, 128, 128)), device=DEV)
     assert tuple(lbm.lbm_get_fused_config(lat.ctx))[::2] == (12, 7)
