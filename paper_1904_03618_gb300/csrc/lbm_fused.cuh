@@ -594,13 +594,14 @@ template <typename T, bool WALLS>
 static cudaError_t launch_fused_async(const void* src, void* dst,
                                       const StepArgs& a, int zc,
                                       cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = device_slot();
   const int bytes = (int)sizeof(AsyncSmem<T>);
-  if (!attr_set) {
+  if (!attr_set[dv]) {
     cudaError_t e = cudaFuncSetAttribute(
         k_fused_async<T, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[dv] = true;
   }
   dim3 blk(kTileW, kAsyncBY);
   dim3 grd((a.nx + kTileW - 3) / (kTileW - 2), (a.ny + kAsyncBY - 3) / (kAsyncBY - 2),
@@ -612,13 +613,14 @@ static cudaError_t launch_fused_async(const void* src, void* dst,
 template <typename T, bool WALLS>
 static cudaError_t launch_fused2(const void* src, void* dst, const StepArgs& a,
                                  int zc, cudaStream_t s) {
-  static bool attr_set = false;
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = device_slot();
   const int bytes = (int)sizeof(Fused2Smem);
-  if (!attr_set) {
+  if (!attr_set[dv]) {
     cudaError_t e = cudaFuncSetAttribute(
         k_fused2<T, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[dv] = true;
   }
   dim3 blk(kTileW, 8);
   dim3 grd((a.nx + kTileW - 3) / (kTileW - 2), (a.ny + kRows2 - 3) / (kRows2 - 2),
@@ -658,7 +660,8 @@ template <typename T, int BY, bool WALLS, int HOLD, int MINB, bool BGK = false>
 static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* cases,
                                   int ncases, int total_items, int zc, int sms,
                                   cudaStream_t s) {
-  static int per_sm = 0;  // resident CTAs per SM, queried once
+  static int per_sm_dev[kMaxDevices] = {};  // resident CTAs per SM, queried once
+  int& per_sm = per_sm_dev[device_slot()];
   if (per_sm == 0) {
     int q = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(

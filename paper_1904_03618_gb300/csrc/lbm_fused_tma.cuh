@@ -628,13 +628,14 @@ static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs&
                                      const CUtensorMap* maps6, int zc, int* err,
                                      cudaStream_t s) {
   static_assert(tma_fits<float, TW, BY, NS, true>(), "SEAM stages do not fit");
-  static bool attr_set = false;
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = device_slot();
   constexpr int bytes = tma_smem_bytes<float, TW, BY, NS, true>();
-  if (!attr_set) {
+  if (!attr_set[dv]) {
     cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS, WALLS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[dv] = true;
   }
   dim3 blk(TW, BY);
   dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
@@ -705,13 +706,14 @@ static cudaError_t launch_tma_v(const void* src, void* dst, const StepArgs& a,
   if constexpr (!tma_fits<T, TW, BY, NS>()) {
     return cudaErrorInvalidValue;
   } else {
-    static bool attr_set = false;
+    static bool attr_set[kMaxDevices] = {};
+    const int dv = device_slot();
     constexpr int bytes = tma_smem_bytes<T, TW, BY, NS>();
-    if (!attr_set) {
+    if (!attr_set[dv]) {
       cudaError_t e = cudaFuncSetAttribute(k_fused_tma<T, WALLS, TW, BY, NS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       if (e != cudaSuccess) return e;
-      attr_set = true;
+      attr_set[dv] = true;
     }
     dim3 blk(TW, BY);
     dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
@@ -755,7 +757,8 @@ static cudaError_t launch_tma_batch_v(const void* src, void* dst, const BatchCas
   if constexpr (!tma_fits<T, TW, BY, NS>()) {
     return cudaErrorInvalidValue;
   } else {
-    static int per_sm = 0;  // resident CTAs per SM, queried once
+    static int per_sm_dev[kMaxDevices] = {};  // resident CTAs per SM, queried once
+    int& per_sm = per_sm_dev[device_slot()];
     constexpr int bytes = tma_smem_bytes<T, TW, BY, NS>();
     if (per_sm == 0) {
       cudaError_t e = cudaFuncSetAttribute(k_fused_tma_batch<T, WALLS, TW, BY, NS>,

@@ -10,6 +10,17 @@
 
 namespace lbm {
 
+// Launch-time facts that belong to a device's context (function attributes,
+// occupancy) are cached per device, so that one process may drive several
+// GPUs (device ordinals from 64 up share slot 0's cache).
+constexpr int kMaxDevices = 64;
+inline int device_slot() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+  return d;
+}
+
+
 constexpr int kDiagSlots = 13;  // accumulated slots of lbm_diagnostics
 
 // Host helpers of the C-ABI layer.  Errors without a context are recorded

@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
 // K split for products with few row tiles and many K slices (linear
 // epilogues only: no bias, no activation); C is zeroed and the CTAs add.
 static int choose_splits(const GemmArgs& g) {
-  static int sms = 0;
+  static int sms_dev[kMaxDevices] = {};
+  int& sms = sms_dev[device_slot()];
   if (sms == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -359,7 +360,8 @@ static int choose_splits(const GemmArgs& g) {
 cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
   GemmArgs g = g_in;
   g.splits = choose_splits(g);
-  static bool attr = false;
+  static bool attr_dev[kMaxDevices] = {};
+  bool& attr = attr_dev[device_slot()];
   // 100 KB of shared memory per CTA keeps at most two CTAs on an SM, so
   // their TMEM allocations (<= 256 columns each) never exceed the SM's 512.
   const int bytes = (int)sizeof(GemmSmem) + 1024 > 100 * 1024 ? (int)sizeof(GemmSmem) + 1024

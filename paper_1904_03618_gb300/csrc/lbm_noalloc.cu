@@ -23,7 +23,6 @@ namespace lbm {
 namespace {
 
 constexpr long long kNoAllocMaxCells = 1LL << 18;  // 262,144 cells, e.g. 64^3
-constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; holds the last call's phase field.
 static __device__ __align__(256) float4 g_noalloc_phase[kNoAllocMaxCells];
