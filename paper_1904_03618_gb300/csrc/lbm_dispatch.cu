@@ -1,4 +1,8 @@
 // Storage-type dispatch and launch configuration of the fused step.
+#include <algorithm>
+#include <functional>
+#include <vector>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -182,15 +186,39 @@ cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int
 }
 
 int seam12_zchunk(const StepArgs& a, int sms) {
+  // One CTA per SM; the hardware hands the CTAs out in launch order (tile
+  // columns fastest, then z chunks) to whichever SM falls free, so a step
+  // lasts as long as that list schedule.  A CTA of p planes costs p + 3
+  // plane-times (two halo planes and a pipeline start).  The full chunks all
+  // last the same and fill the SMs round by round; the shorter last chunk's
+  // CTAs are placed one by one.  Over 6..32 planes at 128^3..256^3 this
+  // picks the measured fastest chunk, where counting whole rounds of
+  // equal CTAs picked 16 planes at 128^3 (4.5 % slower than 24).
+  constexpr double kOverhead = 3.0;
   const long long cols = (long long)((a.nx + 31) / 32) * ((a.ny + 9) / 10);
-  const long long slots = sms > 0 ? sms : 152;
+  const int slots = sms > 0 ? sms : 152;
+  std::vector<double> heap((size_t)slots);
   int best_zc = 12;
-  double best_cost = 1e300;
-  for (int zc = 6; zc <= 24; ++zc) {
-    const long long ctas = cols * ((a.nz + zc - 1) / zc);
-    const double cost = (double)((ctas + slots - 1) / slots) * (zc + 1.5);
-    if (cost <= best_cost + 1e-9) {
-      best_cost = cost;
+  double best_span = 1e300;
+  for (int zc = 6; zc <= 32; ++zc) {
+    const long long full = (long long)(a.nz / zc) * cols;
+    const int tail = a.nz % zc;
+    const double d = zc + kOverhead;
+    const long long rounds = full / slots, extra = full % slots;
+    for (int j = 0; j < slots; ++j) heap[(size_t)j] = (double)(rounds + (j < extra)) * d;
+    double span = (double)(rounds + (extra > 0)) * d;
+    if (tail > 0) {
+      auto later = std::greater<double>();
+      std::make_heap(heap.begin(), heap.end(), later);
+      for (long long c = 0; c < cols; ++c) {
+        std::pop_heap(heap.begin(), heap.end(), later);
+        heap.back() += tail + kOverhead;
+        span = std::max(span, heap.back());
+        std::push_heap(heap.begin(), heap.end(), later);
+      }
+    }
+    if (span <= best_span + 1e-9) {
+      best_span = span;
       best_zc = zc;
     }
   }

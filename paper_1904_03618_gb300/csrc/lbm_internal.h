@@ -103,8 +103,8 @@ cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
 cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
                                   const CUtensorMap* maps6, int zchunk, int* err,
                                   cudaStream_t s);
-// z chunk of the 34 x 12 two-stage SEAM form (the rounds-of-CTAs model of
-// tma_default_config over its tile columns).
+// z chunk of the 34 x 12 two-stage SEAM form: the one whose list schedule of
+// CTAs over the SMs ends first.
 int seam12_zchunk(const StepArgs& a, int sms);
 bool tma_config_fits(int storage, int kind, int ns);
 // Interior width of a tile (30, or 32 for the 34 x 15 tile, tile_y 15).
