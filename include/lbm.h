@@ -80,7 +80,8 @@ typedef enum {
    brackets; see the cited equations for meaning. */
 typedef struct {
   int nx, ny, nz;      /* lattice size, each >= 1, ny and nz <= 65535,
-                          nx*ny*nz < 226 million                            */
+                          nx*ny*nz < 226 million (the in-place calls:
+                          limited by device memory only)                    */
   int wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on
                           both faces (wall at -1/2 and n - 1/2); Sec. IV.B-D;
                           2 moving plates through the first and last layer
@@ -317,6 +318,55 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
    thread. */
 lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
                             float *f_out, void *cuda_stream);
+
+/* ---- In-place step (AA access pattern) ----------------------------------
+   The step of Eq. 1-2 (the same collision, forcing, perturbation,
+   recolouring, walls, wetting rule and BGK option as lbm_step) on ONE
+   population array, float32 [2][19][N] (k = 0 red, 1 blue; cell = (z * ny
+   + y) * nx + x), updated in place: 152 bytes per cell plus a 16-byte
+   scratch, against 304 for the two buffers of a context.  Cell indices are
+   64-bit: nx*ny*nz is limited by device memory only (ny, nz <= 65535).  The
+   paper streams between two arrays; this is a deployment variant with the
+   same result up to FP32 rounding.
+   A state has a parity.  Even (0): f[k][i][x] = f_i^k(x, t), after
+   streaming, the layout of lbm_set_f / lbm_get_f.  Odd (1): f[k][opp(i)][x]
+   = f_i^{k,+}(x, t - 1), the post-collision value before streaming, so
+   f_i^k(x, t) is found at f[k][opp(i)][x - e_i], or at f[k][i][x] where
+   x - e_i lies beyond a wall; e_i in the order of Eq. 5, where opp pairs
+   the directions (1,2), (3,4), ..., (17,18).  A step turns one parity into the
+   other; the caller keeps track of it (after lbm_step_inplace with n steps
+   the parity is (parity + n) mod 2).
+   Each step runs two kernels: the phase field (rho^N, Qbar) of every cell
+   into the scratch, then the in-place collision (488 bytes of memory
+   traffic per cell, against 304 for lbm_step's fused kernel).
+   Moving plates (wall = 2) are rejected with LBM_ERR_ARG.  p->storage and
+   p->kernel are ignored (FP32).  All arrays are device memory owned by the
+   caller; work is queued on cuda_stream (a cudaStream_t, NULL = legacy
+   default stream) and the calls return without waiting.  Errors
+   (LBM_ERR_ARG, LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the
+   calling thread. */
+
+/* Equilibrium populations (Eq. 18 with the improved coefficient when
+   p->improved, else Eq. 6) of the fields rho_R, rho_B (N floats each) and
+   u (u_x, u_y, u_z planes, 3N floats) written into f as an even state.  f
+   must not overlap the fields. */
+lbm_status lbm_inplace_init(const lbm_params *p, const float *rho_R,
+                            const float *rho_B, const float *u, float *f,
+                            void *cuda_stream);
+
+/* nsteps >= 0 time steps of the state f of the given parity (0 or 1), in
+   place.  scratch: N float4 (16 bytes per cell, 16-byte aligned), not
+   overlapping f; its contents on entry are ignored. */
+lbm_status lbm_step_inplace(const lbm_params *p, float *f, int parity,
+                            int nsteps, void *scratch, void *cuda_stream);
+
+/* Reads the state f of the given parity: f_out (may be NULL) receives
+   f_i^k(x, t) in the even layout, rho_R, rho_B (N floats) and u (3N)
+   (each may be NULL) the moments of lbm_moments (u with the half-force
+   shift of Eq. 4).  At least one output; none may overlap f. */
+lbm_status lbm_inplace_read(const lbm_params *p, const float *f, int parity,
+                            float *f_out, float *rho_R, float *rho_B,
+                            float *u, void *cuda_stream);
 
 /* ---- Surrogate network (tensor cores) -----------------------------------
    A fully connected network x -> tanh(x W_1 + b_1) -> ... (depth hidden

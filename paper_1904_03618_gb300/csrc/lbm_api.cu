@@ -98,7 +98,8 @@ static bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static lbm_status validate(const lbm_params* p) {
+// Every check but the 32-bit pair-offset limit of the two-buffer kernels.
+static lbm_status validate_any_size(const lbm_params* p) {
   if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1)
     return fail(nullptr, LBM_ERR_ARG, "nx, ny, nz must be >= 1");
@@ -152,6 +153,12 @@ static lbm_status validate(const lbm_params* p) {
       return fail(nullptr, LBM_ERR_ARG, "force and gravity must be finite");
   if (!isfinite(p->ref_R) || !isfinite(p->ref_B))
     return fail(nullptr, LBM_ERR_ARG, "ref_R and ref_B must be finite");
+  return LBM_OK;
+}
+
+static lbm_status validate(const lbm_params* p) {
+  const lbm_status st = validate_any_size(p);
+  if (st != LBM_OK) return st;
   long long N = (long long)p->nx * p->ny * p->nz;
   // pair offsets (direction * padded plane + cell) are 32-bit
   if ((N + 64) * 19 >= (1LL << 32))
@@ -218,6 +225,7 @@ static StepArgs derive_args(const lbm_params* p, long long plane) {
 // Shared with the other host translation units (declared in lbm_internal.h).
 namespace lbm {
 lbm_status validate_params(const lbm_params* p) { return validate(p); }
+lbm_status validate_params_any_size(const lbm_params* p) { return validate_any_size(p); }
 StepArgs derive_step_args(const lbm_params* p, long long plane) {
   return derive_args(p, plane);
 }

@@ -1,0 +1,337 @@
+// lbm_step_inplace and its companions: the time step on ONE population
+// array, updated in place with the AA access pattern.  Half the population
+// memory of the two-buffer context (168 bytes per cell with the scratch,
+// against 304), and 64-bit cell indices, so a lattice is bounded by device
+// memory alone.
+//
+// Layout: f[(k * 19 + i) * N + cell], k = 0 red, 1 blue,
+// cell = (z * ny + y) * nx + x, FP32.  A state has a parity:
+//   even: slot (i, x) holds f_i(x, t), the population after streaming;
+//   odd:  slot (opp(i), x) holds f_i^+(x, t - 1), the post-collision value
+//         before streaming, so f_i(x, t) sits at slot (opp(i), x - e_i) or,
+//         where x - e_i lies beyond a wall (halfway bounce-back), at slot
+//         (i, x).
+// A step from an even state reads a cell's 38 values from its own slots,
+// collides and writes f_i^+(x) to slot (opp(i), x): the state turns odd and
+// no value moves between cells.  A step from an odd state reads f_i(x, t)
+// where the odd layout keeps it, collides and writes f_i^+(x) to slot
+// (i, x + e_i) -- slot (opp(i), x) where x + e_i lies beyond a wall --
+// which is where the next even state keeps f_i(x + e_i, t + 1).  In both,
+// the slot written for direction i is the slot read for direction opp(i):
+// every cell writes exactly the 38 slots it read, so one thread per cell
+// that reads all of them before writing any races with no other thread.
+//
+// The colour-gradient step also needs the moments of the 18 neighbours at
+// time t (the Eq. 49 stencils of rho^N and Qbar), and a neighbour's slots
+// may already hold time t + 1 when a cell runs.  So each step is two
+// passes: the phase field (rho^N, Qbar) of every cell into a caller-owned
+// scratch of 16 bytes per cell, then the in-place collision.  Algorithmic
+// traffic per cell and step: 152 B read + 16 B written, then 152 + 16 B
+// read and 152 B written -- 488 B, against the 304 B of the fused
+// two-buffer step.
+#include <cstdint>
+
+#include "lbm_device.cuh"
+#include "lbm_equilibrium.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kInplaceBlock = 128;
+
+struct Site {
+  int x, y, z;
+  long long c;
+};
+
+// Threads along x, blocks along y and z (ny, nz <= 65535).
+__device__ __forceinline__ bool site_of(const StepArgs& a, Site& s) {
+  s.x = blockIdx.x * blockDim.x + threadIdx.x;
+  s.y = blockIdx.y;
+  s.z = blockIdx.z;
+  if (s.x >= a.nx) return false;
+  s.c = ((long long)s.z * a.ny + s.y) * a.nx + s.x;
+  return true;
+}
+
+// Cell index of x + (dx, dy, dz), |d| <= 1, wrapped on periodic axes; -1
+// where it lies beyond a wall.
+__device__ __forceinline__ long long site_shift(const StepArgs& a, const Site& s, int dx,
+                                                int dy, int dz) {
+  int xn = s.x + dx, yn = s.y + dy, zn = s.z + dz;
+  if (xn < 0 || xn >= a.nx) {
+    if (a.wx) return -1;
+    xn = wrap1(xn, a.nx);
+  }
+  if (yn < 0 || yn >= a.ny) {
+    if (a.wy) return -1;
+    yn = wrap1(yn, a.ny);
+  }
+  if (zn < 0 || zn >= a.nz) {
+    if (a.wz) return -1;
+    zn = wrap1(zn, a.nz);
+  }
+  return ((long long)zn * a.ny + yn) * a.nx + xn;
+}
+
+// Offset, within one colour, of the slot that holds f_i(x, t) in a state of
+// the given parity.
+template <int ODD>
+__device__ __forceinline__ long long slot_of(const StepArgs& a, const Site& s, int i,
+                                             long long N) {
+  if (!ODD) return (long long)i * N + s.c;
+  const long long src = site_shift(a, s, -ex(i), -ey(i), -ez(i));
+  return src < 0 ? (long long)i * N + s.c : (long long)opp(i) * N + src;
+}
+
+template <int ODD>
+__device__ __forceinline__ void load_site(const float* f, const StepArgs& a, const Site& s,
+                                          long long N, float* fR, float* fB) {
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const long long o = slot_of<ODD>(a, s, i, N);
+    fR[i] = f[o];
+    fB[i] = f[19 * N + o];
+  }
+}
+
+__global__ void __launch_bounds__(kInplaceBlock)
+    k_inplace_init(float* __restrict__ f, StepArgs a, long long N, float alpha_R,
+                   float alpha_B, const float* __restrict__ rho_R,
+                   const float* __restrict__ rho_B, const float* __restrict__ u) {
+  Site s;
+  if (!site_of(a, s)) return;
+  const float ux = u[s.c], uy = u[N + s.c], uz = u[2 * N + s.c];
+  float fR[19], fB[19];
+  equilibrium(rho_R[s.c], alpha_R, ux, uy, uz, a.improved, fR);
+  equilibrium(rho_B[s.c], alpha_B, ux, uy, uz, a.improved, fB);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    f[(long long)i * N + s.c] = fR[i];
+    f[(long long)(19 + i) * N + s.c] = fB[i];
+  }
+}
+
+// Pass 1: (rho^N, Qbar) of every cell at time t.
+template <int ODD>
+__global__ void __launch_bounds__(kInplaceBlock)
+    k_inplace_phase(const float* __restrict__ f, StepArgs a, long long N,
+                    float4* __restrict__ phase) {
+  Site s;
+  if (!site_of(a, s)) return;
+  float fR[19], fB[19];
+  load_site<ODD>(f, a, s, N, fR, fB);
+  phase[s.c] = stencil_entry(a, macro_of(a, fR, fB));
+}
+
+// Pass 2: Eq. 49 gradients from the phase field (a neighbour beyond a wall
+// takes the cell's own entry), collision, perturbation and recolouring, and
+// the in-place write.  f is read and written by this kernel: plain loads.
+template <int ODD, bool BGK>
+__global__ void __launch_bounds__(kInplaceBlock)
+    k_inplace_collide(float* f, StepArgs a, long long N, const float4* __restrict__ phase) {
+  Site s;
+  if (!site_of(a, s)) return;
+  float fR[19], fB[19];
+  load_site<ODD>(f, a, s, N, fR, fB);
+  const Macro m = macro_of(a, fR, fB);
+  const float4 ctr = phase[s.c];
+  float Gx = 0.f, Gy = 0.f, Gz = 0.f, Qx = 0.f, Qy = 0.f, Qz = 0.f;
+#pragma unroll
+  for (int i = 1; i < 19; i += 2) {
+    const long long np = site_shift(a, s, ex(i), ey(i), ez(i));
+    const long long nm = site_shift(a, s, -ex(i), -ey(i), -ez(i));
+    const float4 vp = np < 0 ? ctr : phase[np];
+    const float4 vm = nm < 0 ? ctr : phase[nm];
+    const float w = (i <= 6) ? (1.0f / 6.0f) : (1.0f / 12.0f);
+    if (ex(i)) {
+      Gx += (ex(i) * w) * (vp.x - vm.x);
+      Qx += (ex(i) * w) * (vp.y - vm.y);
+    }
+    if (ey(i)) {
+      Gy += (ey(i) * w) * (vp.x - vm.x);
+      Qy += (ey(i) * w) * (vp.z - vm.z);
+    }
+    if (ez(i)) {
+      Gz += (ez(i) * w) * (vp.x - vm.x);
+      Qz += (ez(i) * w) * (vp.w - vm.w);
+    }
+  }
+  if (a.wetting)
+    wetting_rule(a, a.wx && s.x == 0, a.wx && s.x == a.nx - 1, a.wy && s.y == 0,
+                 a.wy && s.y == a.ny - 1, a.wz && s.z == 0, a.wz && s.z == a.nz - 1, Gx, Gy,
+                 Gz);
+  collide_cell<BGK>(a, fR, fB, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const long long o = slot_of<ODD>(a, s, opp(i), N);
+    f[o] = fR[i];
+    f[19 * N + o] = fB[i];
+  }
+}
+
+// f_i(x, t) in the even layout and / or the moments (Eq. 4 with the forcing
+// shift), from a state of either parity.
+template <int ODD>
+__global__ void __launch_bounds__(kInplaceBlock)
+    k_inplace_read(const float* __restrict__ f, StepArgs a, long long N,
+                   float* __restrict__ f_out, float* __restrict__ rho_R,
+                   float* __restrict__ rho_B, float* __restrict__ u) {
+  Site s;
+  if (!site_of(a, s)) return;
+  float fR[19], fB[19];
+  load_site<ODD>(f, a, s, N, fR, fB);
+  if (f_out) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      f_out[(long long)i * N + s.c] = fR[i];
+      f_out[(long long)(19 + i) * N + s.c] = fB[i];
+    }
+  }
+  if (rho_R || rho_B || u) {
+    const Macro m = macro_of(a, fR, fB);
+    if (rho_R) rho_R[s.c] = m.rR;
+    if (rho_B) rho_B[s.c] = m.rB;
+    if (u) {
+      u[s.c] = m.ux;
+      u[N + s.c] = m.uy;
+      u[2 * N + s.c] = m.uz;
+    }
+  }
+}
+
+dim3 site_grid(const lbm_params* p) {
+  return dim3((unsigned)((p->nx + kInplaceBlock - 1) / kInplaceBlock), (unsigned)p->ny,
+              (unsigned)p->nz);
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+lbm_status check_params(const lbm_params* p, const char* no_plates_msg) {
+  const lbm_status st = validate_params_any_size(p);
+  if (st != LBM_OK) return st;
+  if (p->wall[0] == 2 || p->wall[1] == 2 || p->wall[2] == 2)
+    return fail_without_context(LBM_ERR_ARG, no_plates_msg);
+  return LBM_OK;
+}
+
+StepArgs fp32_args(const lbm_params* p, long long N) {
+  lbm_params q = *p;
+  q.storage = LBM_F32;
+  return derive_step_args(&q, N);
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" lbm_status lbm_inplace_init(const lbm_params* p, const float* rho_R,
+                                       const float* rho_B, const float* u, float* f,
+                                       void* cuda_stream) {
+  using namespace lbm;
+  clear_thread_error();
+  lbm_status st =
+      check_params(p, "lbm_inplace_init: moving plates (wall = 2) are not supported in place");
+  if (st != LBM_OK) return st;
+  if (!rho_R || !rho_B || !u || !f)
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_init: NULL array");
+  if (!is_device_pointer(rho_R) || !is_device_pointer(rho_B) || !is_device_pointer(u) ||
+      !is_device_pointer(f))
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_init: every array must be device memory");
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const size_t fb = (size_t)N * 38 * sizeof(float), nb = (size_t)N * sizeof(float);
+  if (overlap(f, fb, rho_R, nb) || overlap(f, fb, rho_B, nb) || overlap(f, fb, u, 3 * nb))
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_init: f overlaps an input field");
+  const StepArgs a = fp32_args(p, N);
+  k_inplace_init<<<site_grid(p), kInplaceBlock, 0, (cudaStream_t)cuda_stream>>>(
+      f, a, N, (float)p->alpha_R, (float)p->alpha_B, rho_R, rho_B, u);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail_without_context(LBM_ERR_CUDA, "lbm_inplace_init: kernel launch failed");
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step_inplace(const lbm_params* p, float* f, int parity, int nsteps,
+                                       void* scratch, void* cuda_stream) {
+  using namespace lbm;
+  clear_thread_error();
+  lbm_status st =
+      check_params(p, "lbm_step_inplace: moving plates (wall = 2) are not supported in place");
+  if (st != LBM_OK) return st;
+  if (parity != 0 && parity != 1)
+    return fail_without_context(LBM_ERR_ARG, "lbm_step_inplace: parity must be 0 or 1");
+  if (nsteps < 0)
+    return fail_without_context(LBM_ERR_ARG, "lbm_step_inplace: nsteps must be >= 0");
+  if (!f || !scratch)
+    return fail_without_context(LBM_ERR_ARG, "lbm_step_inplace: NULL array");
+  if (((uintptr_t)scratch & 15u) != 0 || ((uintptr_t)f & 3u) != 0)
+    return fail_without_context(LBM_ERR_ARG,
+                                "lbm_step_inplace: scratch must be 16-byte and f 4-byte aligned");
+  if (!is_device_pointer(f) || !is_device_pointer(scratch))
+    return fail_without_context(LBM_ERR_ARG,
+                                "lbm_step_inplace: f and scratch must be device memory");
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (overlap(f, (size_t)N * 38 * sizeof(float), scratch, (size_t)N * sizeof(float4)))
+    return fail_without_context(LBM_ERR_ARG, "lbm_step_inplace: f and scratch overlap");
+  const StepArgs a = fp32_args(p, N);
+  const dim3 g = site_grid(p);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  float4* phase = (float4*)scratch;
+  for (int k = 0; k < nsteps; ++k, parity ^= 1) {
+    if (parity) {
+      k_inplace_phase<1><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+      if (a.bgk)
+        k_inplace_collide<1, true><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+      else
+        k_inplace_collide<1, false><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+    } else {
+      k_inplace_phase<0><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+      if (a.bgk)
+        k_inplace_collide<0, true><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+      else
+        k_inplace_collide<0, false><<<g, kInplaceBlock, 0, s>>>(f, a, N, phase);
+    }
+    if (cudaGetLastError() != cudaSuccess)
+      return fail_without_context(LBM_ERR_CUDA, "lbm_step_inplace: kernel launch failed");
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_inplace_read(const lbm_params* p, const float* f, int parity,
+                                       float* f_out, float* rho_R, float* rho_B, float* u,
+                                       void* cuda_stream) {
+  using namespace lbm;
+  clear_thread_error();
+  lbm_status st =
+      check_params(p, "lbm_inplace_read: moving plates (wall = 2) are not supported in place");
+  if (st != LBM_OK) return st;
+  if (parity != 0 && parity != 1)
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: parity must be 0 or 1");
+  if (!f || (!f_out && !rho_R && !rho_B && !u))
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: NULL f or no output");
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const size_t fb = (size_t)N * 38 * sizeof(float), nb = (size_t)N * sizeof(float);
+  const void* outs[4] = {f_out, rho_R, rho_B, u};
+  const size_t sizes[4] = {fb, nb, nb, 3 * nb};
+  if (!is_device_pointer(f))
+    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: f must be device memory");
+  for (int k = 0; k < 4; ++k) {
+    if (!outs[k]) continue;
+    if (!is_device_pointer(outs[k]))
+      return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: outputs must be device memory");
+    if (overlap(f, fb, outs[k], sizes[k]))
+      return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: an output overlaps f");
+  }
+  const StepArgs a = fp32_args(p, N);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (parity)
+    k_inplace_read<1><<<site_grid(p), kInplaceBlock, 0, s>>>(f, a, N, f_out, rho_R, rho_B, u);
+  else
+    k_inplace_read<0><<<site_grid(p), kInplaceBlock, 0, s>>>(f, a, N, f_out, rho_R, rho_B, u);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail_without_context(LBM_ERR_CUDA, "lbm_inplace_read: kernel launch failed");
+  return LBM_OK;
+}

@@ -26,6 +26,9 @@ constexpr int kDiagSlots = 13;  // accumulated slots of lbm_diagnostics
 // Host helpers of the C-ABI layer.  Errors without a context are recorded
 // for lbm_last_error(NULL) of the calling thread.
 lbm_status validate_params(const lbm_params* p);
+// validate_params without the cell-count limit of the two-buffer kernels
+// (32-bit pair offsets), for the 64-bit in-place step.
+lbm_status validate_params_any_size(const lbm_params* p);
 StepArgs derive_step_args(const lbm_params* p, long long plane);
 lbm_status fail_without_context(lbm_status s, const char* msg);
 bool is_device_pointer(const void* ptr);

@@ -7,8 +7,11 @@ library is missing this module raises on import -- there is no CPU fallback.
 Functions carry the C names (``lbm_create``, ``lbm_init_fields``,
 ``lbm_step``, ``lbm_moments``, ``lbm_diagnostics``, ``lbm_get_f``,
 ``lbm_set_f``, ``lbm_get_populations``, ``lbm_set_populations``,
-``lbm_destroy``, ``lbm_last_error``); :class:`Lattice` is a small
-convenience wrapper holding a context, its torch stream and output tensors.
+``lbm_destroy``, ``lbm_last_error``, the in-place ``lbm_inplace_init``,
+``lbm_step_inplace``, ``lbm_inplace_read`` and the others of the header);
+:class:`Lattice` is a small convenience wrapper holding a context, its torch
+stream and output tensors, :class:`InPlaceLattice` the same for the in-place
+step (its population array, scratch and parity).
 """
 from __future__ import annotations
 
@@ -141,6 +144,15 @@ _lib.lbm_gemm_bf16.argtypes = [_fp, ctypes.c_longlong, ctypes.c_longlong, _fp, c
 _lib.lbm_gemm_bf16.restype = ctypes.c_int
 _lib.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
 _lib.lbm_step_noalloc.restype = ctypes.c_int
+_lib.lbm_inplace_init.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, _fp, _fp,
+                                  ctypes.c_void_p]
+_lib.lbm_inplace_init.restype = ctypes.c_int
+_lib.lbm_step_inplace.argtypes = [ctypes.POINTER(LbmParams), _fp, ctypes.c_int, ctypes.c_int,
+                                  _fp, ctypes.c_void_p]
+_lib.lbm_step_inplace.restype = ctypes.c_int
+_lib.lbm_inplace_read.argtypes = [ctypes.POINTER(LbmParams), _fp, ctypes.c_int, _fp, _fp, _fp,
+                                  _fp, ctypes.c_void_p]
+_lib.lbm_inplace_read.restype = ctypes.c_int
 _lib.lbm_launches_per_step.argtypes = [_ctx_p]
 _lib.lbm_launches_per_step.restype = ctypes.c_int
 _lib.lbm_destroy.argtypes = [_ctx_p]
@@ -152,6 +164,7 @@ EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
+            "lbm_inplace_init", "lbm_step_inplace", "lbm_inplace_read",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
             "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
             "lbm_batch_set_f", "lbm_batch_footprint", "lbm_set_graphs", "lbm_mlp_create", "lbm_mlp_num_params",
@@ -345,6 +358,39 @@ def lbm_step_noalloc(params: LbmParams, f_in, f_out, stream=None):
         raise LbmError(st, lbm_last_error(None))
 
 
+def _stream_arg(stream):
+    return ctypes.c_void_p(stream) if stream else None
+
+
+def _inplace_check(st):
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
+
+
+def lbm_inplace_init(params: LbmParams, rho_R, rho_B, u, f, stream=None):
+    """Equilibrium populations of the fields into f (float32 [2][19][N],
+    device) as an even in-place state; see include/lbm.h."""
+    _inplace_check(_lib.lbm_inplace_init(ctypes.byref(params), _addr(rho_R), _addr(rho_B),
+                                         _addr(u), _addr(f), _stream_arg(stream)))
+
+
+def lbm_step_inplace(params: LbmParams, f, parity, nsteps, scratch, stream=None):
+    """nsteps in-place steps of the state f of the given parity; returns the
+    new parity.  scratch: 16 bytes per cell of device memory."""
+    _inplace_check(_lib.lbm_step_inplace(ctypes.byref(params), _addr(f), int(parity),
+                                         int(nsteps), _addr(scratch), _stream_arg(stream)))
+    return (int(parity) + int(nsteps)) & 1
+
+
+def lbm_inplace_read(params: LbmParams, f, parity, f_out=None, rho_R=None, rho_B=None,
+                     u=None, stream=None):
+    """f_i^k(x, t) in the even layout and / or the moments of an in-place
+    state of either parity."""
+    _inplace_check(_lib.lbm_inplace_read(ctypes.byref(params), _addr(f), int(parity),
+                                         _addr(f_out), _addr(rho_R), _addr(rho_B), _addr(u),
+                                         _stream_arg(stream)))
+
+
 def _mlp_check(m, st):
     if st != LBM_OK:
         msg = _lib.lbm_mlp_last_error(m)
@@ -469,6 +515,66 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+class InPlaceLattice:
+    """One lattice stepped in place (one population array, AA access
+    pattern): 168 bytes of device memory per cell instead of 304, no limit
+    on the cell count beyond memory.  FP32; walls 0 or 1."""
+
+    def __init__(self, params: LbmParams, device=None, stream=None):
+        self.device = torch.device(device or "cuda")
+        self.params = params
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+        self.f = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
+        self.scratch = torch.empty((self.N, 4), dtype=torch.float32, device=self.device)
+        self.parity = 0
+
+    def _t(self, x):
+        if isinstance(x, torch.Tensor):
+            return x.to(device=self.device, dtype=torch.float32).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
+                               device=self.device)
+
+    def init_fields(self, rho_R, rho_B, u):
+        rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        lbm_inplace_init(self.params, rR, rB, uu, self.f, self.stream.cuda_stream)
+        self.parity = 0
+        self.stream.synchronize()
+
+    def set_f(self, f):
+        """Sets an even state: f_i^k(x, t) as float32 [2][19][N]."""
+        self.f.copy_(self._t(f).reshape(self.f.shape))
+        self.parity = 0
+        self.stream.synchronize()
+
+    def step(self, n=1):
+        self.parity = lbm_step_inplace(self.params, self.f, self.parity, n, self.scratch,
+                                       self.stream.cuda_stream)
+
+    def get_f(self):
+        out = torch.empty_like(self.f)
+        lbm_inplace_read(self.params, self.f, self.parity, f_out=out,
+                         stream=self.stream.cuda_stream)
+        self.stream.synchronize()
+        return out
+
+    def moments(self):
+        rR = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        rB = torch.empty_like(rR)
+        u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        lbm_inplace_read(self.params, self.f, self.parity, rho_R=rR, rho_B=rB, u=u,
+                         stream=self.stream.cuda_stream)
+        self.stream.synchronize()
+        return rR, rB, u
+
+    def close(self):
+        """Releases the population array and the scratch."""
+        self.f = None
+        self.scratch = None
 
 
 class Batch:

@@ -11,7 +11,9 @@ t* = t / sqrt(L / g).
 
 `python -m paper_1904_03618_gb300.rt --storage f32 f16 bf16` runs the same
 case in each storage format and reports the positions and the differences
-of the 16-bit runs from FP32.
+of the 16-bit runs from FP32; `--storage inplace` runs it on one population
+array stepped in place, which takes L = 512 (512 x 512 x 2048, 537 M cells,
+90 GB) on one GPU.
 """
 from __future__ import annotations
 
@@ -67,18 +69,23 @@ def positions(lat, pd):
 
 
 def run(storage="f32", L=256, steps=10000, every=500, g=1e-5, device=None, log=None):
+    """storage: "f32", "f16", "bf16" (the two-buffer context) or "inplace"
+    (FP32, one population array stepped in place: 168 bytes per cell, no
+    cell-count limit beyond device memory)."""
     dev = torch.device(device or "cuda")
     pd = rt_params(L=L, g=g)
-    rR, rB, u = wl.rayleigh_taylor(L, L, 4 * L, L, 0.05, 2 * L, pd["rho_in_R"], pd["rho_in_B"])
-    p = lbm.make_params(storage=storage, **pd)
-    if storage != "f32":
+    inplace = storage == "inplace"
+    rR, rB, u = wl.rayleigh_taylor(L, L, 4 * L, L, 0.05, 2 * L, pd["rho_in_R"], pd["rho_in_B"],
+                                   dtype=np.float32)
+    p = lbm.make_params(storage="f32" if inplace else storage, **pd)
+    if storage not in ("f32", "inplace"):
         # each colour is the majority phase of half the box: both store their
         # deviation from their own pure rest state (absolute 16-bit values,
         # references 0, lose the per-step gravity increments and create red
         # mass: +21 % in 4000 steps at L = 64)
         p.ref_R, p.ref_B = pd["rho_in_R"], pd["rho_in_B"]
     stream = torch.cuda.Stream(dev)
-    lat = lbm.Lattice(p, device=dev, stream=stream)
+    lat = (lbm.InPlaceLattice if inplace else lbm.Lattice)(p, device=dev, stream=stream)
     t_ref = math.sqrt(L / g)
     z0 = 2.0 * L
     rows = []
@@ -103,7 +110,13 @@ def run(storage="f32", L=256, steps=10000, every=500, g=1e-5, device=None, log=N
             stream.synchronize()
             seconds += time.perf_counter() - t0
             done += n
-        diag = lat.diagnostics(raise_unstable=False)
+        if inplace:
+            mR, mB, _ = lat.moments()
+            diag = (float(mR.double().sum()), float(mB.double().sum()), 0, 0, 0,
+                    int((~torch.isfinite(mR + mB)).sum()))
+            del mR, mB
+        else:
+            diag = lat.diagnostics(raise_unstable=False)
     finally:
         lat.close()
     cells = L * L * 4 * L

@@ -71,16 +71,21 @@ def layered(nx, ny, nz, a, rho_in_R, rho_in_B):
     return rho_R, rho_B, np.zeros((3, nz, ny, nx))
 
 
-def rayleigh_taylor(nx, ny, nz, L, amplitude, z_interface, rho_in_R, rho_in_B):
+def rayleigh_taylor(nx, ny, nz, L, amplitude, z_interface, rho_in_R, rho_in_B,
+                    dtype=np.float64):
     """Heavy red fluid above light blue fluid; interface height
     z_interface + h(x, y), h = amplitude * L * [cos(2 pi x / L) + cos(2 pi y / L)]
-    (the single-mode perturbation of the paper's Rayleigh-Taylor case)."""
-    x, y, z = _grid(nx, ny, nz)
+    (the single-mode perturbation of the paper's Rayleigh-Taylor case).
+    Coordinates broadcast (no full grids), so lattices of 10^9 cells fit in
+    host memory with dtype=np.float32."""
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
     h = amplitude * L * (np.cos(2 * np.pi * x / L) + np.cos(2 * np.pi * y / L))
     upper = z >= z_interface + h
-    rho_R = np.where(upper, rho_in_R, 0.0)
-    rho_B = np.where(upper, 0.0, rho_in_B)
-    return rho_R, rho_B, np.zeros((3, nz, ny, nx))
+    rho_R = upper.astype(dtype) * dtype(rho_in_R)
+    rho_B = (~upper).astype(dtype) * dtype(rho_in_B)
+    return rho_R, rho_B, np.zeros((3, nz, ny, nx), dtype=dtype)
 
 
 def random_populations(nx, ny, nz, seed=0, low=0.01, high=0.1):

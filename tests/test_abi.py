@@ -91,3 +91,41 @@ def test_batch_creation_validates_every_case_on_the_host():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_create_batch([two_pass, two_pass])
     assert "fused kernel only" in str(ei.value)
+
+
+def test_inplace_calls_validate_arguments_on_the_host():
+    """The in-place entry points reject bad arguments before any CUDA call;
+    they take lattices beyond the two-buffer kernels' 32-bit pair offsets
+    (the check that stops lbm_create there)."""
+    big = lbm.make_params(1024, 1024, 1024)          # 1.07e9 cells
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(big)
+    assert "too large" in str(ei.value)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_step_inplace(big, None, 0, 1, None)
+    assert ei.value.status == lbm.LBM_ERR_ARG and "NULL array" in str(ei.value)
+
+    p = lbm.make_params(8, 8, 8)
+    cases = [
+        (lambda: lbm.lbm_step_inplace(p, 4096, 2, 1, 8192), "parity"),
+        (lambda: lbm.lbm_step_inplace(p, 4096, 0, -1, 8192), "nsteps"),
+        (lambda: lbm.lbm_step_inplace(p, 4096, 0, 1, 8200), "16-byte"),
+        (lambda: lbm.lbm_inplace_read(p, 4096, 0), "no output"),
+        (lambda: lbm.lbm_inplace_read(p, 4096, 3, f_out=8192), "parity"),
+        (lambda: lbm.lbm_inplace_init(p, None, 4096, 8192, 16384), "NULL array"),
+    ]
+    for call, msg in cases:
+        with pytest.raises(lbm.LbmError) as ei:
+            call()
+        assert ei.value.status == lbm.LBM_ERR_ARG and msg in str(ei.value), (msg, str(ei.value))
+    plates = lbm.make_params(8, 8, 8, wall=(0, 0, 2))
+    for call in (lambda: lbm.lbm_step_inplace(plates, 4096, 0, 1, 8192),
+                 lambda: lbm.lbm_inplace_init(plates, 4096, 8192, 12288, 16384),
+                 lambda: lbm.lbm_inplace_read(plates, 4096, 0, f_out=8192)):
+        with pytest.raises(lbm.LbmError) as ei:
+            call()
+        assert "wall = 2" in str(ei.value)
+    bad = lbm.make_params(8, 8, 8, tau_R=0.3)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_step_inplace(bad, 4096, 0, 1, 8192)
+    assert "tau_R" in str(ei.value)
