@@ -474,19 +474,28 @@ class Lattice:
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
                                device=self.device)
 
+    def _after_caller(self):
+        """Orders this object's stream after the work queued so far on the
+        caller's current stream: tensors made there (or memory freed there)
+        are only touched by the library once that work is done."""
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
     def init_fields(self, rho_R, rho_B, u):
         rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        self._after_caller()
         lbm_init_fields(self.ctx, rR, rB, uu)
         self._keep = (rR, rB, uu)  # alive until the queued kernel has read them
         self.stream.synchronize()
 
     def set_f(self, f):
         ft = self._t(f)
+        self._after_caller()
         lbm_set_f(self.ctx, ft)
         self.stream.synchronize()
 
     def get_f(self):
         out = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
+        self._after_caller()
         lbm_get_f(self.ctx, out)
         self.stream.synchronize()
         return out
@@ -498,6 +507,7 @@ class Lattice:
         rR = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         rB = torch.empty_like(rR)
         u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        self._after_caller()
         lbm_moments(self.ctx, rR, rB, u)
         self.stream.synchronize()
         return rR, rB, u
@@ -532,6 +542,7 @@ class InPlaceLattice:
         self.f = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
         self.scratch = torch.empty((self.N, 4), dtype=torch.float32, device=self.device)
         self.parity = 0
+        self._after_caller()
 
     def _t(self, x):
         if isinstance(x, torch.Tensor):
@@ -539,15 +550,25 @@ class InPlaceLattice:
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
                                device=self.device)
 
+    def _after_caller(self):
+        """Orders this object's stream after the work queued so far on the
+        caller's current stream: tensors made there (or memory freed there)
+        are only touched by the library once that work is done."""
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
     def init_fields(self, rho_R, rho_B, u):
         rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        self._after_caller()
         lbm_inplace_init(self.params, rR, rB, uu, self.f, self.stream.cuda_stream)
         self.parity = 0
         self.stream.synchronize()
 
     def set_f(self, f):
         """Sets an even state: f_i^k(x, t) as float32 [2][19][N]."""
-        self.f.copy_(self._t(f).reshape(self.f.shape))
+        ft = self._t(f).reshape(self.f.shape)
+        self._after_caller()
+        with torch.cuda.stream(self.stream):
+            self.f.copy_(ft)
         self.parity = 0
         self.stream.synchronize()
 
@@ -557,6 +578,7 @@ class InPlaceLattice:
 
     def get_f(self):
         out = torch.empty_like(self.f)
+        self._after_caller()
         lbm_inplace_read(self.params, self.f, self.parity, f_out=out,
                          stream=self.stream.cuda_stream)
         self.stream.synchronize()
@@ -566,6 +588,7 @@ class InPlaceLattice:
         rR = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         rB = torch.empty_like(rR)
         u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        self._after_caller()
         lbm_inplace_read(self.params, self.f, self.parity, rho_R=rR, rho_B=rB, u=u,
                          stream=self.stream.cuda_stream)
         self.stream.synchronize()
@@ -595,19 +618,28 @@ class Batch:
         return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32,
                                device=self.device)
 
+    def _after_caller(self):
+        """Orders this object's stream after the work queued so far on the
+        caller's current stream: tensors made there (or memory freed there)
+        are only touched by the library once that work is done."""
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
     def init_fields(self, case, rho_R, rho_B, u):
         rR, rB, uu = self._t(rho_R), self._t(rho_B), self._t(u)
+        self._after_caller()
         lbm_batch_init_fields(self.ctx, case, rR, rB, uu)
         self.stream.synchronize()
 
     def set_f(self, case, f):
         ft = self._t(f)
+        self._after_caller()
         lbm_batch_set_f(self.ctx, case, ft)
         self.stream.synchronize()
 
     def get_f(self, case):
         out = torch.empty((2, 19) + self.shapes[case], dtype=torch.float32,
                           device=self.device)
+        self._after_caller()
         lbm_batch_get_f(self.ctx, case, out)
         self.stream.synchronize()
         return out
@@ -617,6 +649,7 @@ class Batch:
         rR = torch.empty(shape, dtype=torch.float32, device=self.device)
         rB = torch.empty_like(rR)
         u = torch.empty((3,) + shape, dtype=torch.float32, device=self.device)
+        self._after_caller()
         lbm_batch_moments(self.ctx, case, rR, rB, u)
         self.stream.synchronize()
         return rR, rB, u
