@@ -23,9 +23,12 @@
  *     detects which (CUDA unified addressing) and copies accordingly.
  *     Caller-owned memory is only read or written during the call's stream
  *     work and never retained.
- *   - All work is ordered on the stream given to lbm_create.  Calls that
- *     return data to a host pointer synchronise that stream before
- *     returning; others return as soon as the work is queued.
+ *   - All work is ordered on the stream given to lbm_create (or to the
+ *     stateless calls).  Calls that return data to a host pointer
+ *     synchronise that stream before returning; others return as soon as
+ *     the work is queued.  Nothing is ordered across streams: device memory
+ *     the caller wrote (or will reuse) on another stream must be ordered
+ *     against this one by the caller (an event and cudaStreamWaitEvent).
  *   - Every function returns an lbm_status; nothing aborts, traps or exits.
  *     On failure lbm_last_error() describes the cause.
  *   - Lattice units throughout: delta_x = delta_t = c = 1.
