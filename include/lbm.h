@@ -255,6 +255,18 @@ lbm_status lbm_set_fused_config(lbm_ctx *ctx, int tile_y, int zchunk, int hold);
 lbm_status lbm_get_fused_config(const lbm_ctx *ctx, int *tile_y, int *zchunk,
                                 int *hold);
 
+/* The fused configuration lbm_create picks for a single lattice with these
+   parameters on a GPU with `sms` streaming multiprocessors (0: 152, the
+   GB300), computed on the host without a GPU: the same rules, with every
+   tensor map taken as encodable (which holds on every lattice the TMA
+   eligibility rules admit).  For the 34 x 12 seam form the z chunk is the
+   one whose list schedule of CTAs over the SMs ends first: one CTA per SM,
+   handed out in launch order to the first SM that falls free, each costing
+   its planes + 3 plane-times.  Errors: LBM_ERR_ARG (invalid parameters,
+   NULL output, sms < 0), described by lbm_last_error(NULL). */
+lbm_status lbm_default_fused_config(const lbm_params *p, int sms, int *tile_y,
+                                    int *zchunk, int *hold);
+
 /* Number of kernel launches one lbm_step(ctx, 1) issues (1 for the fused
    kernel, 2 for the two-pass form). */
 int lbm_launches_per_step(const lbm_ctx *ctx);

@@ -984,6 +984,35 @@ extern "C" lbm_status lbm_get_fused_config(const lbm_ctx* c, int* tile_y,
   return LBM_OK;
 }
 
+extern "C" lbm_status lbm_default_fused_config(const lbm_params* p, int sms, int* tile_y,
+                                               int* zchunk, int* hold) {
+  g_create_err[0] = 0;
+  lbm_status st = validate(p);
+  if (st != LBM_OK) return st;
+  if (!tile_y || !zchunk || !hold)
+    return fail(nullptr, LBM_ERR_ARG, "lbm_default_fused_config: NULL output");
+  if (sms < 0) return fail(nullptr, LBM_ERR_ARG, "lbm_default_fused_config: sms must be >= 0");
+  // the choice lbm_create makes for a single lattice, with every tensor map
+  // encoded (they do on every lattice tma_eligible / seam_eligible admit)
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const StepArgs a = derive_args(p, (N + 63) / 64 * 64);
+  lbm::FusedConfig f = lbm::default_fused_config(a, p->storage);
+  if (p->kernel == LBM_KERNEL_FUSED && lbm::tma_eligible(a, p->storage)) {
+    const bool maps_ok[3] = {true, true, true};
+    lbm::FusedConfig t;
+    if (lbm::tma_default_config(a, p->storage, sms, maps_ok, &t)) f = t;
+    if (lbm::seam_eligible(a, p->storage)) {
+      f.tile_y = 12;
+      f.hold = 7;
+      f.zchunk = lbm::seam12_zchunk(a, sms);
+    }
+  }
+  *tile_y = f.tile_y;
+  *zchunk = f.zchunk;
+  *hold = f.hold;
+  return LBM_OK;
+}
+
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
   return ((c->ncases == 1 && c->kernel == LBM_KERNEL_TWO_PASS) ? 2 : 1) +

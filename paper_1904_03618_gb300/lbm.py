@@ -142,6 +142,11 @@ _lib.lbm_gemm_bf16.argtypes = [_fp, ctypes.c_longlong, ctypes.c_longlong, _fp, c
                                ctypes.c_longlong, _fp, ctypes.c_longlong, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, _fp, ctypes.c_void_p]
 _lib.lbm_gemm_bf16.restype = ctypes.c_int
+_lib.lbm_default_fused_config.argtypes = [ctypes.POINTER(LbmParams), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]
+_lib.lbm_default_fused_config.restype = ctypes.c_int
 _lib.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
 _lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_inplace_init.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, _fp, _fp,
@@ -163,7 +168,8 @@ _lib.lbm_last_error.restype = ctypes.c_char_p
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations",
-            "lbm_set_fused_config", "lbm_get_fused_config", "lbm_step_noalloc",
+            "lbm_set_fused_config", "lbm_get_fused_config", "lbm_default_fused_config",
+            "lbm_step_noalloc",
             "lbm_inplace_init", "lbm_step_inplace", "lbm_inplace_read",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
             "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
@@ -346,6 +352,17 @@ def lbm_set_fused_config(ctx, tile_y, zchunk, hold):
 def lbm_get_fused_config(ctx):
     v = [ctypes.c_int() for _ in range(3)]
     _check(ctx, _lib.lbm_get_fused_config(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def lbm_default_fused_config(params: LbmParams, sms=0):
+    """(tile_y, zchunk, hold) lbm_create would pick for this single lattice
+    on a GPU with `sms` SMs (0: 152); host only, no GPU needed."""
+    v = [ctypes.c_int() for _ in range(3)]
+    st = _lib.lbm_default_fused_config(ctypes.byref(params), int(sms),
+                                       *[ctypes.byref(x) for x in v])
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
     return tuple(x.value for x in v)
 
 

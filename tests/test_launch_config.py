@@ -1,0 +1,80 @@
+"""lbm_default_fused_config: the launch configuration lbm_create picks,
+computed on the host.
+
+Pinned to the configurations live contexts reported (lbm_get_fused_config)
+on a GB300 (152 SMs) for the same lattices; the seam form's z chunk is
+checked against a naive CTA-by-CTA simulation of the list schedule it
+models (one CTA per SM, CTAs handed out in launch order -- tile columns
+fastest, then z chunks -- to the SM that falls free first, each costing its
+planes + 3 plane-times), over many lattice shapes and SM counts."""
+import heapq
+
+import pytest
+
+from paper_1904_03618_gb300 import lbm
+
+
+def _droplet(n, **kw):
+    d = dict(nx=n, ny=n, nz=n, wall=(0, 0, 0), rho_in_R=10.0, rho_in_B=1.0,
+             alpha_R=0.97, alpha_B=0.7, A_R=0.01125, A_B=0.01125)
+    d.update(kw)
+    return d
+
+
+@pytest.mark.parametrize("kw,want", [
+    (_droplet(128), (12, 24, 7)),
+    (_droplet(160), (12, 30, 7)),
+    (_droplet(192), (12, 31, 7)),
+    (_droplet(256), (12, 32, 7)),
+    (_droplet(256, nz=1024, wall=(0, 0, 1)), (12, 32, 7)),   # Rayleigh-Taylor lattice
+    (_droplet(128, storage="f16"), (15, 12, 8)),
+    (_droplet(128, wall=(1, 1, 0)), (15, 12, 7)),
+])
+def test_matches_the_configurations_live_contexts_reported(kw, want):
+    d = dict(kw)
+    nx, ny, nz = d.pop("nx"), d.pop("ny"), d.pop("nz")
+    p = lbm.make_params(nx, ny, nz, **d)
+    assert lbm.lbm_default_fused_config(p, 152) == want
+    assert lbm.lbm_default_fused_config(p, 0) == want        # 0 means 152
+
+
+def _span(cols, nz, zc, sms, overhead=3.0):
+    heap = [0.0] * sms
+    for k in range((nz + zc - 1) // zc):
+        planes = min(zc, nz - k * zc)
+        for _ in range(cols):
+            t = heapq.heappop(heap)
+            heapq.heappush(heap, t + planes + overhead)
+    return max(heap)
+
+
+@pytest.mark.parametrize("nx,ny,nz,sms", [
+    (128, 128, 128, 152), (160, 160, 160, 152), (96, 64, 200, 152), (256, 40, 77, 152),
+    (64, 64, 64, 152), (128, 128, 128, 132), (34, 15, 9, 152), (192, 96, 300, 80),
+    (512, 512, 64, 152), (40, 30, 500, 16),
+])
+def test_seam_chunk_is_the_shortest_list_schedule(nx, ny, nz, sms):
+    p = lbm.make_params(nx, ny, nz)
+    tile_y, zchunk, hold = lbm.lbm_default_fused_config(p, sms)
+    assert (tile_y, hold) == (12, 7)
+    cols = ((nx + 31) // 32) * ((ny + 9) // 10)
+    spans = {zc: _span(cols, nz, zc, sms) for zc in range(6, 33)}
+    best = min(spans.values())
+    want = max(zc for zc, s in spans.items() if s <= best + 1e-9)   # ties: the longer chunk
+    assert zchunk == min(want, nz)
+
+
+def test_forms_outside_the_seam_rules():
+    # BGK and the two-pass kernel keep the shared-memory hold form
+    assert lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64, collision="bgk"))[::2] == (8, 2)
+    assert lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64, kernel="two_pass"))[::2] == (8, 2)
+    # too narrow for the 34-wide seam tile
+    assert lbm.lbm_default_fused_config(lbm.make_params(32, 64, 64))[0] != 12
+    # odd nx: the x seam is not a 16-byte TMA coordinate
+    assert lbm.lbm_default_fused_config(lbm.make_params(65, 64, 64))[::2] == (8, 2)
+    for n in (1, 3, 5):                                    # the chunk never exceeds nz
+        assert lbm.lbm_default_fused_config(lbm.make_params(64, 64, n))[1] <= n
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64), -1)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64, tau_R=0.2))
