@@ -78,3 +78,23 @@ def test_forms_outside_the_seam_rules():
         lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64), -1)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_default_fused_config(lbm.make_params(64, 64, 64, tau_R=0.2))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kw", [
+    _droplet(128), _droplet(160), _droplet(64, nz=200), _droplet(256, nz=1024, wall=(0, 0, 1)),
+    _droplet(128, storage="f16"), _droplet(128, storage="bf16"), _droplet(128, wall=(1, 1, 0)),
+    _droplet(96, wall=(1, 1, 1)), _droplet(64, collision="bgk"), _droplet(64, kernel="two_pass"),
+])
+def test_query_equals_the_live_context(kw):
+    torch = pytest.importorskip("torch")
+    d = dict(kw)
+    nx, ny, nz = d.pop("nx"), d.pop("ny"), d.pop("nz")
+    p = lbm.make_params(nx, ny, nz, **d)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lat = lbm.Lattice(p, device=torch.device("cuda:0"))
+    try:
+        live = lbm.lbm_get_fused_config(lat.ctx)
+    finally:
+        lat.close()
+    assert lbm.lbm_default_fused_config(p, sms) == live
