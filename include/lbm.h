@@ -378,7 +378,8 @@ lbm_status lbm_step_inplace(const lbm_params *p, float *f, int parity,
 /* Reads the state f of the given parity: f_out (may be NULL) receives
    f_i^k(x, t) in the even layout, rho_R, rho_B (N floats) and u (3N)
    (each may be NULL) the moments of lbm_moments (u with the half-force
-   shift of Eq. 4).  At least one output; none may overlap f. */
+   shift of Eq. 4).  At least one output; none may overlap f or another
+   output. */
 lbm_status lbm_inplace_read(const lbm_params *p, const float *f, int parity,
                             float *f_out, float *rho_R, float *rho_B,
                             float *u, void *cuda_stream);

@@ -335,6 +335,10 @@ extern "C" lbm_status lbm_inplace_read(const lbm_params* p, const float* f, int 
   const size_t fb = (size_t)N * 38 * sizeof(float), nb = (size_t)N * sizeof(float);
   const void* outs[4] = {f_out, rho_R, rho_B, u};
   const size_t sizes[4] = {fb, nb, nb, 3 * nb};
+  for (int k = 0; k < 4; ++k)
+    for (int l = k + 1; l < 4; ++l)
+      if (outs[k] && outs[l] && overlap(outs[k], sizes[k], outs[l], sizes[l]))
+        return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: two outputs overlap");
   if (!is_device_pointer(f))
     return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: f must be device memory");
   for (int k = 0; k < 4; ++k) {

@@ -113,6 +113,9 @@ def test_inplace_calls_validate_arguments_on_the_host():
         (lambda: lbm.lbm_inplace_read(p, 4096, 0), "no output"),
         (lambda: lbm.lbm_inplace_read(p, 4096, 3, f_out=8192), "parity"),
         (lambda: lbm.lbm_inplace_init(p, None, 4096, 8192, 16384), "NULL array"),
+        # rho_R (512 floats) at 1 << 20 overlaps u starting 1 KB later
+        (lambda: lbm.lbm_inplace_read(p, 4096, 0, rho_R=1 << 20, u=(1 << 20) + 1024),
+         "two outputs overlap"),
     ]
     for call, msg in cases:
         with pytest.raises(lbm.LbmError) as ei:
