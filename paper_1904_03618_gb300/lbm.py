@@ -558,6 +558,10 @@ class InPlaceLattice:
             self.stream = stream or torch.cuda.current_stream(self.device)
         self.f = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
         self.scratch = torch.empty((self.N, 4), dtype=torch.float32, device=self.device)
+        # used on self.stream: the allocator must not reuse the memory while
+        # work queued there may still touch it
+        self.f.record_stream(self.stream)
+        self.scratch.record_stream(self.stream)
         self.parity = 0
         self._after_caller()
 
@@ -612,7 +616,10 @@ class InPlaceLattice:
         return rR, rB, u
 
     def close(self):
-        """Releases the population array and the scratch."""
+        """Releases the population array and the scratch (after the work
+        queued on the lattice's stream)."""
+        if self.f is not None:
+            self.stream.synchronize()
         self.f = None
         self.scratch = None
 
