@@ -2,26 +2,35 @@
 
 One bench "step" is one lattice time step (all of: pull streaming, moments,
 gradients, collision, perturbation, recolouring, store) over the whole
-lattice.  Workload (default): moving droplet in uniform flow, 128^3 periodic,
-radius 20, background velocity (0.05, 0, 0), density ratio 10, viscosity
-ratio 1, sigma = 0.005, beta = 0.7, FP32 storage and arithmetic.
+lattice.  Headline workload (default): the three-dimensional Rayleigh-Taylor
+instability of Sec. IV.C on 256 x 256 x 1024 cells, periodic in x and y,
+halfway bounce-back walls in z, heavy red fluid (3) over light blue fluid (1)
+(Atwood number 0.5), gravity 1e-5, Re = 256, single-mode cosine interface of
+amplitude 0.05 L (Eq. 56), FP32 storage and arithmetic.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--storage f32|f16|bf16] [--kernel fused|two_pass] [--n 128]
+                  [--workload rt|droplet] [--storage f32|f16|bf16]
+                  [--kernel fused|two_pass] [--L 256] [--n 128] [--gemm]
 
 Prints one JSON line.  `value` is whole-job MLUPS with the populations
-resident in HBM (inputs of 637 MB, larger than the 129 MB L2, so no flush is
-needed between steps); `e2e` is the same metric through the C ABI with host
-buffers (initial fields uploaded from pinned host memory, every step's FP64
-diagnostics copied back into pinned host memory in stream order through
-lbm_step_diagnostics_async, final moments downloaded, all inside the timed
-region).  Multi-GPU runs are independent replicas (one lattice per rank):
-the step has no cross-lattice exchange.
+resident in HBM (20 GB of FP32 populations, far larger than the 129 MB L2,
+so no flush is needed between steps); `e2e` is the same metric through the
+C ABI with host buffers (initial fields uploaded from pinned host memory,
+every step's FP64 diagnostics copied back into pinned host memory in stream
+order through lbm_step_diagnostics_async, final moments downloaded, all
+inside the timed region; the field transfers are paid once per e2e run, so
+e2e grows with the number of steps).  Extra keys: `droplet_128` (the 128^3
+moving droplet in FP32, FP16, BF16 and the in-place step), `storage_variants`
+(the headline workload in FP16 and BF16), `batch` (512 independent droplet
+cases in one launch per step), `oracle_error` (FP32 / FP16 / BF16 runs
+against the FP64 oracle on the CPU-baseline sample).  Multi-GPU runs are
+independent replicas (one lattice per rank).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import shutil
 import statistics
@@ -36,9 +45,13 @@ sys.path.insert(0, ROOT)
 METRIC = ("MLUPS (two-fluid D3Q19) and % of HBM roofline; FP16-store vs FP32 "
           "at stated error")
 BYTES_PER_VALUE = {"f32": 4, "f16": 2, "bf16": 2}
+# algorithmic bytes of one cell update: 38 populations read + 38 written
+ALG_BYTES = {"f32": 304, "f16": 152, "bf16": 152}
 
 
-def workload(n):
+# ---------------------------------------------------------------------------
+# Workloads
+def droplet_params(n):
     """Moving droplet in uniform flow (density ratio 10, sigma = 0.005)."""
     return dict(nx=n, ny=n, nz=n, wall=(0, 0, 0), improved=True,
                 rho_in_R=10.0, rho_in_B=1.0, alpha_R=0.97, alpha_B=0.7,
@@ -47,19 +60,53 @@ def workload(n):
                 force=(0.0, 0.0, 0.0), gravity=(0.0, 0.0, 0.0))
 
 
-def storage_references(storage, rho_in_R, rho_in_B, rho_R, rho_B):
-    """Deviation references for FP16/BF16 storage: the colour with more mass
-    (the background phase) is stored as f - rho_in phi, the other as is, so
-    that the absent colour stays exactly zero."""
-    if storage == "f32":
-        return 0.0, 0.0
-    return (rho_in_R, 0.0) if rho_R.sum() >= rho_B.sum() else (0.0, rho_in_B)
-
-
-def workload_fields(n):
+def droplet_fields(n):
     from paper_1904_03618_gb300 import workloads
     return workloads.droplet(n, n, n, 20.0 * n / 128.0, 10.0, 1.0,
                              velocity=(0.05, 0.0, 0.0))
+
+
+def rt_params(L):
+    from paper_1904_03618_gb300 import rt
+    return rt.rt_params(L=L)
+
+
+def rt_fields(L, dtype=None):
+    import numpy as np
+
+    from paper_1904_03618_gb300 import workloads
+    return workloads.rayleigh_taylor(L, L, 4 * L, L, 0.05, 2 * L, 3.0, 1.0,
+                                     dtype=dtype or np.float64)
+
+
+def workload(kind, size):
+    """(lbm params dict, fields function of the size, description)."""
+    if kind == "rt":
+        pd = rt_params(size)
+        desc = ("Rayleigh-Taylor instability, %dx%dx%d D3Q19 two-fluid, periodic x/y, "
+                "bounce-back walls in z, density 3/1 (Atwood 0.5), gravity 1e-5, Re 256, "
+                "Eq. 56 single-mode perturbation amplitude 0.05 L, A_R = A_B = 1e-3, "
+                "beta 0.7" % (size, size, 4 * size))
+        return pd, rt_fields, desc
+    pd = droplet_params(size)
+    desc = ("moving droplet in uniform flow, %d^3 periodic D3Q19 two-fluid, R=%g, "
+            "u=(0.05,0,0), density ratio 10, viscosity ratio 1, sigma=0.005, beta=0.7"
+            % (size, 20.0 * size / 128.0))
+    return pd, droplet_fields, desc
+
+
+def storage_references(storage, pd, rho_R, rho_B, both=False):
+    """Deviation references for FP16/BF16 storage.  Droplets: the colour
+    with more mass (the background phase) is stored as f - rho_in phi, the
+    other as is, so that the absent colour stays exactly zero.  Rayleigh-
+    Taylor (`both`): each colour fills half the box, so both store their
+    deviation from their own pure rest state."""
+    if storage == "f32":
+        return 0.0, 0.0
+    if both:
+        return pd["rho_in_R"], pd["rho_in_B"]
+    return ((pd["rho_in_R"], 0.0) if rho_R.sum() >= rho_B.sum()
+            else (0.0, pd["rho_in_B"]))
 
 
 # ---------------------------------------------------------------------------
@@ -125,10 +172,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel, storage, n):
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("lbm_fused.cuh", "lbm_fused_tma.cuh", "lbm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(key, cells):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current source of the kernel (source hash recorded beside it)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "fused_step_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -137,63 +191,101 @@ def profiled_traffic(kernel, storage, n):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in ("lbm_fused.cuh", "lbm_fused_tma.cuh", "lbm_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
-    key = "%s_%s" % (kernel, storage)
-    if vals.get("source_sha256") != h.hexdigest()[:16] or key + "_bytes_per_cell" not in vals:
+    if vals.get("source_sha256") != kernel_source_hash() or key + "_bytes_per_cell" not in vals:
         return None
-    return float(vals[key + "_bytes_per_cell"]) * n ** 3
+    return float(vals[key + "_bytes_per_cell"]) * cells
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(n_sample, seconds):
+# CPU oracle legs (the only parts of the benchmark that run oracle/)
+def cpu_oracle_sample(args):
     """Time the FP64 oracle, as it stands, on the host cores on a bounded
-    sample of the workload (a smaller cube of the same case)."""
+    sample of the headline workload: the same case on a smaller lattice
+    (Rayleigh-Taylor L = args.cpu_L: L x L x 4L cells, same gravity and
+    Reynolds number), as many steps as fit in about args.cpu_seconds.
+    Returns the baseline record and the oracle's final state."""
     import oracle
-    from paper_1904_03618_gb300 import workloads
-    pd = workload(n_sample)
+    size = args.cpu_L if args.workload == "rt" else args.cpu_n
+    pd, fields, _ = workload(args.workload, size)
     p = oracle.params_from(pd)
-    rR, rB, u = workloads.droplet(n_sample, n_sample, n_sample, 20.0 * n_sample / 128.0,
-                                  10.0, 1.0, velocity=(0.05, 0.0, 0.0))
+    rR, rB, u = fields(size)
     f = oracle.init(p, rR, rB, u)
+    cells = pd["nx"] * pd["ny"] * pd["nz"]
     t0 = time.perf_counter()
-    f = oracle.step(p, f, 1)
-    one = time.perf_counter() - t0
-    steps = max(1, int(seconds / max(one, 1e-6)))
+    f = oracle.step(p, f, 2)
+    one = (time.perf_counter() - t0) / 2
+    steps = max(2, int(args.cpu_seconds / max(one, 1e-6)))
+    f0 = oracle.init(p, rR, rB, u)
     t0 = time.perf_counter()
-    f = oracle.step(p, f, steps)
+    f = oracle.step(p, f0, steps)
     dt = time.perf_counter() - t0
-    cells = n_sample ** 3 * steps
-    return {"value": cells / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "%d^3 lattice of the same case, %d steps, %.1f s" % (
-                n_sample, steps, dt)}, steps, dt
+    rec = {"value": cells * steps / dt / 1e6, "unit": "MLUPS",
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "%dx%dx%d lattice of the same case, %d steps, %.1f s" % (
+               pd["nx"], pd["ny"], pd["nz"], steps, dt)}
+    mR, mB, mu = oracle.moments(p, f)
+    return rec, (pd, size, steps, mR, mB, mu)
+
+
+def oracle_error(lbm, dev, sample, args):
+    """FP32 / FP16 / BF16 runs of the CPU-baseline sample on the GPU, from
+    the same initial fields and for the same number of steps as the oracle:
+    relative L2 of the total density and of the velocity against the FP64
+    oracle, and each colour's relative mass change."""
+    import numpy as np
+    import torch
+    pd, size, steps, mR, mB, mu = sample
+    _, fields, _ = workload(args.workload, size)
+    rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in fields(size))
+    rho_o = mR + mB
+    out = {"steps": steps, "lattice": [pd["nx"], pd["ny"], pd["nz"]]}
+    for storage in ("f32", "f16", "bf16"):
+        p = lbm.make_params(storage=storage, **pd)
+        p.ref_R, p.ref_B = storage_references(storage, pd, rR, rB,
+                                              both=args.workload == "rt")
+        s = torch.cuda.Stream(dev)
+        lat = lbm.Lattice(p, device=dev, stream=s)
+        lat.init_fields(rR, rB, u)
+        lat.step(steps)
+        gR, gB, gu = (t.double().cpu().numpy() for t in lat.moments())
+        lat.close()
+        rho = gR + gB
+        un = max(float(np.linalg.norm(mu)), 1e-3 * math.sqrt(mu.size))
+        out[storage] = {
+            "rho_rel_l2": float(np.linalg.norm(rho - rho_o) / np.linalg.norm(rho_o)),
+            "u_rel_l2": float(np.linalg.norm(gu - mu) / un),
+            "mass_R_rel_change": float(gR.sum() / rR.astype(np.float64).sum() - 1.0),
+            "mass_B_rel_change": float(gB.sum() / rB.astype(np.float64).sum() - 1.0),
+            "oracle_mass_R_rel_change": float(mR.sum() / rR.astype(np.float64).sum() - 1.0),
+        }
+    return out
 
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle, as it stands, on the host cores.  Each
-    bench step is one oracle time step on a cube of the same case whose size
-    is chosen so that warm-up plus timed steps take about two minutes."""
+    bench step is one oracle time step on a lattice of the same case whose
+    size is chosen so that warm-up plus timed steps take about two minutes."""
     if rank != 0:
         return
     import oracle
-    from paper_1904_03618_gb300 import workloads
-    probe = 24
-    pp = oracle.params_from(workload(probe))
-    fr, fb, fu = workloads.droplet(probe, probe, probe, 20.0 * probe / 128.0, 10.0, 1.0,
-                                   velocity=(0.05, 0.0, 0.0))
-    fp = oracle.init(pp, fr, fb, fu)
+    probe = 8 if args.workload == "rt" else 24
+    pd, fields, _ = workload(args.workload, probe)
+    pp = oracle.params_from(pd)
+    fp = oracle.init(pp, *fields(probe))
     t0 = time.perf_counter()
     oracle.step(pp, fp, 2)
-    rate = 2 * probe ** 3 / (time.perf_counter() - t0)
+    cells_probe = pd["nx"] * pd["ny"] * pd["nz"]
+    rate = 2 * cells_probe / (time.perf_counter() - t0)
     budget = 120.0 / (args.steps + args.warmup)
-    ns = int(max(8, min(args.n, (rate * budget) ** (1.0 / 3.0))))
-    pd = workload(ns)
+    full = args.L if args.workload == "rt" else args.n
+    shape_cells = 4.0 if args.workload == "rt" else 1.0  # cells = shape * size^3
+    size = int(max(8, min(full, (rate * budget / shape_cells) ** (1.0 / 3.0))))
+    if args.workload == "rt":
+        size -= size % 2
+    pd, fields, _ = workload(args.workload, size)
     p = oracle.params_from(pd)
-    rR, rB, u = workloads.droplet(ns, ns, ns, 20.0 * ns / 128.0, 10.0, 1.0,
-                                  velocity=(0.05, 0.0, 0.0))
-    f = oracle.init(p, rR, rB, u)
+    f = oracle.init(p, *fields(size))
+    cells = pd["nx"] * pd["ny"] * pd["nz"]
     for _ in range(args.warmup):
         f = oracle.step(p, f, 1)
     per_step = []
@@ -202,11 +294,11 @@ def run_reference(args, rank, world):
         f = oracle.step(p, f, 1)
         per_step.append(time.perf_counter() - t0)
     mean = statistics.mean(per_step)
-    mlups = ns ** 3 / mean / 1e6
+    mlups = cells / mean / 1e6
     cb = {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(),
           "kind": "oracle",
-          "sample": "each step: one FP64 oracle step on a %d^3 cube of the same case "
-                    "(%d steps timed)" % (ns, args.steps)}
+          "sample": "each step: one FP64 oracle step on a %dx%dx%d lattice of the same "
+                    "case (%d steps timed)" % (pd["nx"], pd["ny"], pd["nz"], args.steps)}
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * mean, "higher_is_better": True, "scaling": "weak",
@@ -218,15 +310,16 @@ def run_reference(args, rank, world):
 
 
 def config_block(args, world):
-    return {"workload": "moving droplet in uniform flow, %d^3 periodic D3Q19 two-fluid, "
-                        "R=%g, u=(0.05,0,0), density ratio 10, viscosity ratio 1, "
-                        "sigma=0.005, beta=0.7" % (args.n, 20.0 * args.n / 128.0),
-            "lattice": [args.n, args.n, args.n], "storage": args.storage,
+    size = args.L if args.workload == "rt" else args.n
+    pd, _, desc = workload(args.workload, size)
+    cells = pd["nx"] * pd["ny"] * pd["nz"]
+    return {"workload": desc,
+            "lattice": [pd["nx"], pd["ny"], pd["nz"]], "storage": args.storage,
             "kernel": args.kernel, "fused_config": args.fused_config or "library default",
             "model": "improved (Eq. 18 + Eq. 45 correction)",
             "parallelism": "replicas x%d" % world if world > 1 else "single GPU",
-            "l2_policy": "inputs larger than L2 (%.0f MB populations)" % (
-                args.n ** 3 * 38 * BYTES_PER_VALUE[args.storage] / 1e6)}
+            "l2_policy": "inputs larger than L2 (%.0f MB populations per buffer)" % (
+                cells * 38 * BYTES_PER_VALUE[args.storage] / 1e6)}
 
 
 # ---------------------------------------------------------------------------
@@ -248,6 +341,26 @@ def whole_job_mlups(world, cells_per_rank, seconds):
 
 
 # ---------------------------------------------------------------------------
+def time_steps(lbm, torch, ctx, stream, steps, warmup):
+    """(mean per-launch ms, total ms) of `steps` single-step calls on the
+    context's stream, CUDA events on that stream."""
+    for _ in range(warmup):
+        lbm.lbm_step(ctx, 1)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        lbm.lbm_step(ctx, 1)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    stream.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev), t0.elapsed_time(t1)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -265,13 +378,13 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    n = args.n
-    N = n ** 3
-    pd = workload(n)
-    rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in workload_fields(n))
+    size = args.L if args.workload == "rt" else args.n
+    pd, fields, _ = workload(args.workload, size)
+    N = pd["nx"] * pd["ny"] * pd["nz"]
+    rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in fields(size))
     params = lbm.make_params(storage=args.storage, kernel=args.kernel, **pd)
-    params.ref_R, params.ref_B = storage_references(args.storage, pd["rho_in_R"],
-                                                    pd["rho_in_B"], rR, rB)
+    params.ref_R, params.ref_B = storage_references(args.storage, pd, rR, rB,
+                                                    both=args.workload == "rt")
     stream = torch.cuda.Stream(dev)
     lat = lbm.Lattice(params, device=dev, stream=stream)
     if args.kernel == "fused" and args.fused_config:
@@ -279,6 +392,7 @@ def run_ours(args, rank, world, local_rank):
         lbm.lbm_set_fused_config(lat.ctx, ty, zc, hold)
     lat.init_fields(rR, rB, u)
     launches = lbm.lbm_launches_per_step(lat.ctx)
+    fused_cfg = lbm.lbm_get_fused_config(lat.ctx) if args.kernel == "fused" else None
 
     # --- device-resident throughput -------------------------------------
     for _ in range(args.warmup):
@@ -316,10 +430,11 @@ def run_ours(args, rank, world, local_rank):
     oR = torch.empty(rR.shape, dtype=torch.float32).pin_memory()
     oB = torch.empty(rB.shape, dtype=torch.float32).pin_memory()
     ou = torch.empty(u.shape, dtype=torch.float32).pin_memory()
-    e2e_steps = max(args.steps // 4, 10)
+    e2e_steps = max(args.steps, 20)
     monitor = torch.zeros((e2e_steps, 16), dtype=torch.float64).pin_memory()
     lbm.lbm_init_fields(lat.ctx, hR, hB, hu)  # warm the staging buffers
     lbm.lbm_moments(lat.ctx, oR, oB, ou)
+    lbm.lbm_sync(lat.ctx)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -340,30 +455,46 @@ def run_ours(args, rank, world, local_rank):
     e2e_check = {"steps_reported": int((mon[:, 12] > 0).sum()),
                  "nonfinite_cells_max": float(mon[:, 5].max()),
                  "error_words": int((mon[:, 14] != 0).sum())}
+    del hR, hB, hu, oR, oB, ou
 
     # --- roofline of the dominant kernel --------------------------------
     peak, peak_kind = measured_peaks()
-    alg_bytes = 2 * 38 * BYTES_PER_VALUE[args.storage] * N  # read + write per launch
+    alg_bytes = ALG_BYTES[args.storage] * N  # read + write per launch
     # launch_ms brackets one lbm_step call: the fused kernel's launch, or both
     # launches of the two-pass form (charged together to the step's bytes)
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.kernel, args.storage, n)
-
-    variants = None
-    if rank == 0 and world == 1 and args.storage == "f32" and not args.no_variants:
-        variants = storage_variants(lbm, dev, pd, rR, rB, u, n, args)
+    traffic = profiled_traffic("%s_%s_%s" % (args.workload, args.kernel, args.storage), N)
     lat.close()
-    batch = batch_measure(args, dev) if (rank == 0 and args.batch > 0) else None
+    del lat
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_variants:
+        if args.workload == "rt" and args.storage == "f32":
+            extras["storage_variants"] = storage_variants_rt(lbm, dev, pd, rR, rB, u, args)
+        del rR, rB, u
+        torch.cuda.empty_cache()
+        extras["droplet_128"] = droplet_variants(lbm, dev, args)
+        torch.cuda.empty_cache()
+    if rank == 0 and args.batch > 0:
+        extras["batch"] = batch_measure(args, dev)
+    if rank == 0 and args.gemm:
+        extras["gemm"] = gemm_measure(lbm, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu, _, _ = cpu_oracle_sample(args.cpu_n, args.cpu_seconds)
+        cpu, sample = cpu_oracle_sample(args)
+        extras["oracle_error"] = oracle_error(lbm, dev, sample, args)
 
     if rank == 0:
+        cfg = config_block(args, world)
+        if fused_cfg is not None:
+            cfg["fused_config_used"] = {"tile_y": fused_cfg[0], "zchunk": fused_cfg[1],
+                                        "hold": fused_cfg[2]}
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic", "config": config_block(args, world),
+                "dtype": args.storage, "data": "synthetic", "config": cfg,
                 "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                         "check": e2e_check},
@@ -373,78 +504,106 @@ def run_ours(args, rank, world, local_rank):
                              "traffic": traffic,
                              "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind
                              if peak_kind == "measured" else "fallback 6.8 TB/s",
-                             "algorithmic_bytes_per_cell": 2 * 38 * BYTES_PER_VALUE[args.storage],
+                             "algorithmic_bytes_per_cell": ALG_BYTES[args.storage],
                              "kernel_ms": launch_ms},
                 "clocks": clocks,
-                "storage_variants": variants,
-                "batch": batch,
                 "cpu_baseline": cpu,
                 "check": {"nonfinite_cells": diag[5], "negative_density_cells": diag[6],
                           "mass_R": diag[0], "mass_B": diag[1]}}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def storage_variants(lbm, dev, pd, rR, rB, u, n, args):
-    """FP16 / BF16 deviation storage and the FP32 in-place step (one
-    population array) on the same workload: device-resident MLUPS (same
-    timing as the FP32 line, fewer steps) and the error after
-    `variant_steps` steps against the FP32 two-buffer run from the same
-    initial state: relative L2 of the total density and of the velocity
-    (velocity normalised by its FP32 L2 norm)."""
-    import torch
-    out = {}
-    steps = args.variant_steps
-
-    def run(storage, nsteps, timed):
-        p = lbm.make_params(storage=storage, kernel=args.kernel, **pd)
-        p.ref_R, p.ref_B = storage_references(storage, pd["rho_in_R"], pd["rho_in_B"], rR, rB)
-        s = torch.cuda.Stream(dev)
-        lat = lbm.Lattice(p, device=dev, stream=s)
-        lat.init_fields(rR, rB, u)
-        ms = None
-        if timed:
-            for _ in range(args.warmup):
-                lbm.lbm_step(lat.ctx, 1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            for _ in range(timed):
-                lbm.lbm_step(lat.ctx, 1)
-            e1.record(s)
-            s.synchronize()
-            ms = e0.elapsed_time(e1) / timed
-            lat.init_fields(rR, rB, u)
-        lat.step(nsteps)
-        mom = lat.moments()
-        lat.close()
-        return ms, mom
-
-    _, ref = run("f32", steps, 0)
+def _drift(got, ref):
+    rho = (got[0] + got[1]).double()
     rho_ref = (ref[0] + ref[1]).double()
-    u_ref = ref[2].double()
+    uu, u_ref = got[2].double(), ref[2].double()
+    return {"rho_rel_l2": float((rho - rho_ref).norm() / rho_ref.norm()),
+            "u_rel_l2": float((uu - u_ref).norm() / u_ref.norm())}
+
+
+def _run_lattice(lbm, dev, p, fields, nsteps, timed, warmup):
+    """(mean ms per step over `timed` steps or None, moments after `nsteps`
+    steps from the initial fields)."""
+    import torch
+    s = torch.cuda.Stream(dev)
+    lat = lbm.Lattice(p, device=dev, stream=s)
+    lat.init_fields(*fields)
+    ms = None
+    if timed:
+        ms, _ = time_steps(lbm, torch, lat.ctx, s, timed, warmup)
+        lat.init_fields(*fields)
+    lat.step(nsteps)
+    mom = lat.moments()
+    lat.close()
+    return ms, mom
+
+
+def storage_variants_rt(lbm, dev, pd, rR, rB, u, args):
+    """The headline workload with FP16 / BF16 deviation storage: MLUPS
+    (CUDA events, per launch) and the drift of the density and velocity
+    against the FP32 run after `variant_steps` steps from the same state."""
     peak, _ = measured_peaks()
+    N = pd["nx"] * pd["ny"] * pd["nz"]
+    steps = args.variant_steps
+    p = lbm.make_params(storage="f32", kernel=args.kernel, **pd)
+    _, ref = _run_lattice(lbm, dev, p, (rR, rB, u), steps, 0, args.warmup)
+    out = {}
     for storage in ("f16", "bf16"):
-        ms, got = run(storage, steps, max(args.steps // 4, 50))
-        rho = (got[0] + got[1]).double()
-        uu = got[2].double()
-        mlups = n ** 3 / (ms * 1e-3) / 1e6
-        out[storage] = {
-            "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
-            "roofline_frac": mlups * 1e6 * 152 / (peak * 1e9),
-            "algorithmic_bytes_per_cell": 152,
-            "err_vs_f32_after_steps": steps,
-            "rho_rel_l2": float((rho - rho_ref).norm() / rho_ref.norm()),
-            "u_rel_l2": float((uu - u_ref).norm() / u_ref.norm()),
-        }
+        p = lbm.make_params(storage=storage, kernel=args.kernel, **pd)
+        p.ref_R, p.ref_B = storage_references(storage, pd, rR, rB, both=True)
+        ms, got = _run_lattice(lbm, dev, p, (rR, rB, u), steps, max(args.steps, 20),
+                               args.warmup)
+        mlups = N / (ms * 1e-3) / 1e6
+        out[storage] = {"value": mlups, "unit": "MLUPS", "kernel_ms": ms,
+                        "roofline_frac": mlups * 1e6 * ALG_BYTES[storage] / (peak * 1e9),
+                        "algorithmic_bytes_per_cell": ALG_BYTES[storage],
+                        "err_vs_f32_after_steps": steps, **_drift(got, ref)}
+        del got
+    return out
+
+
+def droplet_variants(lbm, dev, args):
+    """The 128^3 moving droplet (density ratio 10): FP32, FP16 and BF16
+    deviation storage and the FP32 in-place step (one population array),
+    device-resident MLUPS and the fraction of the HBM roofline at the
+    algorithmic 304 / 152 bytes per cell update; 16-bit and in-place drift
+    against the FP32 run after `variant_steps` steps."""
+    import numpy as np
+    import torch
+    n = args.n
+    pd = droplet_params(n)
+    rR, rB, u = (np.ascontiguousarray(a, dtype=np.float32) for a in droplet_fields(n))
+    peak, _ = measured_peaks()
+    N = n ** 3
+    steps = args.variant_steps
+    timed = max(args.steps * 5, 100)
+    out = {"workload": workload("droplet", n)[2]}
+    ref = None
+    for storage in ("f32", "f16", "bf16"):
+        p = lbm.make_params(storage=storage, kernel=args.kernel, **pd)
+        p.ref_R, p.ref_B = storage_references(storage, pd, rR, rB)
+        ms, got = _run_lattice(lbm, dev, p, (rR, rB, u), steps, timed, args.warmup)
+        mlups = N / (ms * 1e-3) / 1e6
+        rec = {"value": mlups, "unit": "MLUPS", "kernel_ms": ms,
+               "roofline_frac": mlups * 1e6 * ALG_BYTES[storage] / (peak * 1e9),
+               "algorithmic_bytes_per_cell": ALG_BYTES[storage]}
+        if storage == "f32":
+            ref = got
+            rec["traffic"] = profiled_traffic("droplet_fused_f32", N)
+        else:
+            rec.update(err_vs_f32_after_steps=steps, **_drift(got, ref))
+        out[storage] = rec
     # the in-place step: one FP32 population array (AA access pattern), a
-    # phase-field pass and the in-place collision per step
+    # phase-field pass and the in-place collision per step; its fraction is
+    # taken at the 304 B/cell of the method, not at the 488 B/cell the two
+    # passes move
     p = lbm.make_params(storage="f32", kernel=args.kernel, **pd)
     s = torch.cuda.Stream(dev)
     ip = lbm.InPlaceLattice(p, device=dev, stream=s)
     ip.init_fields(rR, rB, u)
-    timed = max(args.steps // 4, 50)
     ip.step(args.warmup)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -457,19 +616,14 @@ def storage_variants(lbm, dev, pd, rR, rB, u, n, args):
     ip.init_fields(rR, rB, u)
     ip.step(steps)
     got = ip.moments()
-    rho = (got[0] + got[1]).double()
-    uu = got[2].double()
-    mlups = n ** 3 / (ms * 1e-3) / 1e6
+    ip.close()
+    mlups = N / (ms * 1e-3) / 1e6
     out["inplace_f32"] = {
         "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
-        "roofline_frac": mlups * 1e6 * 488 / (peak * 1e9),
-        "algorithmic_bytes_per_cell": 488, "memory_bytes_per_cell": 168,
-        "gpu_launches_per_step": 2,
-        "err_vs_f32_after_steps": steps,
-        "rho_rel_l2": float((rho - rho_ref).norm() / rho_ref.norm()),
-        "u_rel_l2": float((uu - u_ref).norm() / u_ref.norm()),
-    }
-    del ip
+        "roofline_frac": mlups * 1e6 * 304 / (peak * 1e9),
+        "algorithmic_bytes_per_cell": 304, "moved_bytes_per_cell": 488,
+        "memory_bytes_per_cell": 168, "gpu_launches_per_step": 2,
+        "err_vs_f32_after_steps": steps, **_drift(got, ref)}
     return out
 
 
@@ -498,7 +652,7 @@ def batch_measure(args, dev):
             f = workloads.droplet(n, n, n, 0.25 * n, c["rho_in_R"], 1.0,
                                   velocity=(s["speed"], 0.0, 0.0))
             p = lbm.make_params(storage=storage, **c)
-            p.ref_R, p.ref_B = storage_references(storage, c["rho_in_R"], 1.0, f[0], f[1])
+            p.ref_R, p.ref_B = storage_references(storage, c, f[0], f[1])
             plist.append(p)
             fields.append(f)
         stream = torch.cuda.Stream(dev)
@@ -521,9 +675,8 @@ def batch_measure(args, dev):
         bad = sum(b.diagnostics(k, raise_unstable=False)[5] for k in range(0, len(cases), 64))
         b.close()
         mlups = cells / (ms * 1e-3) / 1e6
-        bpc = 304 if storage == "f32" else 152
         out[storage] = {"value": mlups, "unit": "MLUPS", "ms_per_step": ms,
-                        "roofline_frac": mlups * 1e6 * bpc / (peak * 1e9),
+                        "roofline_frac": mlups * 1e6 * ALG_BYTES[storage] / (peak * 1e9),
                         "steps": args.batch_steps, "gpu_launches_per_step": 1,
                         "autotuned_config": {"tile_y": tuned[0], "zchunk": tuned[1],
                                              "hold": tuned[2]},
@@ -532,25 +685,97 @@ def batch_measure(args, dev):
     return out
 
 
+def gemm_measure(lbm, dev):
+    """The surrogate network's tensor-core GEMM (lbm_gemm_bf16) on the
+    shapes of its training: forward H W (65,536 x 256 x 256), the input
+    layer (65,536 x 256 x 5) and the weight gradient H^T dZ (256 x 256 x
+    65,536); TFLOP/s by CUDA events over 20 launches, against cuBLAS on the
+    same BF16-rounded operands (torch.matmul) for context."""
+    import torch
+    torch.manual_seed(0)
+    peak = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        peak = float(json.load(open(path))["bf16_tflops"])
+    shapes = [("forward H W", 65536, 256, 256, False, False),
+              ("weight gradient H^T dZ", 256, 256, 65536, True, False),
+              ("backward dZ W^T", 65536, 256, 256, False, True)]
+    out = {"peak_tflops": peak}
+    err = torch.zeros(4, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    for name, M, N, K, trans_a, trans_b in shapes:
+        if trans_a:  # A stored K x M: A(m, k) = A[k * M + m]
+            A = torch.randn(K, M, device=dev)
+            sa_m, sa_k = 1, M
+        else:
+            A = torch.randn(M, K, device=dev)
+            sa_m, sa_k = K, 1
+        if trans_b:  # B stored N x K: B(k, n) = B[n * K + k]
+            B = torch.randn(N, K, device=dev)
+            sb_k, sb_n = 1, K
+        else:
+            B = torch.randn(K, N, device=dev)
+            sb_k, sb_n = N, 1
+        C = torch.empty(M, N, device=dev)
+        torch.cuda.synchronize(dev)
+
+        def gemm():
+            lbm.lbm_gemm_bf16(A, sa_m, sa_k, B, sb_k, sb_n, C, N, M, N, K, err,
+                              s.cuda_stream)
+        for _ in range(3):
+            gemm()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(20):
+            gemm()
+        e1.record(s)
+        s.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        Ab = (A.t() if trans_a else A).to(torch.bfloat16).contiguous()
+        Bb = (B.t() if trans_b else B).to(torch.bfloat16).contiguous()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                torch.matmul(Ab, Bb)
+            e0.record(s)
+            for _ in range(20):
+                torch.matmul(Ab, Bb)
+            e1.record(s)
+        s.synchronize()
+        ms_cublas = e0.elapsed_time(e1) / 20
+        flops = 2.0 * M * N * K
+        out[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
+                     "cublas_bf16_tflops": flops / ms_cublas / 1e9,
+                     "frac_of_peak": (flops / ms / 1e9 / peak) if peak else None}
+    out["error_word"] = int(err.max().item())
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rt", choices=["rt", "droplet"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "two_pass"])
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--L", type=int, default=256, help="Rayleigh-Taylor edge (L x L x 4L)")
+    ap.add_argument("--n", type=int, default=128, help="droplet cube edge")
     ap.add_argument("--fused-config", default="",
                     help="tile_y,zchunk,hold of the fused kernel (default: library choice)")
-    ap.add_argument("--cpu-n", type=int, default=48)
+    ap.add_argument("--cpu-L", type=int, default=32,
+                    help="Rayleigh-Taylor edge of the CPU-baseline sample")
+    ap.add_argument("--cpu-n", type=int, default=48, help="droplet edge of the CPU sample")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=200)
     ap.add_argument("--batch", type=int, default=512,
                     help="number of cases of the batched droplet sweep (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=30)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--gemm", action="store_true",
+                    help="also time the surrogate's tensor-core GEMM")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -21,6 +21,9 @@
  *     1 blue, i = 0..18 in the order of Eq. 5: 38*N values.
  *   - Pointers marked "host or device" may point to either; the library
  *     detects which (CUDA unified addressing) and copies accordingly.
+ *     Device memory must belong to the GPU the work runs on (the context's
+ *     GPU, or the current one for the calls without a context): a pointer
+ *     to another GPU's memory is refused with LBM_ERR_ARG before any launch.
  *     Caller-owned memory is only read or written during the call's stream
  *     work and never retained.
  *   - All work is ordered on the stream given to lbm_create (or to the
@@ -324,13 +327,18 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
    device array of 262,144 cells (4 MiB) inside the library, held by every
    GPU that loads the library until the process exits: lattices with
    nx*ny*nz > 262,144 are rejected with LBM_ERR_ARG.  The first call on each
-   device looks up that array's device address (once, with the device
-   current); make that first call before any stream capture.  All calls on
+   device looks up that array's device address (with the device current),
+   and a call looks it up again when the CUDA context current on the device
+   is not the one of the last lookup (after cudaDeviceReset, or when an
+   embedder makes a context of its own current, the library is loaded again
+   at another address); make the first call on a device, and the first
+   after such a change, before any stream capture.  All calls on
    a device share the array and it keeps the last call's contents (every
    entry a call reads is written by that call first), so calls that overlap
    on the GPU -- e.g. on two streams at once -- race.  Errors (LBM_ERR_ARG,
    LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the calling
-   thread. */
+   thread; f_in or f_out in host memory, or in device memory of a GPU other
+   than the current one, is LBM_ERR_ARG. */
 lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
                             float *f_out, void *cuda_stream);
 
@@ -355,8 +363,8 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
    into the scratch, then the in-place collision (488 bytes of memory
    traffic per cell, against 304 for lbm_step's fused kernel).
    Moving plates (wall = 2) are rejected with LBM_ERR_ARG.  p->storage and
-   p->kernel are ignored (FP32).  All arrays are device memory owned by the
-   caller; work is queued on cuda_stream (a cudaStream_t, NULL = legacy
+   p->kernel are ignored (FP32).  All arrays are device memory of the
+   current GPU owned by the caller; work is queued on cuda_stream (a cudaStream_t, NULL = legacy
    default stream) and the calls return without waiting.  Errors
    (LBM_ERR_ARG, LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the
    calling thread. */
@@ -431,6 +439,16 @@ lbm_status lbm_gemm_bf16(const float *A, long long sa_m, long long sa_k,
 
 /* Releases everything the context owns.  NULL is allowed. */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* Testing hook of the pointer checks, for machines with one GPU or none;
+   the paper has no counterpart.  enable = 1: until it is called again with
+   enable = 0, every pointer the library classifies is taken to be memory
+   of CUDA memory type `type` (a cudaMemoryType value: 1 host, 2 device, 3
+   managed) on GPU `device`, and `current_device` is taken to be the current
+   GPU, without asking the CUDA runtime.  Process-wide; not for use while
+   other threads call the library. */
+void lbm_test_fake_pointer_attributes(int enable, int type, int device,
+                                      int current_device);
 
 /* Text of the last error on ctx (never NULL; "" after success).  With
    ctx == NULL, the last error of a failed lbm_create in this thread. */

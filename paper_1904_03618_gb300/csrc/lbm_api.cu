@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "../../include/lbm.h"
@@ -89,14 +90,52 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
-static bool is_device_ptr(const void* ptr) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+// Where a caller's pointer lives, seen from the GPU the work runs on.
+// Device memory of another GPU is refused by every entry point that hands
+// caller pointers to a kernel: without peer access the kernel would fault.
+enum PtrWhere { kPtrHost = 0, kPtrHere = 1, kPtrOtherDevice = 2 };
+
+// Test hook (lbm_test_fake_pointer_attributes): a fixed answer in place of
+// cudaPointerGetAttributes and cudaGetDevice, so that the checks can be
+// exercised on machines with one GPU or none.
+static std::atomic<int> g_fake_on{0};
+static std::atomic<int> g_fake_type{0}, g_fake_device{0}, g_fake_current{0};
+
+// The device the context-free entry points run on (the current one).
+static int current_device() {
+  if (g_fake_on.load()) return g_fake_current.load();
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return d;
 }
+
+static PtrWhere pointer_where(const void* ptr, int run_device, int* owner) {
+  int type, device;
+  if (g_fake_on.load()) {
+    type = g_fake_type.load();
+    device = g_fake_device.load();
+  } else {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return kPtrHost;
+    }
+    type = at.type;
+    device = at.device;
+  }
+  *owner = device;
+  if (type == cudaMemoryTypeManaged) return kPtrHere;
+  if (type != cudaMemoryTypeDevice) return kPtrHost;
+  return device == run_device ? kPtrHere : kPtrOtherDevice;
+}
+
+// Context API: *device = the pointer may be read or written by the
+// context's kernels; host memory is staged; another GPU's memory fails.
+static lbm_status caller_memory(lbm_ctx* c, const void* ptr, const char* what,
+                                bool* device);
 
 // Every check but the 32-bit pair-offset limit of the two-buffer kernels.
 static lbm_status validate_any_size(const lbm_params* p) {
@@ -232,7 +271,21 @@ StepArgs derive_step_args(const lbm_params* p, long long plane) {
 lbm_status fail_without_context(lbm_status s, const char* msg) {
   return fail(nullptr, s, "%s", msg);
 }
-bool is_device_pointer(const void* ptr) { return is_device_ptr(ptr); }
+lbm_status require_current_device(const void* ptr, const char* what) {
+  const int cur = current_device();
+  int owner = -1;
+  switch (pointer_where(ptr, cur, &owner)) {
+    case kPtrHere:
+      return LBM_OK;
+    case kPtrOtherDevice:
+      return fail(nullptr, LBM_ERR_ARG,
+                  "%s is device memory of GPU %d, but GPU %d is current: make the GPU that "
+                  "owns the arrays current before the call",
+                  what, owner, cur);
+    default:
+      return fail(nullptr, LBM_ERR_ARG, "%s must be device memory", what);
+  }
+}
 void clear_thread_error() { g_create_err[0] = 0; }
 }  // namespace lbm
 
@@ -517,11 +570,31 @@ static lbm_status ensure_staging(lbm_ctx* c, size_t floats) {
   return LBM_OK;
 }
 
+static lbm_status caller_memory(lbm_ctx* c, const void* ptr, const char* what,
+                                bool* device) {
+  int owner = -1;
+  switch (pointer_where(ptr, c->device, &owner)) {
+    case kPtrHere:
+      *device = true;
+      return LBM_OK;
+    case kPtrOtherDevice:
+      return fail(c, LBM_ERR_ARG,
+                  "%s is device memory of GPU %d, but the context runs on GPU %d", what,
+                  owner, c->device);
+    default:
+      *device = false;
+      return LBM_OK;
+  }
+}
+
 // Makes `n` floats at `ptr` (host or device) readable by kernels: returns
 // ptr itself for device memory, else a staging copy at `slot` floats.
 static lbm_status device_input(lbm_ctx* c, const float* ptr, size_t n,
                                size_t slot, const float** out) {
-  if (is_device_ptr(ptr)) {
+  bool dev = false;
+  lbm_status st = caller_memory(c, ptr, "an input field", &dev);
+  if (st != LBM_OK) return st;
+  if (dev) {
     *out = ptr;
     return LBM_OK;
   }
@@ -563,7 +636,12 @@ extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_
   if ((st = settle_diag(c, -1)) != LBM_OK) return st;
   CaseRec& r = c->cases[k];
   const size_t N = (size_t)r.N;
-  const bool all_dev = is_device_ptr(rho_R) && is_device_ptr(rho_B) && is_device_ptr(u);
+  bool dR_dev = false, dB_dev = false, dU_dev = false;
+  if ((st = caller_memory(c, rho_R, "rho_R", &dR_dev)) != LBM_OK ||
+      (st = caller_memory(c, rho_B, "rho_B", &dB_dev)) != LBM_OK ||
+      (st = caller_memory(c, u, "u", &dU_dev)) != LBM_OK)
+    return st;
+  const bool all_dev = dR_dev && dB_dev && dU_dev;
   if (!all_dev && (st = ensure_staging(c, 5 * N)) != LBM_OK) return st;
   const float *dR, *dB, *dU;
   if ((st = device_input(c, rho_R, N, 0, &dR)) != LBM_OK) return st;
@@ -714,7 +792,10 @@ extern "C" lbm_status lbm_batch_moments(lbm_ctx* c, int k, float* rho_R,
   bool host[3];
   bool any_host = false;
   for (int q = 0; q < 3; ++q) {
-    host[q] = outs[q] && !is_device_ptr(outs[q]);
+    bool dev = false;
+    if (outs[q] && (st = caller_memory(c, outs[q], "a moments output", &dev)) != LBM_OK)
+      return st;
+    host[q] = outs[q] && !dev;
     any_host = any_host || host[q];
   }
   if (any_host && (st = ensure_staging(c, 5 * N)) != LBM_OK) return st;
@@ -846,7 +927,9 @@ extern "C" lbm_status lbm_batch_get_f(lbm_ctx* c, int k, float* f) {
   if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "get_f before init");
   const CaseRec& r = c->cases[k];
   const size_t n = 38 * (size_t)r.N;
-  if (is_device_ptr(f)) {
+  bool dev = false;
+  if ((st = caller_memory(c, f, "f", &dev)) != LBM_OK) return st;
+  if (dev) {
     LBM_CUDA(c, lbm::launch_get_f(c->storage, case_buffer(c, c->cur, k), r.args, f,
                                   c->stream),
              "get_f kernel");
@@ -874,7 +957,9 @@ extern "C" lbm_status lbm_batch_set_f(lbm_ctx* c, int k, const float* f) {
   CaseRec& r = c->cases[k];
   const size_t n = 38 * (size_t)r.N;
   const float* src = f;
-  if (!is_device_ptr(f)) {
+  bool dev = false;
+  if ((st = caller_memory(c, f, "f", &dev)) != LBM_OK) return st;
+  if (!dev) {
     if ((st = ensure_staging(c, n)) != LBM_OK) return st;
     LBM_CUDA(c, cudaMemcpyAsync(c->staging, f, n * sizeof(float),
                                 cudaMemcpyHostToDevice, c->stream),
@@ -1017,4 +1102,12 @@ extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
   return ((c->ncases == 1 && c->kernel == LBM_KERNEL_TWO_PASS) ? 2 : 1) +
          (c->plate_axis >= 0 ? 1 : 0);
+}
+
+extern "C" void lbm_test_fake_pointer_attributes(int enable, int type, int device,
+                                                 int current_device) {
+  g_fake_type.store(type);
+  g_fake_device.store(device);
+  g_fake_current.store(current_device);
+  g_fake_on.store(enable ? 1 : 0);
 }

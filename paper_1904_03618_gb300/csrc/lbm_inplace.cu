@@ -258,9 +258,11 @@ extern "C" lbm_status lbm_inplace_init(const lbm_params* p, const float* rho_R,
   if (st != LBM_OK) return st;
   if (!rho_R || !rho_B || !u || !f)
     return fail_without_context(LBM_ERR_ARG, "lbm_inplace_init: NULL array");
-  if (!is_device_pointer(rho_R) || !is_device_pointer(rho_B) || !is_device_pointer(u) ||
-      !is_device_pointer(f))
-    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_init: every array must be device memory");
+  if ((st = require_current_device(rho_R, "lbm_inplace_init: rho_R")) != LBM_OK ||
+      (st = require_current_device(rho_B, "lbm_inplace_init: rho_B")) != LBM_OK ||
+      (st = require_current_device(u, "lbm_inplace_init: u")) != LBM_OK ||
+      (st = require_current_device(f, "lbm_inplace_init: f")) != LBM_OK)
+    return st;
   const long long N = (long long)p->nx * p->ny * p->nz;
   const size_t fb = (size_t)N * 38 * sizeof(float), nb = (size_t)N * sizeof(float);
   if (overlap(f, fb, rho_R, nb) || overlap(f, fb, rho_B, nb) || overlap(f, fb, u, 3 * nb))
@@ -289,9 +291,9 @@ extern "C" lbm_status lbm_step_inplace(const lbm_params* p, float* f, int parity
   if (((uintptr_t)scratch & 15u) != 0 || ((uintptr_t)f & 3u) != 0)
     return fail_without_context(LBM_ERR_ARG,
                                 "lbm_step_inplace: scratch must be 16-byte and f 4-byte aligned");
-  if (!is_device_pointer(f) || !is_device_pointer(scratch))
-    return fail_without_context(LBM_ERR_ARG,
-                                "lbm_step_inplace: f and scratch must be device memory");
+  if ((st = require_current_device(f, "lbm_step_inplace: f")) != LBM_OK ||
+      (st = require_current_device(scratch, "lbm_step_inplace: scratch")) != LBM_OK)
+    return st;
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (overlap(f, (size_t)N * 38 * sizeof(float), scratch, (size_t)N * sizeof(float4)))
     return fail_without_context(LBM_ERR_ARG, "lbm_step_inplace: f and scratch overlap");
@@ -339,12 +341,11 @@ extern "C" lbm_status lbm_inplace_read(const lbm_params* p, const float* f, int 
     for (int l = k + 1; l < 4; ++l)
       if (outs[k] && outs[l] && overlap(outs[k], sizes[k], outs[l], sizes[l]))
         return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: two outputs overlap");
-  if (!is_device_pointer(f))
-    return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: f must be device memory");
+  if ((st = require_current_device(f, "lbm_inplace_read: f")) != LBM_OK) return st;
   for (int k = 0; k < 4; ++k) {
     if (!outs[k]) continue;
-    if (!is_device_pointer(outs[k]))
-      return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: outputs must be device memory");
+    if ((st = require_current_device(outs[k], "lbm_inplace_read: an output")) != LBM_OK)
+      return st;
     if (overlap(f, fb, outs[k], sizes[k]))
       return fail_without_context(LBM_ERR_ARG, "lbm_inplace_read: an output overlaps f");
   }

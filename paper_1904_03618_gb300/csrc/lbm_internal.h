@@ -31,7 +31,10 @@ lbm_status validate_params(const lbm_params* p);
 lbm_status validate_params_any_size(const lbm_params* p);
 StepArgs derive_step_args(const lbm_params* p, long long plane);
 lbm_status fail_without_context(lbm_status s, const char* msg);
-bool is_device_pointer(const void* ptr);
+// LBM_OK if ptr is device (or managed) memory usable on the current GPU;
+// else LBM_ERR_ARG with a message naming `what` (host memory, or device
+// memory of another GPU) for lbm_last_error(NULL).
+lbm_status require_current_device(const void* ptr, const char* what);
 void clear_thread_error();
 
 cudaError_t launch_init_eq(int storage, void* dst, const StepArgs& a,

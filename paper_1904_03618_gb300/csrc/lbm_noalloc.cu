@@ -13,8 +13,11 @@
 //
 // The host code never uses the array's name as a device address (on the
 // host it is only a stand-in symbol); the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on it.
+// cudaGetSymbolAddress, with the device current, on the first call made on
+// it, and again whenever the CUDA context current on that device differs
+// from the one the address was taken in (after cudaDeviceReset, or when an
+// embedder makes a context of its own current, the library's device image
+// is loaded again at another address).
 #include <mutex>
 
 #include "lbm_internal.h"
@@ -27,8 +30,31 @@ constexpr long long kNoAllocMaxCells = 1LL << 18;  // 262,144 cells, e.g. 64^3
 // Shared by every call on a device; holds the last call's phase field.
 static __device__ __align__(256) float4 g_noalloc_phase[kNoAllocMaxCells];
 
+// Per device: the context the address was looked up in, and the address.
+CUcontext g_phase_ctx[kMaxDevices];
 float4* g_phase_addr[kMaxDevices];
 std::mutex g_phase_mutex;
+
+// The driver context current on this thread (the runtime makes the
+// device's primary context current on its first call), through the
+// runtime's driver entry point; nullptr if it cannot be read.
+CUcontext current_context() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  static GetCurrentFn get_current = nullptr;
+  if (!get_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    get_current = (GetCurrentFn)fn;
+  }
+  CUcontext ctx = nullptr;
+  return get_current(&ctx) == CUDA_SUCCESS ? ctx : nullptr;
+}
 
 // Phase pass: (rho^N, Qbar) of every cell from f_i^k(x, t), read in place
 // (the input is the state after streaming, layout [k][i][cell]).
@@ -138,9 +164,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* f_in,
   const char* b0 = (const char*)f_out;
   if (a0 < b0 + bytes && b0 < a0 + bytes)
     return fail_without_context(LBM_ERR_ARG, "lbm_step_noalloc: f_in and f_out overlap");
-  if (!is_device_pointer(f_in) || !is_device_pointer(f_out))
-    return fail_without_context(LBM_ERR_ARG,
-                                "lbm_step_noalloc: f_in and f_out must be device memory");
+  if ((st = require_current_device(f_in, "lbm_step_noalloc: f_in")) != LBM_OK ||
+      (st = require_current_device(f_out, "lbm_step_noalloc: f_out")) != LBM_OK)
+    return st;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -148,16 +174,20 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, const float* f_in,
   float4* phase = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_phase_mutex);
-    if (!g_phase_addr[dev]) {
-      // once per device, with that device current
+    const CUcontext ctx = current_context();
+    if (!g_phase_addr[dev] || !ctx || ctx != g_phase_ctx[dev]) {
+      // with this device and this context current
       float4* ptr = nullptr;
       e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_phase);
       if (e != cudaSuccess || !ptr) {
         cudaGetLastError();
+        g_phase_addr[dev] = nullptr;
         return fail_without_context(LBM_ERR_CUDA,
                                     "lbm_step_noalloc: cudaGetSymbolAddress of the scratch failed");
       }
       g_phase_addr[dev] = ptr;
+      // the lookup has made the device's context current if none was
+      g_phase_ctx[dev] = current_context();
     }
     phase = g_phase_addr[dev];
   }

@@ -132,3 +132,40 @@ def test_inplace_calls_validate_arguments_on_the_host():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_step_inplace(bad, 4096, 0, 1, 8192)
     assert "tau_R" in str(ei.value)
+
+
+def test_pointers_of_another_gpu_are_refused_before_any_launch():
+    """The calls that hand caller pointers to kernels refuse device memory
+    of a GPU other than the one the work runs on (a kernel reading it
+    without peer access faults).  The attribute lookup is faked, so no
+    second GPU -- and no GPU at all -- is needed: every pointer is taken to
+    be device memory of GPU 1 while GPU 0 is current."""
+    fake = lbm._lib.lbm_test_fake_pointer_attributes
+    fake.argtypes = [ctypes.c_int] * 4
+    fake.restype = None
+    p = lbm.make_params(8, 8, 8)
+    n = 8 * 8 * 8
+    f_in, f_out = 1 << 24, (1 << 24) + 38 * 4 * n + 4096
+    fld = [(1 << 26) + k * 4 * 3 * n for k in range(4)]
+    calls = [
+        (lambda: lbm.lbm_step_noalloc(p, f_in, f_out), "lbm_step_noalloc: f_in"),
+        (lambda: lbm.lbm_inplace_init(p, fld[0], fld[1], fld[2], f_in),
+         "lbm_inplace_init: rho_R"),
+        (lambda: lbm.lbm_step_inplace(p, f_in, 0, 1, fld[3]), "lbm_step_inplace: f"),
+        (lambda: lbm.lbm_inplace_read(p, f_in, 0, rho_R=fld[0]), "lbm_inplace_read: f"),
+    ]
+    fake(1, 2, 1, 0)
+    try:
+        for call, what in calls:
+            with pytest.raises(lbm.LbmError) as ei:
+                call()
+            msg = str(ei.value)
+            assert ei.value.status == lbm.LBM_ERR_ARG, msg
+            assert what in msg and "device memory of GPU 1" in msg and "GPU 0 is current" in msg
+        # host memory is refused by the same calls with its own message
+        fake(1, 1, 0, 0)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_step_noalloc(p, f_in, f_out)
+        assert "f_in must be device memory" in str(ei.value)
+    finally:
+        fake(0, 0, 0, 0)
