@@ -356,6 +356,42 @@ struct StageReduce<T, TW, BY, 19> {
                                              float*, float2&) {}
 };
 
+// Thread -> cell of a TW x BY tile: the interior cells first, row by row
+// (one tile row per warp when TW - 2 = 32), then the ring (top row, bottom
+// row, left column, right column).  The collision runs only in interior
+// cells, so its warps have every lane busy, and the ring's moment-only work
+// fills warps of its own, which skip the collision.
+template <int TW, int BY>
+__device__ __forceinline__ void tile_cell(int L, int& tx, int& ty) {
+  constexpr int IW = TW - 2, IH = BY - 2;
+  if (L < IW * IH) {
+    tx = 1 + L % IW;
+    ty = 1 + L / IW;
+    return;
+  }
+  int r = L - IW * IH;
+  if (r < TW) {
+    tx = r;
+    ty = 0;
+    return;
+  }
+  r -= TW;
+  if (r < TW) {
+    tx = r;
+    ty = BY - 1;
+    return;
+  }
+  r -= TW;
+  tx = r < IH ? 0 : TW - 1;
+  ty = 1 + (r < IH ? r : r - IH);
+}
+// The thread that issues a plane's tensor copies: the first ring thread (a
+// ring warp has no collision to delay).
+template <int TW, int BY>
+__host__ __device__ constexpr int tma_issuer() {
+  return (TW - 2) * (BY - 2);
+}
+
 // One work item of the TMA-staged step: tile (bx, by) of the lattice `a`,
 // planes [zb, ze).  The CTA's stage mbarriers are initialised; G0 counts
 // the fills of the CTA's earlier items (their stage use), so that the
@@ -381,7 +417,9 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(
       smem + NS * SB + tma_win_bytes<TW, BY>() + tma_hold_bytes<TW, BY>(HV));
 
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TW + tx;
+  const int tid = threadIdx.y * TW + threadIdx.x;
+  int tx, ty;
+  tile_cell<TW, BY>(tid, tx, ty);
   const Geometry<WALLS, BY, TW> g(a, tx, ty, bx, by);
   const unsigned plane = (unsigned)a.plane;
   const Pair* srcp = reinterpret_cast<const Pair*>(src);
@@ -445,7 +483,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     }
   };
   auto issue = [&](int k) {
-    if (tid == 0) issue_one(k);
+    if (tid == tma_issuer<TW, BY>()) issue_one(k);
   };
   // Pulls plane zl: window slot and reduced state (f, rho_R, rho_B, u).
   auto fill = [&](int k, float* f, float* hu) {
@@ -482,7 +520,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   };
   // after a failed wait: the copies of fills k .. k + NS - 1 may be in flight
   auto drain = [&](int k) {
-    if (tid == 0) atomicExch(err, 1);
+    if (tid == tma_issuer<TW, BY>()) atomicExch(err, 1);
     for (int j = k; j < k + NS && j < K; ++j) tma_wait(mb(j), par(j));
   };
 
