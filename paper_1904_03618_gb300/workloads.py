@@ -71,6 +71,18 @@ def layered(nx, ny, nz, a, rho_in_R, rho_in_B):
     return rho_R, rho_B, np.zeros((3, nz, ny, nx))
 
 
+def layered_nodes(nx, ny, nz, a, rho_in_R, rho_in_B):
+    """Layered channel between no-slip plates lying on the first and last
+    node of y: node j sits at y_j = j - (ny - 1)/2 (the plates at +-(ny - 1)/2),
+    red where |y_j| <= a, blue elsewhere; at rest."""
+    _, y, _ = _grid(nx, ny, nz)
+    yc = y - (ny - 1) / 2.0
+    inside = np.abs(yc) <= a
+    rho_R = np.where(inside, rho_in_R, 0.0)
+    rho_B = np.where(inside, 0.0, rho_in_B)
+    return rho_R, rho_B, np.zeros((3, nz, ny, nx))
+
+
 def rayleigh_taylor(nx, ny, nz, L, amplitude, z_interface, rho_in_R, rho_in_B,
                     dtype=np.float64):
     """Heavy red fluid above light blue fluid; interface height
