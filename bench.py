@@ -24,7 +24,10 @@ moving droplet in FP32, FP16, BF16 and the in-place step), `storage_variants`
 (the headline workload in FP16 and BF16), `batch` (512 independent droplet
 cases in one launch per step), `oracle_error` (FP32 / FP16 / BF16 runs
 against the FP64 oracle on the CPU-baseline sample).  Multi-GPU runs are
-independent replicas (one lattice per rank).
+independent replicas (one lattice per rank, weak scaling); `--slabs` cuts
+one lattice into z-slabs over the ranks instead (NCCL halo exchange after
+every step, strong scaling), or with `--emulate-slabs S` into S slabs on
+one GPU.
 """
 from __future__ import annotations
 
@@ -751,6 +754,81 @@ def gemm_measure(lbm, dev):
     return out
 
 
+def run_slabs(args, rank, world, local_rank):
+    """One lattice cut into z-slabs, one per rank (NCCL halo exchange after
+    every step, paper_1904_03618_gb300/slabs.py), or --emulate-slabs S slabs
+    on one GPU in one process (device copies).  value = cells of the whole
+    lattice per second over the slowest rank (strong scaling)."""
+    import numpy as np
+    import torch
+
+    from paper_1904_03618_gb300 import lbm, slabs
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    size = args.L if args.workload == "rt" else args.n
+    pd, fields_fn, desc = workload(args.workload, size)
+    N = pd["nx"] * pd["ny"] * pd["nz"]
+    fields = tuple(np.ascontiguousarray(a, dtype=np.float32) for a in fields_fn(size))
+    refs = storage_references(args.storage, pd, fields[0], fields[1],
+                              both=args.workload == "rt")
+    if world > 1:
+        plan = slabs.SlabPlan(pd["nz"], world, rank, bool(pd["wall"][2]))
+        obj = slabs.SlabLattice(pd, plan, dist, dev, args.storage, refs)
+        obj.init_fields(fields)
+        nslabs = world
+        ctxs = [obj.lat.ctx]
+    else:
+        nslabs = max(1, args.emulate_slabs)
+        obj = slabs.SlabsOnOneDevice(pd, nslabs, device=dev, storage=args.storage, refs=refs)
+        obj.init_fields(fields)
+        ctxs = [lat.ctx for lat in obj.lats]
+    del fields
+    stream = torch.cuda.current_stream(dev)
+    obj.step(args.warmup)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    obj.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    # the step kernels alone (no exchange), for the roofline of this rank
+    k_ms, _ = time_steps(lbm, torch, ctxs[0], stream, args.steps, 1)
+    plan0 = obj.plan if world > 1 else obj.plans[0]
+    local_cells = pd["nx"] * pd["ny"] * plan0.nz_local
+    peak, peak_kind = measured_peaks()
+    achieved = ALG_BYTES[args.storage] * local_cells / (k_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": N / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                "config": dict(config_block(args, world),
+                               parallelism="z-slabs x%d (%s)" % (
+                                   nslabs, "NCCL point-to-point halo exchange" if world > 1
+                                   else "one device, device-copy halo exchange")),
+                "e2e": None,
+                "gpu_launches": args.steps * nslabs,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                             "peak_source": "%s hbm_gbs" % peak_kind,
+                             "algorithmic_bytes_per_cell": ALG_BYTES[args.storage],
+                             "kernel_ms": k_ms, "kernel": "step of slab 0 (own planes "
+                             "plus ghosts), exchange excluded"},
+                "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    obj.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -776,6 +854,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--gemm", action="store_true",
                     help="also time the surrogate's tensor-core GEMM")
+    ap.add_argument("--slabs", action="store_true",
+                    help="one lattice cut into z-slabs over the ranks (strong scaling)")
+    ap.add_argument("--emulate-slabs", type=int, default=1,
+                    help="with --slabs on one GPU: that many slabs in one process")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -783,6 +865,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.slabs:
+        run_slabs(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

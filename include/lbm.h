@@ -175,7 +175,9 @@ lbm_status lbm_moments(lbm_ctx *ctx, float *rho_R, float *rho_B, float *u);
    [13] count of cells with rho_R < 0 or rho_B < 0 (small negative colour
         densities in the minority phase are a normal effect of the
         recolouring, Eq. 10-11; informational)
-   [14] error word of the step kernels' bounded waits (0: none)
+   [14] error word of the step kernels' bounded waits (0: none); it stays
+        set until a single lattice's state is set anew (lbm_init_fields,
+        lbm_set_f, lbm_set_populations), for a batch until it is destroyed
    [15] 0 (reserved).
    The colour masses and the momentum are exact to about FP64 accuracy
    (compensated FP32 accumulators per direction and thread, FP64 across
@@ -224,6 +226,27 @@ size_t lbm_population_bytes(const lbm_ctx *ctx);
    Both synchronise the context stream. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src);
+
+/* Halo planes of a z-slab decomposition of one lattice over several
+   contexts (one per GPU or per slab); the paper has no counterpart.  A
+   slab's context covers its own planes plus two ghost planes on each side
+   that has a neighbour, with wall[2] = 1: a cell's update reads the stored
+   state within two planes, so after every step the two outermost planes
+   of each neighbour's own range, copied into the ghost planes, make the
+   slab's own planes evolve exactly as in the undivided lattice (the ghost
+   planes themselves are overwritten by the next copy).
+   lbm_get_planes copies the stored planes z0 .. z0 + n - 1 of the current
+   state into dst, lbm_set_planes copies src into them: raw storage format
+   (the buffer the next step pulls from; FP16 / BF16 as stored
+   deviations), layout [i][z][y][x][colour], n * lbm_plane_bytes() bytes.
+   Single-lattice contexts only; 0 <= z0, n >= 1, z0 + n <= nz.  dst / src
+   are host or device memory (device memory of the context's GPU); the copy
+   is queued on the context stream and the calls return without waiting
+   (pageable host memory makes the copy synchronous).
+   lbm_plane_bytes: bytes of one plane, 19 * nx * ny * 2 * element size. */
+size_t lbm_plane_bytes(const lbm_ctx *ctx);
+lbm_status lbm_get_planes(lbm_ctx *ctx, int z0, int n, void *dst);
+lbm_status lbm_set_planes(lbm_ctx *ctx, int z0, int n, const void *src);
 
 /* Launch configuration of the fused kernel (LBM_KERNEL_FUSED), the knob the
    autotuner turns; results are identical for every valid configuration.
@@ -413,9 +436,12 @@ typedef struct lbm_mlp lbm_mlp;
 lbm_status lbm_mlp_create(int n_in, int width, int depth, int n_out,
                           int max_batch, void *cuda_stream, lbm_mlp **out);
 size_t lbm_mlp_num_params(const lbm_mlp *m);
-/* Copies the parameters in and resets the Adam state and step count. */
+/* Copies the parameters in and resets the Adam state, the step count and
+   the record of a bounded wait that gave up. */
 lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *theta);
 lbm_status lbm_mlp_get_params(lbm_mlp *m, float *theta);
+/* y = network(x); synchronises the stream (LBM_ERR_TIMEOUT if a GEMM's
+   bounded wait gave up). */
 lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, int batch, float *y);
 /* Loss (host float, nullable) and gradient (num_params floats, nullable). */
 lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *x, const float *t,
@@ -449,6 +475,27 @@ void lbm_destroy(lbm_ctx *ctx);
    other threads call the library. */
 void lbm_test_fake_pointer_attributes(int enable, int type, int device,
                                       int current_device);
+
+/* Testing hook of the bounded device waits; the paper has no counterpart.
+   Sets, on the current GPU, how long the step kernels' waits for their
+   tensor copies (stage_ns, default 20 ms) and the surrogate GEMM's waits
+   for its tensor-core commits (mma_ns, default 200 ms) last before they
+   give up and report LBM_ERR_TIMEOUT (0 restores a default; a limit
+   below 1000 ns, shorter than a tick of the GPU's global timer, gives up
+   at the first poll that finds the copies or MMAs outstanding).  The wait
+   that follows a give-up, for the block's own copies or MMAs still in
+   flight, keeps its full limit.  Synchronises the device; call it while no
+   work of the library runs. */
+lbm_status lbm_test_set_wait_limits(unsigned long long stage_ns,
+                                    unsigned long long mma_ns);
+
+/* Testing hooks of the allocation paths; the paper has no counterpart.
+   lbm_test_fail_allocation(n), n > 0: the n-th device or pinned host
+   allocation the library makes from now on fails as cudaMalloc does when
+   memory runs out (n <= 0: none).  lbm_test_live_allocations: allocations
+   the library has made and not yet released. */
+void lbm_test_fail_allocation(int n);
+long long lbm_test_live_allocations(void);
 
 /* Text of the last error on ctx (never NULL; "" after success).  With
    ctx == NULL, the last error of a failed lbm_create in this thread. */

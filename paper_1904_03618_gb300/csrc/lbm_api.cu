@@ -90,6 +90,64 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
+// Allocation layer: every device and pinned-host allocation of the library
+// goes through these, so that the live count is known and a test can make
+// the n-th next allocation fail (as cudaMalloc does when memory runs out).
+static std::atomic<long long> g_live_allocs{0};
+static std::atomic<int> g_fail_countdown{0};
+
+static bool injected_failure() {
+  int n = g_fail_countdown.load();
+  while (n > 0) {
+    if (g_fail_countdown.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
+
+namespace lbm {
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  --g_live_allocs;
+}
+cudaError_t host_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocHost(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+void host_free(void* p) {
+  if (!p) return;
+  cudaFreeHost(p);
+  --g_live_allocs;
+}
+}  // namespace lbm
+
+extern "C" void lbm_test_fail_allocation(int n) { g_fail_countdown.store(n > 0 ? n : 0); }
+extern "C" long long lbm_test_live_allocations(void) { return g_live_allocs.load(); }
+
+extern "C" lbm_status lbm_test_set_wait_limits(unsigned long long stage_ns,
+                                               unsigned long long mma_ns) {
+  cudaError_t e = lbm::tma_set_wait_ns<float>(stage_ns);
+  if (e == cudaSuccess) e = lbm::tma_set_wait_ns<__half>(stage_ns);
+  if (e == cudaSuccess) e = lbm::tma_set_wait_ns<__nv_bfloat16>(stage_ns);
+  if (e == cudaSuccess) e = lbm::mlp_set_wait_ns(mma_ns);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+
 // Where a caller's pointer lives, seen from the GPU the work runs on.
 // Device memory of another GPU is refused by every entry point that hands
 // caller pointers to a kernel: without peer access the kernel would fault.
@@ -295,19 +353,19 @@ static void release(lbm_ctx* c) {
   cudaGetDevice(&prev);
   if (c->device >= 0) cudaSetDevice(c->device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  cudaFree(c->pop[0]);
-  cudaFree(c->pop[1]);
-  cudaFree(c->phase);
-  cudaFree(c->diag_part);
-  cudaFree(c->diag_out);
-  cudaFree(c->diag_done);
-  cudaFreeHost(c->diag_host);
-  cudaFree(c->staging);
-  cudaFree(c->d_cases);
-  cudaFree(c->foot);
-  cudaFree(c->d_flags);
+  lbm::dev_free(c->pop[0]);
+  lbm::dev_free(c->pop[1]);
+  lbm::dev_free(c->phase);
+  lbm::dev_free(c->diag_part);
+  lbm::dev_free(c->diag_out);
+  lbm::dev_free(c->diag_done);
+  lbm::host_free(c->diag_host);
+  lbm::dev_free(c->staging);
+  lbm::dev_free(c->d_cases);
+  lbm::dev_free(c->foot);
+  lbm::dev_free(c->d_flags);
   for (int b = 0; b < 2; ++b)
-    for (int w = 0; w < 3; ++w) cudaFree(c->d_bmaps[b][w]);
+    for (int w = 0; w < 3; ++w) lbm::dev_free(c->d_bmaps[b][w]);
   delete[] c->cases;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -425,22 +483,22 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
   const size_t bytes = (size_t)pairs * 2 * c->elem;
   lbm_status st = LBM_OK;
   for (int b = 0; b < 2 && st == LBM_OK; ++b)
-    if (cudaMalloc(&c->pop[b], bytes) != cudaSuccess)
+    if (lbm::dev_alloc((void**)&c->pop[b], bytes) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
   if (st == LBM_OK && c->kernel == LBM_KERNEL_TWO_PASS &&
-      cudaMalloc(&c->phase, sizeof(float4) * (size_t)c->max_cells) != cudaSuccess)
+      lbm::dev_alloc((void**)&c->phase, sizeof(float4) * (size_t)c->max_cells) != cudaSuccess)
     st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the phase field failed");
   if (st == LBM_OK) {
     c->diag_blocks = lbm::diag_capacity(c->storage, c->sms);
-    if (cudaMalloc(&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
-        cudaMalloc(&c->diag_out, sizeof(double) * 16) != cudaSuccess ||
-        cudaMalloc(&c->diag_done, sizeof(unsigned)) != cudaSuccess ||
-        cudaMallocHost(&c->diag_host, sizeof(double) * 16) != cudaSuccess ||
+    if (lbm::dev_alloc((void**)&c->diag_part, sizeof(double) * lbm::kDiagSlots * c->diag_blocks) != cudaSuccess ||
+        lbm::dev_alloc((void**)&c->diag_out, sizeof(double) * 16) != cudaSuccess ||
+        lbm::dev_alloc((void**)&c->diag_done, sizeof(unsigned)) != cudaSuccess ||
+        lbm::host_alloc((void**)&c->diag_host, sizeof(double) * 16) != cudaSuccess ||
         cudaMemset(c->diag_done, 0, sizeof(unsigned)) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of diagnostics scratch failed");
   }
   if (st == LBM_OK) {
-    if (cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
+    if (lbm::dev_alloc((void**)&c->d_flags, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the error word failed");
   }
@@ -484,7 +542,7 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
           ok = lbm::tma_build_maps(c->storage,
                                    (char*)c->pop[b] + (size_t)c->cases[k].pair_base * 2 * c->elem,
                                    c->cases[k].args, w, hm + 2 * k) == cudaSuccess;
-        ok = ok && cudaMalloc(&c->d_bmaps[b][w], sizeof(CUtensorMap) * 2 * ncases) == cudaSuccess &&
+        ok = ok && lbm::dev_alloc((void**)&c->d_bmaps[b][w], sizeof(CUtensorMap) * 2 * ncases) == cudaSuccess &&
              cudaMemcpy(c->d_bmaps[b][w], hm, sizeof(CUtensorMap) * 2 * ncases,
                         cudaMemcpyHostToDevice) == cudaSuccess;
       }
@@ -504,7 +562,7 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
     }
   }
   if (st == LBM_OK && ncases > 1 &&
-      cudaMalloc(&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
+      lbm::dev_alloc((void**)&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
     st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the case table failed");
   if (st == LBM_OK) {
     st = upload_case_table(c);
@@ -558,11 +616,11 @@ extern "C" int lbm_num_cases(const lbm_ctx* c) { return c ? c->ncases : 0; }
 
 static lbm_status ensure_staging(lbm_ctx* c, size_t floats) {
   if (c->staging_floats >= floats) return LBM_OK;
-  cudaFree(c->staging);
+  lbm::dev_free(c->staging);
   c->staging = nullptr;
   c->staging_floats = 0;
   drop_graph(c);
-  if (cudaMalloc(&c->staging, floats * sizeof(float)) != cudaSuccess) {
+  if (lbm::dev_alloc((void**)&c->staging, floats * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, LBM_ERR_OOM, "cudaMalloc of %zu staging floats failed", floats);
   }
@@ -602,6 +660,15 @@ static lbm_status device_input(lbm_ctx* c, const float* ptr, size_t n,
                               cudaMemcpyHostToDevice, c->stream),
            "cudaMemcpyAsync H2D");
   *out = c->staging + slot;
+  return LBM_OK;
+}
+
+// A single lattice whose state is set anew starts without the error word of
+// the bounded waits of earlier steps (a batch keeps it: its cases were
+// stepped together, and the word does not say which failed).
+static lbm_status fresh_state(lbm_ctx* c) {
+  if (c->ncases == 1)
+    LBM_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   return LBM_OK;
 }
 
@@ -651,6 +718,7 @@ extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_
                                   (float)r.p.alpha_R, (float)r.p.alpha_B, dR, dB, dU,
                                   c->stream),
            "init kernel");
+  if ((st = fresh_state(c)) != LBM_OK) return st;
   r.initialized = 1;
   c->steps = 0;
   c->err[0] = 0;
@@ -905,7 +973,7 @@ extern "C" lbm_status lbm_batch_footprint(lbm_ctx* c, int axis, int index,
     if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "footprint before init (case %d)", k);
   }
   if (!c->foot)
-    LBM_CUDA(c, cudaMalloc(&c->foot, sizeof(unsigned long long) * c->ncases), "cudaMalloc");
+    LBM_CUDA(c, lbm::dev_alloc((void**)&c->foot, sizeof(unsigned long long) * c->ncases), "cudaMalloc");
   LBM_CUDA(c, cudaMemsetAsync(c->foot, 0, sizeof(unsigned long long) * c->ncases, c->stream),
            "cudaMemsetAsync");
   for (int k = 0; k < c->ncases; ++k)
@@ -969,6 +1037,7 @@ extern "C" lbm_status lbm_batch_set_f(lbm_ctx* c, int k, const float* f) {
   LBM_CUDA(c, lbm::launch_set_f(c->storage, case_buffer(c, c->cur, k), r.args, src,
                                 c->stream),
            "set_f kernel");
+  if ((st = fresh_state(c)) != LBM_OK) return st;
   r.initialized = 1;
   c->steps = 0;
   c->err[0] = 0;
@@ -1002,10 +1071,61 @@ extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
   LBM_CUDA(c, cudaMemcpyAsync(c->pop[c->cur], src, lbm_population_bytes(c),
                               cudaMemcpyDefault, c->stream),
            "cudaMemcpyAsync");
+  {
+    lbm_status st = fresh_state(c);
+    if (st != LBM_OK) return st;
+  }
   LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
   for (int k = 0; k < c->ncases; ++k) c->cases[k].initialized = 1;
   c->err[0] = 0;
   return LBM_OK;
+}
+
+extern "C" size_t lbm_plane_bytes(const lbm_ctx* c) {
+  if (!c || c->ncases != 1) return 0;
+  const CaseRec& r = c->cases[0];
+  return (size_t)19 * r.p.nx * r.p.ny * 2 * c->elem;
+}
+
+// One strided copy: direction i's planes z0 .. z0 + n - 1 are contiguous in
+// the buffer (cell = (z ny + y) nx + x), direction planes r.args.plane pairs
+// apart; the caller's side holds the 19 runs back to back.
+static lbm_status plane_copy(lbm_ctx* c, int z0, int n, void* host_side, bool to_caller) {
+  if (!c) return LBM_ERR_ARG;
+  if (c->ncases != 1) return fail(c, LBM_ERR_ARG, "plane copies need a single-lattice context");
+  if (!host_side) return fail(c, LBM_ERR_ARG, "NULL plane buffer");
+  const CaseRec& r = c->cases[0];
+  if (z0 < 0 || n < 1 || z0 + n > r.p.nz)
+    return fail(c, LBM_ERR_ARG, "planes [%d, %d) outside [0, %d)", z0, z0 + n, r.p.nz);
+  if (!r.initialized) return fail(c, LBM_ERR_STATE, "plane copy before init");
+  bool dev = false;
+  lbm_status st = caller_memory(c, host_side, "the plane buffer", &dev);
+  if (st != LBM_OK) return st;
+  // writing the current buffer waits for diagnostics still reading it
+  if (!to_caller && (st = settle_diag(c, c->cur)) != LBM_OK) return st;
+  const size_t pair = 2 * c->elem;
+  const size_t cells = (size_t)r.p.nx * r.p.ny;
+  const size_t run = (size_t)n * cells * pair;
+  char* buf = (char*)c->pop[c->cur] + (size_t)z0 * cells * pair;
+  const size_t pitch = (size_t)r.args.plane * pair;
+  if (to_caller)
+    LBM_CUDA(c, cudaMemcpy2DAsync(host_side, run, buf, pitch, run, 19, cudaMemcpyDefault,
+                                  c->stream),
+             "cudaMemcpy2DAsync");
+  else
+    LBM_CUDA(c, cudaMemcpy2DAsync(buf, pitch, host_side, run, run, 19, cudaMemcpyDefault,
+                                  c->stream),
+             "cudaMemcpy2DAsync");
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_planes(lbm_ctx* c, int z0, int n, void* dst) {
+  return plane_copy(c, z0, n, dst, true);
+}
+
+extern "C" lbm_status lbm_set_planes(lbm_ctx* c, int z0, int n, const void* src) {
+  return plane_copy(c, z0, n, const_cast<void*>(src), false);
 }
 
 extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,

@@ -56,8 +56,20 @@
 
 namespace lbm {
 
-// A stage's copies land within microseconds; a wait gives up after this.
+// A stage's copies land within microseconds; a wait gives up after
+// g_tma_wait_ns, kTmaWaitNs unless a test has shortened it to exercise the
+// give-up path (tma_set_wait_ns).  The drain after a give-up always waits
+// up to kTmaWaitNs, so that no CTA leaves with its own copies in flight.
 constexpr unsigned long long kTmaWaitNs = 20ull * 1000 * 1000;
+static __device__ unsigned long long g_tma_wait_ns = kTmaWaitNs;
+
+// Sets g_tma_wait_ns of this translation unit on the current device (0:
+// the default); instantiated once per storage type's unit.
+template <typename T>
+cudaError_t tma_set_wait_ns(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : kTmaWaitNs;
+  return cudaMemcpyToSymbol(g_tma_wait_ns, &v, sizeof v);
+}
 
 template <typename T>
 __host__ __device__ constexpr int tma_pair_bytes() {
@@ -179,12 +191,33 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait for a phase of a stage mbarrier (kTmaWaitNs of wall time).
-__device__ __forceinline__ bool tma_wait(unsigned mbar, unsigned parity) {
+__device__ __forceinline__ bool mbar_test(unsigned mbar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// The give-up limit of this launch, read once per CTA (a volatile read:
+// only the host writes it, so its initial value is no constant).
+__device__ __forceinline__ unsigned long long tma_wait_limit() {
+  return *(const volatile unsigned long long*)&g_tma_wait_ns;
+}
+// Bounded wait for a phase of a stage mbarrier: `limit` ns of wall time on
+// the global timer.  A limit below 1000 ns (shorter than a tick of that
+// timer, and than the time a blocking try_wait may suspend the thread) is a
+// test of the give-up path: one non-blocking poll decides.
+__device__ __forceinline__ bool tma_wait(unsigned mbar, unsigned parity,
+                                         unsigned long long limit = kTmaWaitNs) {
+  if (limit < 1000) return mbar_test(mbar, parity);
   if (mbar_try(mbar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try(mbar, parity))
-    if (global_ns() - t0 > kTmaWaitNs) return false;
+    if (global_ns() - t0 > limit) return false;
   return true;
 }
 
@@ -403,7 +436,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
                                           const StepArgs& a, const CUtensorMap* map0,
                                           const CUtensorMap* map1, int bx, int by, int zb,
                                           int ze, unsigned char* smem, unsigned G0,
-                                          int* __restrict__ err,
+                                          int* __restrict__ err, unsigned long long wait_ns,
                                           const SeamStripMaps* strips = nullptr) {
   static_assert(!SEAM || tma_pair_bytes<T>() == 8,
                 "the SEAM form is FP32, periodic in x and y (walls in z allowed)");
@@ -521,7 +554,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   // after a failed wait: the copies of fills k .. k + NS - 1 may be in flight
   auto drain = [&](int k) {
     if (tid == tma_issuer<TW, BY>()) atomicExch(err, 1);
-    for (int j = k; j < k + NS && j < K; ++j) tma_wait(mb(j), par(j));
+    for (int j = k; j < k + NS && j < K; ++j) tma_wait(mb(j), par(j), kTmaWaitNs);
   };
 
   float cf[19], ch[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -529,9 +562,9 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     issue(0);
     issue(1);
     float tf[19], th[5];
-    bool ok = tma_wait(mb(0), par(0));
+    bool ok = tma_wait(mb(0), par(0), wait_ns);
     if (ok) fill(0, tf, th);
-    ok = ok && tma_wait(mb(1), par(1));
+    ok = ok && tma_wait(mb(1), par(1), wait_ns);
     if (ok) fill(1, cf, ch);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(0);
@@ -542,14 +575,14 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   } else {
     issue(0);
     float tf[19], th[5];
-    bool ok = tma_wait(mb(0), par(0));
+    bool ok = tma_wait(mb(0), par(0), wait_ns);
     if (ok) fill(0, tf, th);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(0);
       return false;
     }
     issue(1);
-    ok = tma_wait(mb(1), par(1));
+    ok = tma_wait(mb(1), par(1), wait_ns);
     if (ok) fill(1, cf, ch);
     if (!__syncthreads_and(ok ? 1 : 0)) {
       drain(1);
@@ -560,7 +593,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   for (int k = 2; k < K; ++k) {
     const int z = zb + k - 2;  // plane that collides; plane z + 1 is filled
     float nf[19], nh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    const bool got = tma_wait(mb(k), par(k));
+    const bool got = tma_wait(mb(k), par(k), wait_ns);
     if (got) {
       fill(k, nf, nh);
       if (g.interior) {  // private slot of this thread
@@ -629,7 +662,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
   tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS>(smem), NS);
   __syncthreads();
   tma_chunk<T, WALLS, TW, BY, NS>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y, zb, ze,
-                                  smem, 0u, err);
+                                  smem, 0u, err, tma_wait_limit());
 }
 
 // SEAM form (FP32, periodic in x and y, one stage): the source buffer's six
@@ -658,7 +691,7 @@ __global__ void __launch_bounds__(TW* BY, 1)
   __syncthreads();
   const SeamStripMaps strips = {&mxs, &mys0, &mys1, &mcs};
   tma_chunk<float, WALLS, TW, BY, NS, true>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y,
-                                            zb, ze, smem, 0u, err, &strips);
+                                            zb, ze, smem, 0u, err, tma_wait_limit(), &strips);
 }
 
 template <int TW, int BY, int NS, bool WALLS>
@@ -702,6 +735,7 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     return;
   }
   tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS>(smem), NS);
+  const unsigned long long wait_ns = tma_wait_limit();
   unsigned G0 = 0;
   for (int w = blockIdx.x; w < total_items; w += gridDim.x) {
     __syncthreads();  // the previous item is done with the shared state
@@ -730,7 +764,8 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
     const int ze = min(zb + zchunk, sa.nz);
     const size_t off = 2 * (size_t)bc.pair_base;
     if (!tma_chunk<T, WALLS, TW, BY, NS>(src_base + off, dst_base + off, sa, maps + 2 * s_case,
-                                         maps + 2 * s_case + 1, bx, by, zb, ze, smem, G0, err))
+                                         maps + 2 * s_case + 1, bx, by, zb, ze, smem, G0, err,
+                                         wait_ns))
       return;
     G0 += (unsigned)(ze - zb + 2);
   }

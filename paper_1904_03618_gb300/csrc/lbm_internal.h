@@ -120,6 +120,20 @@ bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind
                         FusedConfig* out);
 template <typename T>
 bool tma_config_fits_storage(int kind, int ns);
+// Give-up limit of the TMA stage waits (0: the default, 20 ms) on the
+// current device, per storage type's kernels; for tests of the give-up path.
+template <typename T>
+cudaError_t tma_set_wait_ns(unsigned long long ns);
+// The same for the tensor-core commit waits of the surrogate's GEMM
+// (default 200 ms).
+cudaError_t mlp_set_wait_ns(unsigned long long ns);
+
+// Device and pinned host allocations of the library, counted; a testing
+// hook (lbm_test_fail_allocation) makes the n-th next one fail.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t host_alloc(void** p, size_t bytes);
+void host_free(void* p);
 template <typename T>
 cudaError_t launch_fused_tma_storage(const void* src, void* dst, const StepArgs& a,
                                      const CUtensorMap* maps, int kind, int ns, int zchunk,

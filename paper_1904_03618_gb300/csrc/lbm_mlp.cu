@@ -34,7 +34,11 @@ constexpr int kM = 128;     // rows per CTA (UMMA M)
 constexpr int kKT = 64;     // K per shared-memory slice
 constexpr int kNMax = 256;  // UMMA N limit for M = 128
 constexpr int kThreads = 128;
-constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;  // bounded mbarrier wait
+// Bounded mbarrier wait: g_mma_wait_ns, kWaitNs unless a test has shortened
+// it to exercise the give-up path; the second chance before TMEM is released
+// always waits up to kWaitNs.
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;
+static __device__ unsigned long long g_mma_wait_ns = kWaitNs;
 
 struct GemmArgs {
   const float* A;
@@ -100,14 +104,35 @@ __device__ __forceinline__ bool mbar_poll(unsigned addr, unsigned phase) {
       : "memory");
   return done != 0;
 }
-// Bounded wait (kWaitNs of wall time on the global timer).
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned phase) {
+__device__ __forceinline__ bool mbar_test(unsigned addr, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// The give-up limit of this launch, read once per CTA (a volatile read:
+// only the host writes it, so its initial value is no constant).
+__device__ __forceinline__ unsigned long long mma_wait_limit() {
+  return *(const volatile unsigned long long*)&g_mma_wait_ns;
+}
+// Bounded wait: `limit` ns of wall time on the global timer.  A limit below
+// 1000 ns (shorter than a tick of that timer, and than the time a blocking
+// try_wait may suspend the thread) is a test of the give-up path: one
+// non-blocking poll decides.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned phase,
+                                          unsigned long long limit = kWaitNs) {
+  if (limit < 1000) return mbar_test(addr, phase);
   if (mbar_poll(addr, phase)) return true;
   unsigned long long t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   while (!mbar_poll(addr, phase)) {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > kWaitNs) return false;
+    if (t - t0 > limit) return false;
   }
   return true;
 }
@@ -228,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = sm.tmem_base;
+  const unsigned long long wait_ns = mma_wait_limit();
 
   const unsigned a_base = smem_u32(sm.a), b_base = smem_u32(sm.b);
   const unsigned idesc = instr_desc(n_mma);
@@ -274,13 +300,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
     }
     // wait for the MMAs of this slice before the slices are rewritten; the
     // verdict is made uniform over the CTA so every thread leaves together
-    ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    ok = __syncthreads_and(mbar_wait(mbar, phase, wait_ns) ? 1 : 0) != 0;
     phase ^= 1u;
   }
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
-    // give in-flight MMAs a second bounded chance before TMEM is released
-    mbar_wait(mbar, phase ^ 1u);
+    // give in-flight MMAs a second bounded chance (at the full limit)
+    // before TMEM is released
+    mbar_wait(mbar, phase ^ 1u, kWaitNs);
   } else if (kt0 < kt1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 = rows of the tile
@@ -427,6 +454,11 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g,
 }
 
 }  // namespace mlp
+
+cudaError_t mlp_set_wait_ns(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : mlp::kWaitNs;
+  return cudaMemcpyToSymbol(mlp::g_mma_wait_ns, &v, sizeof v);
+}
 }  // namespace lbm
 
 // ---------------------------------------------------------------------------
@@ -470,16 +502,16 @@ static lbm_status mlp_fail(lbm_mlp* m, lbm_status s, const char* fmt, ...) {
   } while (0)
 
 static void mlp_release(lbm_mlp* m) {
-  cudaFree(m->theta);
-  cudaFree(m->grad);
-  cudaFree(m->adam_m);
-  cudaFree(m->adam_v);
-  cudaFree(m->acts);
-  cudaFree(m->dz[0]);
-  cudaFree(m->dz[1]);
-  cudaFree(m->dy);
-  cudaFree(m->loss);
-  cudaFree(m->err);
+  lbm::dev_free(m->theta);
+  lbm::dev_free(m->grad);
+  lbm::dev_free(m->adam_m);
+  lbm::dev_free(m->adam_v);
+  lbm::dev_free(m->acts);
+  lbm::dev_free(m->dz[0]);
+  lbm::dev_free(m->dz[1]);
+  lbm::dev_free(m->dy);
+  lbm::dev_free(m->loss);
+  lbm::dev_free(m->err);
 }
 
 extern "C" lbm_status lbm_mlp_create(int n_in, int width, int depth, int n_out,
@@ -520,14 +552,17 @@ extern "C" lbm_status lbm_mlp_create(int n_in, int width, int depth, int n_out,
   const size_t pb = sizeof(float) * (size_t)o;
   const size_t wmax = (size_t)max_batch * (size_t)(width > n_out ? (width > n_in ? width : n_in)
                                                                   : (n_out > n_in ? n_out : n_in));
-  bool okay = cudaMalloc(&m->theta, pb) == cudaSuccess && cudaMalloc(&m->grad, pb) == cudaSuccess &&
-              cudaMalloc(&m->adam_m, pb) == cudaSuccess && cudaMalloc(&m->adam_v, pb) == cudaSuccess &&
-              cudaMalloc(&m->acts, sizeof(float) * (size_t)ao) == cudaSuccess &&
-              cudaMalloc(&m->dz[0], sizeof(float) * wmax) == cudaSuccess &&
-              cudaMalloc(&m->dz[1], sizeof(float) * wmax) == cudaSuccess &&
-              cudaMalloc(&m->dy, sizeof(float) * (size_t)max_batch * n_out) == cudaSuccess &&
-              cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&m->err, sizeof(int)) == cudaSuccess;
+  using lbm::dev_alloc;
+  bool okay = dev_alloc((void**)&m->theta, pb) == cudaSuccess &&
+              dev_alloc((void**)&m->grad, pb) == cudaSuccess &&
+              dev_alloc((void**)&m->adam_m, pb) == cudaSuccess &&
+              dev_alloc((void**)&m->adam_v, pb) == cudaSuccess &&
+              dev_alloc((void**)&m->acts, sizeof(float) * (size_t)ao) == cudaSuccess &&
+              dev_alloc((void**)&m->dz[0], sizeof(float) * wmax) == cudaSuccess &&
+              dev_alloc((void**)&m->dz[1], sizeof(float) * wmax) == cudaSuccess &&
+              dev_alloc((void**)&m->dy, sizeof(float) * (size_t)max_batch * n_out) == cudaSuccess &&
+              dev_alloc((void**)&m->loss, sizeof(float)) == cudaSuccess &&
+              dev_alloc((void**)&m->err, sizeof(int)) == cudaSuccess;
   if (!okay) {
     cudaGetLastError();
     mlp_release(m);
@@ -565,6 +600,8 @@ extern "C" lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* theta) {
            "cudaMemsetAsync");
   MLP_CUDA(m, cudaMemsetAsync(m->adam_v, 0, sizeof(float) * (size_t)m->nparams, m->stream),
            "cudaMemsetAsync");
+  // new parameters start a new history: a give-up reported before is cleared
+  MLP_CUDA(m, cudaMemsetAsync(m->err, 0, sizeof(int), m->stream), "cudaMemsetAsync");
   MLP_CUDA(m, cudaStreamSynchronize(m->stream), "stream sync");
   m->step = 0;
   return LBM_OK;
@@ -639,7 +676,7 @@ extern "C" lbm_status lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, flo
   MLP_CUDA(m, cudaMemcpyAsync(y, yd, sizeof(float) * (size_t)batch * m->n_out,
                               cudaMemcpyDefault, m->stream),
            "cudaMemcpyAsync");
-  return LBM_OK;
+  return check_err(m);  // synchronises: a GEMM wait that gave up is reported
 }
 
 // Loss and gradient into m->grad (device).

@@ -10,4 +10,5 @@ template cudaError_t launch_fused_tma_batch_storage<__nv_bfloat16>(
     const void*, void*, const BatchCase*, int, int, bool, const CUtensorMap*, int, int, int, int*,
     int, cudaStream_t);
 template bool tma_config_fits_storage<__nv_bfloat16>(int, int);
+template cudaError_t tma_set_wait_ns<__nv_bfloat16>(unsigned long long);
 }  // namespace lbm

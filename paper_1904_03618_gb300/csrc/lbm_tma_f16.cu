@@ -10,4 +10,5 @@ template cudaError_t launch_fused_tma_batch_storage<__half>(
     const void*, void*, const BatchCase*, int, int, bool, const CUtensorMap*, int, int, int, int*,
     int, cudaStream_t);
 template bool tma_config_fits_storage<__half>(int, int);
+template cudaError_t tma_set_wait_ns<__half>(unsigned long long);
 }  // namespace lbm

@@ -10,6 +10,7 @@ template cudaError_t launch_fused_tma_batch_storage<float>(
     const void*, void*, const BatchCase*, int, int, bool, const CUtensorMap*, int, int, int, int*,
     int, cudaStream_t);
 template bool tma_config_fits_storage<float>(int, int);
+template cudaError_t tma_set_wait_ns<float>(unsigned long long);
 
 // SEAM forms (FP32, periodic in x and y, walls in z allowed): 34 x 15 with
 // one stage, 34 x 12 with two.

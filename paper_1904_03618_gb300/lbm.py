@@ -96,6 +96,12 @@ _lib.lbm_get_populations.argtypes = [_ctx_p, _fp]
 _lib.lbm_get_populations.restype = ctypes.c_int
 _lib.lbm_set_populations.argtypes = [_ctx_p, _fp]
 _lib.lbm_set_populations.restype = ctypes.c_int
+_lib.lbm_plane_bytes.argtypes = [_ctx_p]
+_lib.lbm_plane_bytes.restype = ctypes.c_size_t
+_lib.lbm_get_planes.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, _fp]
+_lib.lbm_get_planes.restype = ctypes.c_int
+_lib.lbm_set_planes.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, _fp]
+_lib.lbm_set_planes.restype = ctypes.c_int
 _lib.lbm_set_fused_config.argtypes = [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.lbm_set_fused_config.restype = ctypes.c_int
 _lib.lbm_get_fused_config.argtypes = [_ctx_p] + [ctypes.POINTER(ctypes.c_int)] * 3
@@ -167,7 +173,8 @@ _lib.lbm_last_error.restype = ctypes.c_char_p
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
-            "lbm_get_populations", "lbm_set_populations",
+            "lbm_get_populations", "lbm_set_populations", "lbm_plane_bytes",
+            "lbm_get_planes", "lbm_set_planes",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_default_fused_config",
             "lbm_step_noalloc",
             "lbm_inplace_init", "lbm_step_inplace", "lbm_inplace_read",
@@ -343,6 +350,18 @@ def lbm_get_populations(ctx, dst):
 
 def lbm_set_populations(ctx, src):
     _check(ctx, _lib.lbm_set_populations(ctx, _addr(src)))
+
+
+def lbm_plane_bytes(ctx) -> int:
+    return int(_lib.lbm_plane_bytes(ctx))
+
+
+def lbm_get_planes(ctx, z0, n, dst):
+    _check(ctx, _lib.lbm_get_planes(ctx, int(z0), int(n), _addr(dst)))
+
+
+def lbm_set_planes(ctx, z0, n, src):
+    _check(ctx, _lib.lbm_set_planes(ctx, int(z0), int(n), _addr(src)))
 
 
 def lbm_set_fused_config(ctx, tile_y, zchunk, hold):

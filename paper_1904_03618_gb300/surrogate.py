@@ -68,14 +68,15 @@ def relaxation_times(s: dict, setup: ImpactSetup):
     return (P.tau_from_nu(nu_d, alpha_R), P.tau_from_nu(nu_g, ALPHA_B), alpha_R)
 
 
-def sample_impacts(n: int, setup: ImpactSetup, seed: int = 2024) -> list:
-    """n parameter sets drawn from RANGES, keeping those whose relaxation
-    times lie in [TAU_MIN, TAU_MAX] (the stable window of the solver)."""
+def sample_impacts(n: int, setup: ImpactSetup, seed: int = 2024, ranges: dict = None) -> list:
+    """n parameter sets drawn from `ranges` (default RANGES), keeping those
+    whose relaxation times lie in [TAU_MIN, TAU_MAX] (the stable window of
+    the solver)."""
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n:
         s = {}
-        for k, (lo, hi) in RANGES.items():
+        for k, (lo, hi) in (ranges or RANGES).items():
             if k == "theta_deg":
                 s[k] = float(rng.uniform(lo, hi))
             else:
@@ -304,11 +305,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=4000, help="training steps")
     ap.add_argument("--chunk", type=int, default=512)
     ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--series", type=int, default=16, help="sample times K per run")
+    ap.add_argument("--density-max", type=float, default=RANGES["density_ratio"][1])
+    ap.add_argument("--reynolds", type=float, nargs=2, default=list(RANGES["reynolds"]))
     ap.add_argument("--out", default=None, help="write the report (JSON) here")
     args = ap.parse_args(argv)
     setup = ImpactSetup(radius=args.radius, box=tuple(args.box), speed=args.speed,
-                        t_end=args.t_end)
-    samples = sample_impacts(args.samples, setup, seed=args.seed)
+                        t_end=args.t_end, samples=args.series)
+    ranges = dict(RANGES, density_ratio=(RANGES["density_ratio"][0], args.density_max),
+                  reynolds=tuple(args.reynolds))
+    samples = sample_impacts(args.samples, setup, seed=args.seed, ranges=ranges)
     runs = run_impacts(samples, setup, chunk=args.chunk,
                        log=lambda m: print(m, flush=True))
     rep = report(runs, train_steps=args.steps)
@@ -348,7 +354,9 @@ def report(runs: ImpactRuns, train_steps: int = 4000, width: int = 256, depth: i
     A = np.hstack([X[tr], np.ones((len(tr), 1))])
     coef, *_ = np.linalg.lstsq(A, Y[tr], rcond=None)
     lin_pred = np.hstack([X[te], np.ones((len(te), 1))]) @ coef
+    lo_hi = lambda k: [min(sm[k] for sm in runs.samples), max(sm[k] for sm in runs.samples)]  # noqa: E731
     return {
+        "sampled_ranges": {k: lo_hi(k) for k in RANGES},
         "setup": {"radius": runs.setup.radius, "box": list(runs.setup.box),
                   "speed": runs.setup.speed, "steps": runs.setup.steps,
                   "sample_steps": runs.setup.sample_steps, "storage": runs.setup.storage},

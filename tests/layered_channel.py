@@ -87,6 +87,26 @@ def oracle_e_u(name, improved, steps, eq18_coef=None, threads=1):
     return e_u(u[0, 0, :, 0], analytic_profile(muR, muB, printed_case(name)["M"]))
 
 
+def oracle_profile(name, improved, steps, gscale=1.0, threads=1):
+    """(u_x on the 101 nodes, E_u) of the FP64 oracle after `steps` steps
+    from the analytic profile, with the body force G * gscale."""
+    global G
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle
+    g0 = G
+    try:
+        G = g0 * gscale
+        d, muR, muB = case_params(name, improved)
+        ua = analytic_profile(muR, muB, printed_case(name)["M"])
+        fields = initial_fields(name, True)
+    finally:
+        G = g0
+    p = oracle.params_from(d)
+    f = oracle.step(p, oracle.init(p, *fields), steps)
+    _, _, u = oracle.moments(p, f)
+    return u[0, 0, :, 0].copy(), e_u(u[0, 0, :, 0], ua)
+
+
 def equal_viscosity_error(improved, steps, threads=1):
     """Max |u_x - u_x^a| / max u_x^a of the oracle for the channel with case
     A's densities (0.1 / 0.8, alpha_R 0.2, alpha_B 0.9: p_R = p_B = 0.04) and

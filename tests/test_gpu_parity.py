@@ -164,6 +164,39 @@ def test_thousand_steps_static_droplet():
     assert np.linalg.norm(gu - u) / scale <= 1e-4
 
 
+@pytest.mark.parametrize("wall,force,gravity", [
+    ((0, 0, 1), (2e-5, 0.0, 0.0), (0.0, 0.0, -1e-5)),
+    ((1, 1, 1), (0.0, 1e-5, 0.0), (0.0, 0.0, 0.0)),
+])
+def test_thousand_steps_ratio_10_drop_with_walls_and_forcing(wall, force, gravity):
+    """48 x 32 x 24, density ratio 10 (alpha 0.97 / 0.7), unequal relaxation
+    times (tau_R 0.8, tau_B 1.1), sigma = 0.005, a drop
+    of radius 7 moving at (0.02, 0.01, 0) next to the walls, forcing and
+    gravity: 1000 steps of the library's default launch configuration
+    against the oracle, density and velocity relative L2 <= 1e-4 (velocity
+    errors scaled by max(||u_oracle||, 1e-3 sqrt(3N)): with walls on every
+    axis the drop comes nearly to rest, and the near-static field takes the
+    static cases' scale)."""
+    pd = base(48, 32, 24, wall=wall, rho_in_R=10.0, rho_in_B=1.0, alpha_R=0.97,
+              alpha_B=0.7, tau_R=0.8, tau_B=1.1, A_R=0.01125, A_B=0.01125, force=force,
+              gravity=gravity)
+    f0 = droplet_state(pd, 7.0, velocity=(0.02, 0.01, 0.0), noise=1e-3, seed=5)
+    p = oracle.params_from(pd)
+    rR, rB, u = oracle.moments(p, oracle.step(p, f0, 1000))
+    lat = lbm.Lattice(lbm.make_params(**pd), device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    lat.step(1000)
+    gR, gB, gu = (t.double().cpu().numpy() for t in lat.moments())
+    d = lat.diagnostics(raise_unstable=False)
+    lat.close()
+    assert d[5] == 0 and d[6] == 0
+    rho, grho = rR + rB, gR + gB
+    assert np.linalg.norm(grho - rho) / np.linalg.norm(rho) <= 1e-4
+    assert np.linalg.norm(gR - rR) / np.linalg.norm(rR) <= 1e-4
+    scale = max(np.linalg.norm(u), 1e-3 * np.sqrt(u.size))
+    assert np.linalg.norm(gu - u) / scale <= 1e-4
+
+
 def test_full_size_moving_droplet_one_step():
     """128^3 periodic, R = 20, u = (0.05, 0, 0), density ratio 10, sigma =
     0.005: one fused step in the benchmark's launch configuration, compared
