@@ -25,7 +25,7 @@ from . import lbm
 
 # (tile_y, hold) shapes; z chunks are tried for each
 SINGLE_SHAPES = [(8, 2), (8, 7), (8, 8), (16, 8), (16, 7), (8, 3), (8, 0), (16, 1), (16, 4)]
-BATCH_SHAPES = [(8, 2), (15, 7), (15, 8), (8, 7), (8, 0), (16, 1)]
+BATCH_SHAPES = [(12, 7), (8, 2), (15, 7), (15, 8), (8, 7), (8, 0), (16, 1)]
 ZCHUNKS = [8, 12, 16, 24, 32]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1904_03618_gb300",

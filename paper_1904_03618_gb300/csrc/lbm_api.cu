@@ -60,6 +60,8 @@ struct lbm_ctx {
   bool seam_ok;                // smaps built (FP32, periodic in x and y)
   CUtensorMap* d_bmaps[2][3];  // batches: [buffer][tile kind] -> device table, 2 per case
   bool batch_tma_ok[3];        // batch tables built, per tile kind
+  CUtensorMap* d_seam_bmaps[2];  // batches: [buffer] -> six seam maps (tile_y 12) per case
+  bool batch_seam_ok;            // every case runs the batched SEAM form
   int total_items;
   int plate_axis;           // axis of the moving plates (wall = 2), or -1
   double plate_u[2][3];     // their velocities (low, high)
@@ -366,6 +368,7 @@ static void release(lbm_ctx* c) {
   lbm::dev_free(c->d_flags);
   for (int b = 0; b < 2; ++b)
     for (int w = 0; w < 3; ++w) lbm::dev_free(c->d_bmaps[b][w]);
+  for (int b = 0; b < 2; ++b) lbm::dev_free(c->d_seam_bmaps[b]);
   delete[] c->cases;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -560,6 +563,32 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
       c->fused.zchunk = 32;
       c->fused.hold = ns == 2 ? 7 : 8;
     }
+    // FP32 batches periodic in x and y: the SEAM form of the 34 x 12 tile
+    // with two stages, six maps per case and buffer
+    bool seam = true;
+    for (int k = 0; k < ncases && seam; ++k)
+      seam = lbm::batch_seam_eligible(c->cases[k].args, c->storage);
+    CUtensorMap* hs = seam ? new (std::nothrow) CUtensorMap[6 * (size_t)ncases] : nullptr;
+    seam = hs != nullptr;
+    for (int b = 0; b < 2 && seam; ++b) {
+      for (int k = 0; k < ncases && seam; ++k)
+        seam = lbm::tma_build_seam_maps(
+                   (char*)c->pop[b] + (size_t)c->cases[k].pair_base * 2 * c->elem,
+                   c->cases[k].args, 12, hs + 6 * k) == cudaSuccess;
+      seam = seam &&
+             lbm::dev_alloc((void**)&c->d_seam_bmaps[b], sizeof(CUtensorMap) * 6 * ncases) ==
+                 cudaSuccess &&
+             cudaMemcpy(c->d_seam_bmaps[b], hs, sizeof(CUtensorMap) * 6 * ncases,
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    delete[] hs;
+    cudaGetLastError();
+    // an option for the autotuner, not the default: on the 512-case droplet
+    // sweep (GB300) the 34 x 15 one-stage form above runs 11.5 ms per step
+    // against 13.5 ms for this one at its best chunk (48 planes): most of
+    // the sweep's cells are in 96^3 cases, whose 34 x 12 tiles are ragged
+    // in y and carry more ring per cell
+    c->batch_seam_ok = seam;
   }
   if (st == LBM_OK && ncases > 1 &&
       lbm::dev_alloc((void**)&c->d_cases, sizeof(lbm::BatchCase) * ncases) != cudaSuccess)
@@ -737,7 +766,13 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
   const void* src = c->pop[from];
   void* dst = c->pop[from ^ 1];
   cudaError_t e;
-  if (c->ncases > 1 && (c->fused.hold == 7 || c->fused.hold == 8)) {
+  if (c->ncases > 1 && c->fused.tile_y == 12 && c->fused.hold == 7) {
+    e = c->batch_seam_ok
+            ? lbm::launch_fused_tma_seam_batch(src, dst, c->d_cases, c->ncases, c->total_items,
+                                               c->any_walls, c->d_seam_bmaps[from],
+                                               c->fused.zchunk, c->d_flags, c->sms, c->stream)
+            : cudaErrorInvalidValue;
+  } else if (c->ncases > 1 && (c->fused.hold == 7 || c->fused.hold == 8)) {
     const int w = lbm::tma_kind(c->fused.tile_y);
     e = (w == 0 || w == 2) && c->batch_tma_ok[w]
             ? lbm::launch_fused_tma_batch(c->storage, src, dst, c->d_cases, c->ncases,
@@ -1150,7 +1185,19 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
            ? lbm::valid_batch_config(f) && ((hold != 7 && hold != 8) || batch_tma)
            : lbm::valid_fused_config(f, c->storage) && ((hold != 7 && hold != 8) || single_tma));
   if (tile_y == 12) {  // the two-stage SEAM form only
-    if (!(c->ncases == 1 && c->seam_ok && hold == 7 && zchunk >= 0))
+    if (c->ncases > 1) {
+      if (!(c->batch_seam_ok && hold == 7 && zchunk >= 0))
+        return fail(c, LBM_ERR_ARG,
+                    "tile_y 12 is the batched seam form (hold 7) of FP32 batches whose cases "
+                    "are periodic in x and y (MRT, nx a multiple of 2)");
+      c->fused = f;
+      drop_graph(c);
+      lbm_status st = upload_case_table(c);
+      if (st != LBM_OK) return st;
+      c->err[0] = 0;
+      return LBM_OK;
+    }
+    if (!(c->seam_ok && hold == 7 && zchunk >= 0))
       return fail(c, LBM_ERR_ARG,
                   "tile_y 12 is the two-stage seam form (hold 7) of single periodic FP32 "
                   "lattices with nx a multiple of 2, nx >= 34 and ny >= 15");

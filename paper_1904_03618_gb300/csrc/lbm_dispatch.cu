@@ -232,7 +232,10 @@ bool seam_eligible(const StepArgs& a, int storage) {
 
 cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
                                 CUtensorMap maps[6]) {
-  if (!seam_eligible(a, 0) || (tile_y != 15 && tile_y != 12)) return cudaErrorInvalidValue;
+  // the strips need periodic x and y; the batched form also builds them for
+  // cases narrower than a tile (its lanes fall back to global pulls there)
+  if (!tma_eligible(a, 0) || a.wx || a.wy || (tile_y != 15 && tile_y != 12))
+    return cudaErrorInvalidValue;
   const unsigned tw = (unsigned)kTmaTW[2], by = (unsigned)tile_y;
   const unsigned shape[6][2] = {{tw, by}, {tw + 2, by}, {2, by}, {tw, 2}, {tw + 2, 2}, {2, 2}};
   for (int m = 0; m < 6; ++m) {
@@ -247,8 +250,13 @@ cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
 bool valid_batch_config(const FusedConfig& c) {
   const bool shape = (c.tile_y == 8 && (c.hold == 2 || c.hold == 0)) ||
                      (c.tile_y == 16 && c.hold == 1) ||
-                     ((c.tile_y == 8 || c.tile_y == 15) && (c.hold == 7 || c.hold == 8));
+                     ((c.tile_y == 8 || c.tile_y == 15) && (c.hold == 7 || c.hold == 8)) ||
+                     (c.tile_y == 12 && c.hold == 7);
   return shape && c.zchunk > 0;
+}
+
+bool batch_seam_eligible(const StepArgs& a, int storage) {
+  return storage == 0 && tma_eligible(a, storage) && !a.wx && !a.wy && !a.bgk;
 }
 
 bool valid_fused_config(const FusedConfig& c, int storage) {

@@ -669,7 +669,11 @@ static cudaError_t launch_batch_v(const void* src, void* dst, const BatchCase* c
     if (e != cudaSuccess) return e;
     per_sm = q < 1 ? 1 : q;
   }
-  const int grid = min(total_items, sms * per_sm);
+  // one CTA per work item: the hardware hands the next item to whichever
+  // SM frees first (a persistent grid's static round-robin shares of
+  // unequal items end unevenly)
+  const int grid = total_items;
+  (void)sms;
   k_fused_batch<T, BY, WALLS, HOLD, MINB, BGK><<<grid, dim3(kTileW, BY), 0, s>>>(
       cases, ncases, total_items, (const T*)src, (T*)dst, zc);
   return cudaGetLastError();

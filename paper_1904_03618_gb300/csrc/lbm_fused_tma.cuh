@@ -431,7 +431,12 @@ __host__ __device__ constexpr int tma_issuer() {
 // stages and mbarrier phases continue across items.  map0 / map1: the
 // source buffer's tensor maps (param or global space).  Returns false after
 // a wait gave up (*err set, the CTA's copies drained).
-template <typename T, bool WALLS, int TW, int BY, int NS, bool SEAM = false>
+// FALLBACK (SEAM form, batches): a tile that spans both seams of an axis
+// (a case narrower than the tile's interior) gets the strips of its low
+// seam only; its lanes whose sources lie beyond the high seam pull from
+// global memory.
+template <typename T, bool WALLS, int TW, int BY, int NS, bool SEAM = false,
+          bool FALLBACK = false>
 __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restrict__ dst,
                                           const StepArgs& a, const CUtensorMap* map0,
                                           const CUtensorMap* map1, int bx, int by, int zb,
@@ -474,6 +479,12 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
 #pragma unroll
     for (int e = 0; e < 9; ++e)
       loff[e] = seam_lane_off<TW, BY>(tx, ty, cx, cy, e / 3 - 1, e % 3 - 1, a.nx, a.ny);
+  }
+  bool lane_global = false;
+  if constexpr (SEAM && FALLBACK) {
+    const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
+    lane_global = (x0 < 2 && x0 + TW - 2 >= a.nx - 1 && cx >= a.nx - 1) ||
+                  (y0 < 2 && y0 + BY - 2 >= a.ny - 1 && cy >= a.ny - 1);
   }
   int col0 = tx;
   if constexpr (tma_pair_bytes<T>() != 8) col0 = tx + 1 + ((x0 - 2) - ((x0 - 2) & ~3));
@@ -525,7 +536,8 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     float rR = 0.f, rB = 0.f;
     bool from_stage = false;
     if constexpr (SEAM) {
-      if (staged(zl)) {  // every lane (the first and last plane of z walls: global)
+      // every lane (the first and last plane of z walls: global)
+      if (staged(zl) && !lane_global) {
         float2 rho = make_float2(0.f, 0.f);
         StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
         rR = rho.x;
@@ -771,6 +783,87 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
   }
 }
 
+// Batched SEAM step (FP32, every case periodic in x and y): as
+// k_fused_tma_batch on the 34 x 12 tile with two stages, the six seam maps
+// of each case (main 34 and 36 wide, x strip, y strips, corner) from a
+// device table, six per case; cases narrower than the tile run through the
+// FALLBACK lanes.
+template <bool WALLS>
+__global__ void __launch_bounds__(34 * 12, 1)
+    k_fused_tma_seam_batch(const BatchCase* __restrict__ cases, int ncases, int total_items,
+                           const CUtensorMap* __restrict__ maps, const float* __restrict__ src_base,
+                           float* __restrict__ dst_base, int zchunk, int* __restrict__ err) {
+  constexpr int TW = 34, BY = 12, NS = 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ StepArgs sa;
+  __shared__ int s_case, s_item;
+  if (smem_addr(smem) & 127u) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
+    return;
+  }
+  tma_init_barriers(tma_mbar_bytes<float, TW, BY, NS, true>(smem), NS);
+  const unsigned long long wait_ns = tma_wait_limit();
+  unsigned G0 = 0;
+  for (int w = blockIdx.x; w < total_items; w += gridDim.x) {
+    __syncthreads();  // the previous item is done with the shared state
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      int lo = 0, hi = ncases - 1;  // last case with item_start <= w
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cases[mid].item_start <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      s_case = lo;
+      s_item = w - cases[lo].item_start;
+      sa = cases[lo].args;
+      const CUtensorMap* m = maps + 6 * lo;
+      for (int q = 0; q < 6; ++q)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(m + q)
+                     : "memory");
+    }
+    __syncthreads();
+    const BatchCase& bc = cases[s_case];
+    const int item = s_item;
+    const int bx = item % bc.tiles_x, rest = item / bc.tiles_x;
+    const int by = rest % bc.tiles_y, chunk = rest / bc.tiles_y;
+    const int zb = chunk * zchunk;
+    const int ze = min(zb + zchunk, sa.nz);
+    const size_t off = 2 * (size_t)bc.pair_base;
+    const CUtensorMap* m = maps + 6 * s_case;
+    const SeamStripMaps strips = {m + 2, m + 3, m + 4, m + 5};
+    if (!tma_chunk<float, WALLS, TW, BY, NS, true, true>(src_base + off, dst_base + off, sa,
+                                                         m, m + 1, bx, by, zb, ze, smem, G0,
+                                                         err, wait_ns, &strips))
+      return;
+    G0 += (unsigned)(ze - zb + 2);
+  }
+}
+
+template <bool WALLS>
+static cudaError_t launch_tma_seam_batch_v(const void* src, void* dst, const BatchCase* cases,
+                                           int ncases, int total_items, const CUtensorMap* maps,
+                                           int zc, int* err, int sms, cudaStream_t s) {
+  static_assert(tma_fits<float, 34, 12, 2, true>(), "SEAM stages do not fit");
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = device_slot();
+  constexpr int bytes = tma_smem_bytes<float, 34, 12, 2, true>();
+  if (!attr_set[dv]) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam_batch<WALLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set[dv] = true;
+  }
+  // one CTA per work item: the hardware hands the next item to whichever
+  // SM frees first (a persistent grid taking items round-robin ran the
+  // 512-case droplet sweep 20-30 % slower: its static shares of unequal
+  // items end unevenly)
+  const int grid = total_items;
+  (void)sms;
+  k_fused_tma_seam_batch<WALLS><<<grid, dim3(34, 12), bytes, s>>>(
+      cases, ncases, total_items, maps, (const float*)src, (float*)dst, zc, err);
+  return cudaGetLastError();
+}
+
 // Tensor maps are built on the host (lbm_dispatch.cu); the launcher only
 // sets the dynamic shared-memory limit once per instantiation.
 template <typename T, bool WALLS, int TW, int BY, int NS>
@@ -843,7 +936,9 @@ static cudaError_t launch_tma_batch_v(const void* src, void* dst, const BatchCas
       if (e != cudaSuccess) return e;
       per_sm = q < 1 ? 1 : q;
     }
-    const int grid = min(total_items, sms * per_sm);
+    // one CTA per work item (see launch_tma_seam_batch_v)
+    const int grid = total_items;
+    (void)sms;
     k_fused_tma_batch<T, WALLS, TW, BY, NS><<<grid, dim3(TW, BY), bytes, s>>>(
         cases, ncases, total_items, maps, (const T*)src, (T*)dst, zc, err);
     return cudaGetLastError();

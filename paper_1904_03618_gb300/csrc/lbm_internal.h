@@ -113,8 +113,13 @@ cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a,
 // CTAs over the SMs ends first.
 int seam12_zchunk(const StepArgs& a, int sms);
 bool tma_config_fits(int storage, int kind, int ns);
-// Interior width of a tile (30, or 32 for the 34 x 15 tile, tile_y 15).
-inline int tile_interior_x(int tile_y) { return tile_y == 15 ? 32 : 30; }
+// Interior width of a tile (30, or 32 for the 34-wide tiles: tile_y 15, 12).
+inline int tile_interior_x(int tile_y) { return tile_y == 15 || tile_y == 12 ? 32 : 30; }
+// A batch case the batched SEAM form (34 x 12, two stages) can run: FP32,
+// periodic in x and y, TMA eligible, MRT.  Cases narrower than a tile in x
+// or y run it too: lanes whose sources wrap across the far seam of a tile
+// that spans both seams of an axis pull from global memory.
+bool batch_seam_eligible(const StepArgs& a, int storage);
 // Default TMA configuration for a single lattice (false: keep the plain one).
 bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind_ok[3],
                         FusedConfig* out);
@@ -174,6 +179,12 @@ cudaError_t launch_fused_tma_batch(int storage, const void* src, void* dst,
                                    bool walls, const CUtensorMap* maps, int kind, int ns, int zc,
                                    int* err, int sms, cudaStream_t s);
 bool valid_batch_config(const FusedConfig& c);
+// Batched SEAM step: maps6 = the device table of the source buffer's six
+// seam maps (tile_y 12) per case.
+cudaError_t launch_fused_tma_seam_batch(const void* src, void* dst, const BatchCase* cases,
+                                        int ncases, int total_items, bool walls,
+                                        const CUtensorMap* maps6, int zc, int* err, int sms,
+                                        cudaStream_t s);
 bool valid_fused_config(const FusedConfig& c, int storage);
 
 }  // namespace lbm

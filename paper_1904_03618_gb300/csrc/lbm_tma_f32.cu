@@ -27,4 +27,14 @@ cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a,
                   : launch_tma_seam_v<34, 12, 2, false>(src, dst, a, maps6, zc, err, s);
   return cudaErrorInvalidValue;
 }
+
+cudaError_t launch_fused_tma_seam_batch(const void* src, void* dst, const BatchCase* cases,
+                                        int ncases, int total_items, bool walls,
+                                        const CUtensorMap* maps6, int zc, int* err, int sms,
+                                        cudaStream_t s) {
+  return walls ? launch_tma_seam_batch_v<true>(src, dst, cases, ncases, total_items, maps6, zc,
+                                               err, sms, s)
+               : launch_tma_seam_batch_v<false>(src, dst, cases, ncases, total_items, maps6, zc,
+                                                err, sms, s);
+}
 }  // namespace lbm

@@ -180,3 +180,54 @@ def test_batch_step_before_all_cases_are_initialised():
         b.step(1)
     assert ei.value.status == lbm.LBM_ERR_STATE
     b.close()
+
+
+# FP32 cases periodic in x and y: the batched SEAM form (34 x 12 tile, two
+# stages, the periodic seams staged by strip copies), an autotuner option
+# for such batches.  Cases narrower than the tile's 32 x 10 interior in x or y (a
+# tile spanning both seams of the axis) pull the far seam's sources from
+# global memory.
+SEAM_CASES = [
+    _case(32, 32, 32, rho_in_R=1.0, alpha_R=1 / 3, alpha_B=1 / 3, A_R=0.0225, A_B=0.0225),
+    _case(44, 17, 23, wall=(0, 0, 1), gravity=(0, 0, -1e-5)),
+    _case(64, 13, 9, improved=False, force=(1e-5, 0, 0)),
+    _case(20, 20, 20, rho_in_R=10.0, alpha_R=0.97, A_R=0.01125, A_B=0.01125),
+    _case(36, 24, 12, wall=(0, 0, 1), wetting=True, contact_angle_deg=120.0),
+    _case(2, 6, 5, force=(0.0, 1e-5, 0.0)),
+    _case(48, 48, 16),
+]
+
+
+@pytest.mark.parametrize("zchunk", [0, 5, 32])
+def test_batch_seam_cases_equal_single_lattices(zchunk):
+    stream = torch.cuda.Stream(DEV)
+    params = [lbm.make_params(**d) for d in SEAM_CASES]
+    b = lbm.Batch(params, device=DEV, stream=stream)
+    lbm.lbm_set_fused_config(b.ctx, 12, zchunk, 7)
+    for k, d in enumerate(SEAM_CASES):
+        b.init_fields(k, *_fields(d, 7))
+    b.step(7)
+    assert b.diagnostics(0)[5] == 0
+    for k, d in enumerate(SEAM_CASES):
+        got = b.get_f(k)
+        ref = _run_single(d, 7)
+        err = (got.double() - ref.double()).abs().max() / ref.double().abs().max()
+        assert err.item() <= 1e-5, (k, err.item())
+    b.close()
+
+
+@pytest.mark.parametrize("k", [0, 3, 5])
+def test_batch_seam_double_seam_case_against_oracle(k):
+    """Cases narrower than the tile (32^3, 20^3, 2 x 6 x 5): one step of the
+    batched SEAM form against the oracle."""
+    b = lbm.Batch([lbm.make_params(**dd) for dd in SEAM_CASES], device=DEV,
+                  stream=torch.cuda.Stream(DEV))
+    lbm.lbm_set_fused_config(b.ctx, 12, 0, 7)
+    for j, dd in enumerate(SEAM_CASES):
+        b.init_fields(j, *_fields(dd, 7))
+    f0 = b.get_f(k).double().cpu().numpy()
+    b.step(1)
+    got = b.get_f(k).double().cpu().numpy()
+    b.close()
+    ref = oracle.step(oracle.params_from(SEAM_CASES[k]), f0, 1)
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= 1e-5
