@@ -665,7 +665,10 @@ def batch_measure(args, dev):
             lbm.lbm_batch_init_fields(b.ctx, k, rR, rB, u)
         stream.synchronize()
         del fields
-        tuned = autotune.tune(b.ctx, plist, stream, steps=6, cache_path=None)
+        if args.batch_tune:
+            tuned = autotune.tune(b.ctx, plist, stream, steps=6, cache_path=None)
+        else:
+            tuned = lbm.lbm_get_fused_config(b.ctx)
         b.step(max(args.warmup, 4))
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -852,6 +855,8 @@ def main():
     ap.add_argument("--batch", type=int, default=512,
                     help="number of cases of the batched droplet sweep (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--no-batch-tune", dest="batch_tune", action="store_false",
+                    help="run the batch in the library's default configuration")
     ap.add_argument("--gemm", action="store_true",
                     help="also time the surrogate's tensor-core GEMM")
     ap.add_argument("--slabs", action="store_true",

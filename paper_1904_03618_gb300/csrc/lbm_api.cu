@@ -58,6 +58,8 @@ struct lbm_ctx {
   CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
   CUtensorMap smaps[2][2][6];  // [tile: 0 = 34 x 15, 1 = 34 x 12][buffer][map]: SEAM forms
   bool seam_ok;                // smaps built (FP32, periodic in x and y)
+  CUtensorMap smaps16[2][2][4];  // [tile: 0 = 34 x 15, 1 = 34 x 12][buffer][map]: 16-bit SEAM
+  bool seam16_ok;                // smaps16 built (FP16 / BF16, periodic in x and y)
   CUtensorMap* d_bmaps[2][3];  // batches: [buffer][tile kind] -> device table, 2 per case
   bool batch_tma_ok[3];        // batch tables built, per tile kind
   CUtensorMap* d_seam_bmaps[2];  // batches: [buffer] -> six seam maps (tile_y 12) per case
@@ -531,6 +533,20 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
       c->fused.hold = 7;
       c->fused.zchunk = lbm::seam12_zchunk(c->cases[0].args, c->sms);
     }
+    if (lbm::seam16_eligible(c->cases[0].args, c->storage)) {
+      c->seam16_ok = true;
+      for (int t = 0; t < 2 && c->seam16_ok; ++t)
+        for (int b = 0; b < 2 && c->seam16_ok; ++b)
+          c->seam16_ok = lbm::tma_build_seam16_maps(c->storage, c->pop[b], c->cases[0].args,
+                                                    t == 0 ? 15 : 12,
+                                                    c->smaps16[t][b]) == cudaSuccess;
+      cudaGetLastError();
+      if (c->seam16_ok && c->fused.tile_y == 15 && c->fused.hold == 8) {
+        // the 16-bit seam form: two stages, the list-schedule chunk
+        c->fused.hold = 7;
+        c->fused.zchunk = lbm::list_schedule_zchunk(c->cases[0].args, c->sms, 13);
+      }
+    }
   }
   if (st == LBM_OK && ncases > 1) {
     // tensor maps of every case for the batched TMA step (tile kinds 0, 2)
@@ -786,6 +802,11 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
                                 c->fused, c->sms, c->stream);
   else if (c->kernel == LBM_KERNEL_TWO_PASS)
     e = lbm::launch_twopass(c->storage, src, dst, c->cases[0].args, c->phase, c->stream);
+  else if (c->seam16_ok && c->fused.hold == 7 &&
+           (c->fused.tile_y == 15 || c->fused.tile_y == 12))
+    e = lbm::launch_fused_tma_seam16(c->storage, src, dst, c->cases[0].args, c->fused.tile_y,
+                                     c->smaps16[c->fused.tile_y == 15 ? 0 : 1][from],
+                                     c->fused.zchunk, c->d_flags, c->stream);
   else if (c->seam_ok && ((c->fused.hold == 8 && c->fused.tile_y == 15) ||
                            (c->fused.hold == 7 && c->fused.tile_y == 12)))
     e = lbm::launch_fused_tma_seam(src, dst, c->cases[0].args, c->fused.tile_y,
@@ -1197,10 +1218,10 @@ extern "C" lbm_status lbm_set_fused_config(lbm_ctx* c, int tile_y, int zchunk,
       c->err[0] = 0;
       return LBM_OK;
     }
-    if (!(c->seam_ok && hold == 7 && zchunk >= 0))
+    if (!((c->seam_ok || c->seam16_ok) && hold == 7 && zchunk >= 0))
       return fail(c, LBM_ERR_ARG,
-                  "tile_y 12 is the two-stage seam form (hold 7) of single periodic FP32 "
-                  "lattices with nx a multiple of 2, nx >= 34 and ny >= 15");
+                  "tile_y 12 is the two-stage seam form (hold 7) of single periodic lattices "
+                  "with nx a multiple of 2 (FP32) or 4 (16-bit), nx >= 34 and ny >= 15");
     if (zchunk == 0) f.zchunk = lbm::seam12_zchunk(c->cases[0].args, c->sms);
     c->fused = f;
     drop_graph(c);
@@ -1257,6 +1278,10 @@ extern "C" lbm_status lbm_default_fused_config(const lbm_params* p, int sms, int
       f.tile_y = 12;
       f.hold = 7;
       f.zchunk = lbm::seam12_zchunk(a, sms);
+    }
+    if (lbm::seam16_eligible(a, p->storage) && f.tile_y == 15 && f.hold == 8) {
+      f.hold = 7;
+      f.zchunk = lbm::list_schedule_zchunk(a, sms, 13);
     }
   }
   *tile_y = f.tile_y;

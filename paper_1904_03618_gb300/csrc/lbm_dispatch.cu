@@ -185,7 +185,9 @@ cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int
   return cudaSuccess;
 }
 
-int seam12_zchunk(const StepArgs& a, int sms) {
+int seam12_zchunk(const StepArgs& a, int sms) { return list_schedule_zchunk(a, sms, 10); }
+
+int list_schedule_zchunk(const StepArgs& a, int sms, int rows) {
   // One CTA per SM; the hardware hands the CTAs out in launch order (tile
   // columns fastest, then z chunks) to whichever SM falls free, so a step
   // lasts as long as that list schedule.  A CTA of p planes costs p + 3
@@ -195,7 +197,7 @@ int seam12_zchunk(const StepArgs& a, int sms) {
   // picks the measured fastest chunk, where counting whole rounds of
   // equal CTAs picked 16 planes at 128^3 (4.5 % slower than 24).
   constexpr double kOverhead = 3.0;
-  const long long cols = (long long)((a.nx + 31) / 32) * ((a.ny + 9) / 10);
+  const long long cols = (long long)((a.nx + 31) / 32) * ((a.ny + rows - 1) / rows);
   const int slots = sms > 0 ? sms : 152;
   std::vector<double> heap((size_t)slots);
   int best_zc = 12;
@@ -243,6 +245,35 @@ cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+bool seam16_eligible(const StepArgs& a, int storage) {
+  return storage != 0 && tma_eligible(a, storage) && !a.wx && !a.wy && a.nx >= kTmaTW[2] &&
+         a.ny >= kTmaBY[2];
+}
+
+cudaError_t tma_build_seam16_maps(int storage, const void* base, const StepArgs& a, int tile_y,
+                                  CUtensorMap maps[4]) {
+  if (!seam16_eligible(a, storage) || (tile_y != 15 && tile_y != 12))
+    return cudaErrorInvalidValue;
+  const unsigned w = (unsigned)(kTmaTW[2] + 4 + 3) / 4 * 4, by = (unsigned)tile_y;
+  const unsigned shape[4][2] = {{w, by}, {4, by}, {w, 2}, {4, 2}};
+  for (int m = 0; m < 4; ++m) {
+    cudaError_t e = encode_box(storage, base, a, shape[m][0], shape[m][1], &maps[m]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fused_tma_seam16(int storage, const void* src, void* dst, const StepArgs& a,
+                                    int tile_y, const CUtensorMap* maps4, int zchunk, int* err,
+                                    cudaStream_t s) {
+  if (storage == 1)
+    return launch_fused_tma_seam16_storage<__half>(src, dst, a, tile_y, maps4, zchunk, err, s);
+  if (storage == 2)
+    return launch_fused_tma_seam16_storage<__nv_bfloat16>(src, dst, a, tile_y, maps4, zchunk,
+                                                          err, s);
+  return cudaErrorInvalidValue;
 }
 
 // Batched kernel variants: (tile_y, hold) = (8, 2), (8, 0), (16, 1), and

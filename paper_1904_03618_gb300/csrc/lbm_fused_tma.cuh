@@ -117,9 +117,36 @@ template <int TW, int BY>
 __host__ __device__ constexpr int seam_block_bytes() {
   return seam_cs_off<TW, BY>(TW + 2) + 128;
 }
+// 16-bit SEAM form (4-byte pairs; TMA boxes start on 16-byte boundaries, so
+// strips are four pairs wide): per direction one block = main box (W16 =
+// TW + 4 rounded up to 4 pairs, from x = (x0 - 2) & ~3) | x strip (4 x BY,
+// from x = nx - 4 at the low seam, 0 at the high one) | y strip (W16 x 2) |
+// corner (4 x 2), each part 128-byte aligned.
+template <int TW>
+__host__ __device__ constexpr int s16_w() {
+  return (TW + 4 + 3) / 4 * 4;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int s16_xs_off() {
+  return (s16_w<TW>() * BY * 4 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int s16_ys_off() {
+  return s16_xs_off<TW, BY>() + (4 * BY * 4 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int s16_cs_off() {
+  return s16_ys_off<TW, BY>() + (s16_w<TW>() * 2 * 4 + 127) / 128 * 128;
+}
+template <int TW, int BY>
+__host__ __device__ constexpr int s16_block_bytes() {
+  return s16_cs_off<TW, BY>() + 128;
+}
 template <typename T, int TW, int BY, bool SEAM = false>
 __host__ __device__ constexpr int tma_stage_bytes() {
-  return SEAM ? 19 * seam_block_bytes<TW, BY>() : tma_box_off<T, TW, BY>(19);
+  return SEAM ? 19 * (tma_pair_bytes<T>() == 8 ? seam_block_bytes<TW, BY>()
+                                                : s16_block_bytes<TW, BY>())
+              : tma_box_off<T, TW, BY>(19);
 }
 // Bytes the 19 copies of a plane deliver (the boxes without their padding):
 // the transaction count the stage's mbarrier expects.
@@ -363,6 +390,94 @@ struct StageReduceSeam<TW, BY, 19> {
                                              float2&) {}
 };
 
+// 16-bit SEAM form, one thread: the main boxes of a plane (one map) ...
+template <int TW, int BY, int I>
+struct TmaIssueSeamMain16 {
+  __device__ __forceinline__ static void run(unsigned block0, const CUtensorMap* m0, int x0,
+                                             int y0, int zz, int nz, unsigned mbar) {
+    tma_load_4d(block0 + (unsigned)(I * s16_block_bytes<TW, BY>()), m0, (x0 - 2) & ~3,
+                y0 - 1 - ey(I), wrap1(zz - ez(I), nz), I, mbar);
+    TmaIssueSeamMain16<TW, BY, I + 1>::run(block0, m0, x0, y0, zz, nz, mbar);
+  }
+};
+template <int TW, int BY>
+struct TmaIssueSeamMain16<TW, BY, 19> {
+  __device__ __forceinline__ static void run(unsigned, const CUtensorMap*, int, int, int, int,
+                                             unsigned) {}
+};
+// ... and, on a seam tile, the strips a lane can read (xs: first pair of the
+// x strip, nx - 4 or 0; ys: first row of the y strip, ny - 2 or 0; < 0: none).
+template <int TW, int BY, int I>
+struct TmaIssueStrips16 {
+  __device__ __forceinline__ static void run(unsigned block0, const SeamStripMaps& sm, int x0,
+                                             int y0, int zz, int nz, int xs, int ys, bool xlo,
+                                             bool ylo, unsigned mbar) {
+    const unsigned blk = block0 + (unsigned)(I * s16_block_bytes<TW, BY>());
+    const int y = y0 - 1 - ey(I);
+    const int z = wrap1(zz - ez(I), nz);
+    const bool cx = xs >= 0 && seam_crosses<I>(ex(I), xlo);
+    const bool cy = ys >= 0 && seam_crosses<I>(ey(I), ylo);
+    if (cx) tma_load_4d(blk + s16_xs_off<TW, BY>(), sm.xs, xs, y, z, I, mbar);
+    if (cy) tma_load_4d(blk + s16_ys_off<TW, BY>(), sm.ys0, (x0 - 2) & ~3, ys, z, I, mbar);
+    if (cx && cy) tma_load_4d(blk + s16_cs_off<TW, BY>(), sm.cs, xs, ys, z, I, mbar);
+    TmaIssueStrips16<TW, BY, I + 1>::run(block0, sm, x0, y0, zz, nz, xs, ys, xlo, ylo, mbar);
+  }
+};
+template <int TW, int BY>
+struct TmaIssueStrips16<TW, BY, 19> {
+  __device__ __forceinline__ static void run(unsigned, const SeamStripMaps&, int, int, int, int,
+                                             int, int, bool, bool, unsigned) {}
+};
+template <int TW, int BY>
+__host__ __device__ constexpr int seam16_tx_bytes(bool xstrip, bool ystrip, bool xlo, bool ylo) {
+  int b = 0;
+  for (int i = 0; i < 19; ++i) {
+    const bool cx = xstrip && (xlo ? ex(i) >= 0 : ex(i) <= 0);
+    const bool cy = ystrip && (ylo ? ey(i) >= 0 : ey(i) <= 0);
+    b += s16_w<TW>() * BY * 4;
+    if (cx) b += 4 * BY * 4;
+    if (cy) b += s16_w<TW>() * 2 * 4;
+    if (cx && cy) b += 4 * 2 * 4;
+  }
+  return b;
+}
+// Byte offset, within a direction's block, of the pair a lane reads for a
+// direction (ex, ey) in the 16-bit SEAM form (see seam_lane_off).
+template <int TW, int BY>
+__device__ __forceinline__ unsigned seam16_lane_off(int tx, int ty, int cx, int cy, int ex_,
+                                                    int ey_, int nx, int ny) {
+  constexpr int W = s16_w<TW>();
+  const int col = tx + 3 - ex_;  // the main box starts at x0 - 4 (x0 a multiple of 4)
+  const int sx = cx - ex_, sy = cy - ey_;
+  const bool xin = sx >= 0 && sx < nx, yin = sy >= 0 && sy < ny;
+  const int xi = sx < 0 ? sx + 4 : sx - nx, yc = sy < 0 ? sy + 2 : sy - ny;
+  const bool used = cx >= -1 && cx <= nx && cy >= -1 && cy <= ny;
+  const bool xok = used && xi >= 0 && xi < 4, yok = used && yc >= 0 && yc < 2;
+  int off = (ty * W + col) * 4;
+  if (!xin && yin && xok) off = s16_xs_off<TW, BY>() + (ty * 4 + xi) * 4;
+  if (xin && !yin && yok) off = s16_ys_off<TW, BY>() + (yc * W + col) * 4;
+  if (!xin && !yin && xok && yok) off = s16_cs_off<TW, BY>() + (yc * 4 + xi) * 4;
+  return (unsigned)off;
+}
+template <typename T, int TW, int BY, int I>
+struct StageReduceSeam16 {
+  __device__ __forceinline__ static void run(const unsigned char* stage, const unsigned* loff,
+                                             const StepArgs& a, float* f, float2& rho) {
+    using Pair = typename Store<T>::Pair;
+    float2 v = Store<T>::to_float2(*reinterpret_cast<const Pair*>(
+        stage + I * s16_block_bytes<TW, BY>() + loff[(ex(I) + 1) * 3 + (ey(I) + 1)]));
+    add_offsets<T, I>(a, v);
+    rho = __fadd2_rn(rho, v);
+    f[I] = v.x + v.y;
+    StageReduceSeam16<T, TW, BY, I + 1>::run(stage, loff, a, f, rho);
+  }
+};
+template <typename T, int TW, int BY>
+struct StageReduceSeam16<T, TW, BY, 19> {
+  __device__ __forceinline__ static void run(const unsigned char*, const unsigned*,
+                                             const StepArgs&, float*, float2&) {}
+};
+
 // Reads the 19 pairs of one cell from a stage, reduced on the fly to
 // (f_i = fR_i + fB_i, rho_R, rho_B).  col0 = tx (FP32) or tx + 1 + o (16-bit).
 template <typename T, int TW, int BY, int I>
@@ -443,8 +558,8 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
                                           int ze, unsigned char* smem, unsigned G0,
                                           int* __restrict__ err, unsigned long long wait_ns,
                                           const SeamStripMaps* strips = nullptr) {
-  static_assert(!SEAM || tma_pair_bytes<T>() == 8,
-                "the SEAM form is FP32, periodic in x and y (walls in z allowed)");
+  static_assert(!SEAM || tma_pair_bytes<T>() == 8 || (TW - 2) % 4 == 0,
+                "the 16-bit SEAM form needs tile columns on 16-byte boundaries");
   constexpr int SB = tma_stage_bytes<T, TW, BY, SEAM>();
   constexpr int HV = tma_hold_vals<T, TW, BY, NS, SEAM>();
   using Pair = typename Store<T>::Pair;
@@ -469,7 +584,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   int TX = tma_stage_tx_bytes<T, TW, BY>();
   int seam_xs = -1, seam_ys = -1;
   unsigned loff[9];
-  if constexpr (SEAM) {
+  if constexpr (SEAM && tma_pair_bytes<T>() == 8) {
     const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
     if (x0 < 2) seam_xs = a.nx - 2;
     else if (x0 + TW - 2 >= a.nx - 1) seam_xs = 0;
@@ -479,6 +594,16 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
 #pragma unroll
     for (int e = 0; e < 9; ++e)
       loff[e] = seam_lane_off<TW, BY>(tx, ty, cx, cy, e / 3 - 1, e % 3 - 1, a.nx, a.ny);
+  } else if constexpr (SEAM) {  // 16-bit pairs: strips four pairs wide
+    const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;
+    if (x0 < 2) seam_xs = a.nx - 4;
+    else if (x0 + TW - 2 >= a.nx - 1) seam_xs = 0;
+    if (y0 < 2) seam_ys = a.ny - 2;
+    else if (y0 + BY - 2 >= a.ny - 1) seam_ys = 0;
+    TX = seam16_tx_bytes<TW, BY>(seam_xs >= 0, seam_ys >= 0, x0 < 2, y0 < 2);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      loff[e] = seam16_lane_off<TW, BY>(tx, ty, cx, cy, e / 3 - 1, e % 3 - 1, a.nx, a.ny);
   }
   bool lane_global = false;
   if constexpr (SEAM && FALLBACK) {
@@ -513,12 +638,17 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m),
                    "r"(TX)
                    : "memory");
-      if constexpr (SEAM) {
+      if constexpr (SEAM && tma_pair_bytes<T>() == 8) {
         TmaIssueSeamMain<TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz,
                                          m);
         if (seam_xs >= 0 || seam_ys >= 0)
           TmaIssueStrips<TW, BY, 0>::run(st_addr(k), *strips, x0, y0, wrap1(zl, a.nz), a.nz,
                                          seam_xs, seam_ys, x0 < 2, y0 < 2, m);
+      } else if constexpr (SEAM) {
+        TmaIssueSeamMain16<TW, BY, 0>::run(st_addr(k), map0, x0, y0, wrap1(zl, a.nz), a.nz, m);
+        if (seam_xs >= 0 || seam_ys >= 0)
+          TmaIssueStrips16<TW, BY, 0>::run(st_addr(k), *strips, x0, y0, wrap1(zl, a.nz), a.nz,
+                                           seam_xs, seam_ys, x0 < 2, y0 < 2, m);
       } else {
         TmaIssue<T, TW, BY, 0>::run(st_addr(k), map0, map1, x0, y0, wrap1(zl, a.nz), a.nz, m);
       }
@@ -539,7 +669,10 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
       // every lane (the first and last plane of z walls: global)
       if (staged(zl) && !lane_global) {
         float2 rho = make_float2(0.f, 0.f);
-        StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
+        if constexpr (tma_pair_bytes<T>() == 8)
+          StageReduceSeam<TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, f, rho);
+        else
+          StageReduceSeam16<T, TW, BY, 0>::run(stage0 + stage_of(k) * SB, loff, a, f, rho);
         rR = rho.x;
         rB = rho.y;
         from_stage = true;
@@ -726,6 +859,70 @@ static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs&
                                                    maps6[1], maps6[2], maps6[3], maps6[4],
                                                    maps6[5], zc, err);
   return cudaGetLastError();
+}
+
+// 16-bit SEAM form (FP16 / BF16 deviation storage, periodic in x and y,
+// walls in z allowed): the source buffer's four maps (main W16 x BY, x strip
+// 4 x BY, y strip W16 x 2, corner 4 x 2) as kernel parameters.
+template <typename T, int TW, int BY, int NS, bool WALLS>
+__global__ void __launch_bounds__(TW* BY, 1)
+    k_fused_tma_seam16(const T* __restrict__ src, T* __restrict__ dst,
+                       const __grid_constant__ StepArgs a,
+                       const __grid_constant__ CUtensorMap map0,
+                       const __grid_constant__ CUtensorMap mxs,
+                       const __grid_constant__ CUtensorMap mys,
+                       const __grid_constant__ CUtensorMap mcs, int zchunk,
+                       int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int zb = blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, a.nz);
+  if (zb >= ze) return;
+  if (smem_addr(smem) & 127u) {  // the copies need 128-byte aligned blocks
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
+    return;
+  }
+  tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS, true>(smem), NS);
+  __syncthreads();
+  const SeamStripMaps strips = {&mxs, &mys, &mys, &mcs};
+  tma_chunk<T, WALLS, TW, BY, NS, true>(src, dst, a, &map0, &map0, blockIdx.x, blockIdx.y, zb,
+                                        ze, smem, 0u, err, tma_wait_limit(), &strips);
+}
+
+template <typename T, int TW, int BY, int NS, bool WALLS>
+static cudaError_t launch_tma_seam16_v(const void* src, void* dst, const StepArgs& a,
+                                       const CUtensorMap* maps4, int zc, int* err,
+                                       cudaStream_t s) {
+  static_assert(tma_fits<T, TW, BY, NS, true>(), "16-bit SEAM stages do not fit");
+  static bool attr_set[kMaxDevices] = {};
+  const int dv = device_slot();
+  constexpr int bytes = tma_smem_bytes<T, TW, BY, NS, true>();
+  if (!attr_set[dv]) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam16<T, TW, BY, NS, WALLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr_set[dv] = true;
+  }
+  dim3 blk(TW, BY);
+  dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
+  k_fused_tma_seam16<T, TW, BY, NS, WALLS><<<grd, blk, bytes, s>>>(
+      (const T*)src, (T*)dst, a, maps4[0], maps4[1], maps4[2], maps4[3], zc, err);
+  return cudaGetLastError();
+}
+
+// 16-bit SEAM forms: tile_y 15 (34 x 15) or 12 (34 x 12), two stages.
+template <typename T>
+cudaError_t launch_fused_tma_seam16_storage(const void* src, void* dst, const StepArgs& a,
+                                            int tile_y, const CUtensorMap* maps4, int zchunk,
+                                            int* err, cudaStream_t s) {
+  const int zc = zchunk > 0 ? zchunk : a.nz;
+  const bool zwalls = a.wz != 0;
+  if (tile_y == 15)
+    return zwalls ? launch_tma_seam16_v<T, 34, 15, 2, true>(src, dst, a, maps4, zc, err, s)
+                  : launch_tma_seam16_v<T, 34, 15, 2, false>(src, dst, a, maps4, zc, err, s);
+  if (tile_y == 12)
+    return zwalls ? launch_tma_seam16_v<T, 34, 12, 2, true>(src, dst, a, maps4, zc, err, s)
+                  : launch_tma_seam16_v<T, 34, 12, 2, false>(src, dst, a, maps4, zc, err, s);
+  return cudaErrorInvalidValue;
 }
 
 // Batched TMA step: persistent CTAs take the work items (case, z chunk,

@@ -109,9 +109,27 @@ cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
 cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
                                   const CUtensorMap* maps6, int zchunk, int* err,
                                   cudaStream_t s);
+// 16-bit SEAM forms (FP16 / BF16, 34 x 15 or 34 x 12 threads, two stages;
+// tile_y 15 or 12): periodic in x and y (walls in z allowed), nx a multiple
+// of 4, nx >= 34 and ny >= 15.  Four maps over the source buffer: main (38
+// rounded up to 40 pairs x tile_y), x strip (4 x tile_y), y strip (40 x 2),
+// corner (4 x 2).
+bool seam16_eligible(const StepArgs& a, int storage);
+cudaError_t tma_build_seam16_maps(int storage, const void* base, const StepArgs& a, int tile_y,
+                                  CUtensorMap maps[4]);
+template <typename T>
+cudaError_t launch_fused_tma_seam16_storage(const void* src, void* dst, const StepArgs& a,
+                                            int tile_y, const CUtensorMap* maps4, int zchunk,
+                                            int* err, cudaStream_t s);
+cudaError_t launch_fused_tma_seam16(int storage, const void* src, void* dst, const StepArgs& a,
+                                    int tile_y, const CUtensorMap* maps4, int zchunk, int* err,
+                                    cudaStream_t s);
 // z chunk of the 34 x 12 two-stage SEAM form: the one whose list schedule of
 // CTAs over the SMs ends first.
 int seam12_zchunk(const StepArgs& a, int sms);
+// The same list-schedule model for a 34-wide tile of `rows` interior rows
+// (one CTA per SM): 10 for the 34 x 12 tile, 13 for the 34 x 15 tile.
+int list_schedule_zchunk(const StepArgs& a, int sms, int rows);
 bool tma_config_fits(int storage, int kind, int ns);
 // Interior width of a tile (30, or 32 for the 34-wide tiles: tile_y 15, 12).
 inline int tile_interior_x(int tile_y) { return tile_y == 15 || tile_y == 12 ? 32 : 30; }

@@ -11,4 +11,7 @@ template cudaError_t launch_fused_tma_batch_storage<__nv_bfloat16>(
     int, cudaStream_t);
 template bool tma_config_fits_storage<__nv_bfloat16>(int, int);
 template cudaError_t tma_set_wait_ns<__nv_bfloat16>(unsigned long long);
+template cudaError_t launch_fused_tma_seam16_storage<__nv_bfloat16>(const void*, void*, const StepArgs&,
+                                                         int, const CUtensorMap*, int, int*,
+                                                         cudaStream_t);
 }  // namespace lbm

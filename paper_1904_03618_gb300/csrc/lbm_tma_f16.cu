@@ -11,4 +11,7 @@ template cudaError_t launch_fused_tma_batch_storage<__half>(
     int, cudaStream_t);
 template bool tma_config_fits_storage<__half>(int, int);
 template cudaError_t tma_set_wait_ns<__half>(unsigned long long);
+template cudaError_t launch_fused_tma_seam16_storage<__half>(const void*, void*, const StepArgs&,
+                                                         int, const CUtensorMap*, int, int*,
+                                                         cudaStream_t);
 }  // namespace lbm

@@ -101,14 +101,17 @@ def test_seam_form_matches_oracle_across_the_periodic_seams(nx, ny, nz, tile_y, 
 
 
 def test_two_stage_seam_tile_is_accepted_only_where_it_applies():
-    ok = lbm.Lattice(lbm.make_params(**base(64, 30, 9, wall=(0, 0, 1))), device=DEV)
-    lbm.lbm_set_fused_config(ok.ctx, 12, 0, 7)
-    assert lbm.lbm_get_fused_config(ok.ctx)[0] == 12
-    ok.close()
+    for storage in ("f32", "f16", "bf16"):
+        ok = lbm.Lattice(lbm.make_params(storage=storage, **base(64, 30, 9, wall=(0, 0, 1))),
+                         device=DEV)
+        lbm.lbm_set_fused_config(ok.ctx, 12, 0, 7)
+        assert lbm.lbm_get_fused_config(ok.ctx)[0] == 12
+        ok.close()
     refused = [dict(base(64, 30, 9, wall=(1, 0, 0))),            # x walls
                dict(base(64, 30, 9), collision="bgk"),           # BGK: shared-memory hold
                dict(base(30, 30, 9)),                            # nx < 34
-               dict(base(64, 30, 9), storage="f16")]             # 16-bit storage
+               dict(base(64, 30, 9), storage="f16", wall=(0, 1, 0)),  # 16-bit, y walls
+               dict(base(66, 30, 9), storage="f16")]             # 16-bit, nx % 4 != 0
     for d in refused:
         storage = d.pop("storage", "f32")
         lat = lbm.Lattice(lbm.make_params(storage=storage, **d), device=DEV)
@@ -167,3 +170,52 @@ def test_tma_rejected_where_rows_are_not_16_byte_multiples():
             lbm.lbm_set_fused_config(lat.ctx, 15, 0, 2)
     finally:
         lat.close()
+
+
+SEAM16_CASES = [(72, 37, 19), (36, 16, 5), (132, 44, 11), (64, 28, 9), (100, 33, 7)]
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("tile_y", [15, 12])
+@pytest.mark.parametrize("zwall", [0, 1])
+@pytest.mark.parametrize("nx,ny,nz", SEAM16_CASES)
+def test_seam16_form_across_the_periodic_seams(nx, ny, nz, tile_y, zwall, storage):
+    """The 16-bit SEAM form (34 x 15 or 34 x 12 threads, two stages; strips
+    four pairs wide from the lattice's far side): a drop centred on the
+    corner (0, 0) puts the interface across both seams and their corner.
+    Three steps against the shared-memory hold within one rounding step of
+    the storage format, and one step against the oracle fed the stored
+    (rounded) state within the storage-ulp bar of the other 16-bit tests."""
+    pd = base(nx, ny, nz, wall=(0, 0, zwall))
+    rR, rB, u = wl.droplet(nx, ny, nz, 6.0, pd["rho_in_R"], pd["rho_in_B"],
+                           velocity=(0.02, -0.01, 0.005), center=(0.5, 0.5, nz / 2.0),
+                           noise=1e-3, seed=3)
+    f0 = np.asarray(oracle.init(oracle.params_from(pd), rR, rB, u),
+                    dtype=np.float32).astype(np.float64)
+    got, diag = run(pd, f0, 3, 7, 0, storage=storage, tile_y=tile_y)
+    ref_gpu, _ = run(pd, f0, 3, 2, 0, storage=storage)
+    ulp = 2.0 ** -10 if storage == "f16" else 2.0 ** -7
+    assert np.abs(got - ref_gpu).max() <= ulp * np.abs(ref_gpu).max()
+    assert diag[5] == 0
+    # one step from the stored state against the oracle
+    p = lbm.make_params(storage=storage, **pd)
+    p.ref_R, p.ref_B = 0.0, pd["rho_in_B"]
+    lat = lbm.Lattice(p, device=DEV)
+    lbm.lbm_set_fused_config(lat.ctx, tile_y, 0, 7)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    s0 = lat.get_f().double().cpu().numpy()
+    lat.step(1)
+    s1 = lat.get_f().double().cpu().numpy()
+    lat.close()
+    ref = oracle.step(oracle.params_from(pd), s0, 1)
+    unit = 2.0 ** -11 if storage == "f16" else 2.0 ** -8   # the stored format's ulp
+    bar = unit * (1.0 + pd["rho_in_B"] * pd["alpha_B"] / np.abs(ref).max()) + 1e-5
+    assert np.abs(s1 - ref).max() / np.abs(ref).max() <= bar
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_seam16_form_is_the_default_on_a_periodic_16_bit_cube(storage):
+    p = lbm.make_params(storage=storage, **base(128, 128, 128))
+    lat = lbm.Lattice(p, device=DEV)
+    assert tuple(lbm.lbm_get_fused_config(lat.ctx))[::2] == (15, 7)
+    lat.close()

@@ -27,7 +27,7 @@ def _droplet(n, **kw):
     (_droplet(192), (12, 31, 7)),
     (_droplet(256), (12, 32, 7)),
     (_droplet(256, nz=1024, wall=(0, 0, 1)), (12, 32, 7)),   # Rayleigh-Taylor lattice
-    (_droplet(128, storage="f16"), (15, 12, 8)),
+    (_droplet(128, storage="f16"), (15, 18, 7)),    # the 16-bit seam form, two stages
     (_droplet(128, wall=(1, 1, 0)), (15, 12, 7)),
 ])
 def test_matches_the_configurations_live_contexts_reported(kw, want):
