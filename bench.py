@@ -693,20 +693,28 @@ def batch_measure(args, dev):
 
 def gemm_measure(lbm, dev):
     """The surrogate network's tensor-core GEMM (lbm_gemm_bf16) on the
-    shapes of its training: forward H W (65,536 x 256 x 256), the input
-    layer (65,536 x 256 x 5) and the weight gradient H^T dZ (256 x 256 x
-    65,536); TFLOP/s by CUDA events over 20 launches, against cuBLAS on the
-    same BF16-rounded operands (torch.matmul) for context."""
+    shapes of its use: forward H W (65,536 x 256 x 256), the input layer
+    (65,536 x 256 x 5), the backward dZ W^T, the weight gradient H^T dZ
+    (256 x 256 x 65,536), and one layer of a batch-256 training step (256 x
+    256 x 256); time by CUDA events over 20 launches, against cuBLAS on the
+    same BF16-rounded operands (torch.matmul) for context.  The FP32
+    operands are read once and C written once, 4 (MK + KN + MN) bytes: at
+    these shapes the product is bound by HBM (about 86 flop per byte against
+    a ridge near 280), so the line reports both fractions."""
     import torch
     torch.manual_seed(0)
-    peak = None
+    peak = hbm = None
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
-        peak = float(json.load(open(path))["bf16_tflops"])
+        mp = json.load(open(path))
+        peak = float(mp["bf16_tflops"])
+        hbm = float(mp["hbm_gbs"])
     shapes = [("forward H W", 65536, 256, 256, False, False),
+              ("input layer X W", 65536, 256, 5, False, False),
+              ("backward dZ W^T", 65536, 256, 256, False, True),
               ("weight gradient H^T dZ", 256, 256, 65536, True, False),
-              ("backward dZ W^T", 65536, 256, 256, False, True)]
-    out = {"peak_tflops": peak}
+              ("training layer, batch 256", 256, 256, 256, False, False)]
+    out = {"peak_tflops": peak, "hbm_gbs": hbm}
     err = torch.zeros(4, dtype=torch.int32, device=dev)
     s = torch.cuda.Stream(dev)
     for name, M, N, K, trans_a, trans_b in shapes:
@@ -750,9 +758,12 @@ def gemm_measure(lbm, dev):
         s.synchronize()
         ms_cublas = e0.elapsed_time(e1) / 20
         flops = 2.0 * M * N * K
+        nbytes = 4.0 * (M * K + K * N + M * N)
         out[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
                      "cublas_bf16_tflops": flops / ms_cublas / 1e9,
-                     "frac_of_peak": (flops / ms / 1e9 / peak) if peak else None}
+                     "frac_of_peak": (flops / ms / 1e9 / peak) if peak else None,
+                     "operand_gbs": nbytes / ms / 1e6,
+                     "frac_of_hbm": (nbytes / ms / 1e6 / hbm) if hbm else None}
     out["error_word"] = int(err.max().item())
     return out
 

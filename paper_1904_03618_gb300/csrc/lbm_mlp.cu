@@ -3,7 +3,9 @@
 // The network maps impact parameters to a spreading-factor series: dense
 // layers x -> tanh(x W + b) -> ... -> (. W_out + b_out), trained with mean
 // squared error and Adam.  Every matrix product of the forward and backward
-// passes runs in k_gemm_tc:
+// passes runs on the tensor cores, in k_gemm_ws when its K is at most 256
+// (every forward layer and dZ W^T; a persistent warp-specialised kernel,
+// described above it) and otherwise in k_gemm_tc:
 //   - a CTA owns a 128-row tile of C (all of C's columns, N <= 256);
 //   - the A (128 x 64) and B (N x 64) K-slices are converted to BF16 and
 //     written into shared memory in the canonical K-major layout without
@@ -54,6 +56,7 @@ struct GemmArgs {
   long long sc_m;
   int* err;              // set to 1 if a bounded wait gives up
   int splits;            // K split over gridDim.y CTAs; > 1: C zeroed, partials added
+  int ws_bn;             // k_gemm_ws: columns per CTA
 };
 
 struct GemmSmem {
@@ -364,17 +367,597 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent GEMM for products whose whole B fits in shared
+// memory (K <= 256): every forward layer and every dZ W^T of the network.
+//   - B (bn columns x K, BF16) is staged once per CTA and stays resident;
+//   - a CTA walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+//     of its column block blockIdx.y;
+//   - 8 producer warps load the FP32 A slices (128 x 64), round them to BF16
+//     and write them into a 4-stage ring (full / empty mbarriers);
+//   - one thread issues the tcgen05.mma of each slice into one of two TMEM
+//     accumulators and commits them to the slice's empty barrier, and the
+//     finished tile to its accumulator's full barrier;
+//   - 8 epilogue warps (two per TMEM lane quadrant, alternate 32-column
+//     chunks) drain the other accumulator (tcgen05.ld, bias + tanh or the
+//     tanh derivative, FP32 stores) while the next tile accumulates.
+// Every wait is bounded; a role that gives up raises a CTA-wide flag that
+// ends the other roles' waits, and the MMA thread waits (at the full limit)
+// for its last commit before the accumulators are released.
+// ---------------------------------------------------------------------------
+namespace ws {
+constexpr int kEpiWarps = 8;                 // warps 0-7: TMEM lane quadrant warp % 4
+constexpr int kProdWarps = 8;                // warps 8-15
+constexpr int kProd = 32 * kProdWarps;
+constexpr int kMmaWarp = kEpiWarps + kProdWarps;  // warp 16
+constexpr int kThreads = 32 * (kMmaWarp + 1);     // 544
+constexpr int kStages = 4;
+constexpr int kKMax = 256;
+}  // namespace ws
+
+struct WsSmem {
+  __nv_bfloat16 b[kNMax * ws::kKMax];       // B: K / 64 slices of bn x 64, 128 KB
+  __nv_bfloat16 a[ws::kStages][kM * kKT];   // A ring, 4 x 16 KB
+  float bias[kNMax];
+  float ctile[ws::kEpiWarps][32 * 32];  // per-warp 32 x 32 transpose of C (swizzled)
+  unsigned long long full[ws::kStages], empty[ws::kStages], acc_full[2], acc_empty[2];
+  unsigned tmem_base;
+  int give_up;
+};
+
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
+
+// Bounded wait that also ends when another role of the CTA has given up.
+__device__ __forceinline__ bool ws_wait(unsigned addr, unsigned parity,
+                                        unsigned long long limit, const volatile int* give_up) {
+  if (limit < 1000) return mbar_test(addr, parity);
+  if (mbar_poll(addr, parity)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (!mbar_poll(addr, parity)) {
+    if (*give_up) return false;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+
+// Stages the `rows` x 64 slice X(r, k), r in [r0, r0 + rows), k in [k0, k0 +
+// 64), into the K-major core layout as BF16, zero outside [0, R) x [0, K);
+// rows is a multiple of 8, t in [0, NT).
+//   k contiguous: a task is 8 consecutive k of one row (two 16-byte loads,
+//     one 16-byte store: a full row of one core matrix); the 8 tasks of a
+//     quarter-warp take 8 different rows of one core-matrix group, so the
+//     stores hit 8 different bank groups;
+//   rows contiguous: a task is 4 rows x 8 k (eight 16-byte loads along the
+//     rows, transposed in registers into four 16-byte stores); the lanes of
+//     a warp take consecutive row quads, so each load instruction reads 512
+//     contiguous bytes;
+//   other strides: one element per task.
+template <int NT>
+__device__ __forceinline__ void ws_stage(unsigned char* dst, const float* __restrict__ X,
+                                         long long s_r, long long s_k, int r0, int R, int rows,
+                                         int k0, int K, int t) {
+  const bool aligned = (reinterpret_cast<unsigned long long>(X) & 15u) == 0;
+  if (s_k == 1 && aligned && (s_r & 3) == 0) {
+    const int G = rows * 8;
+    constexpr int kB = 4;
+    for (int base = 0; base < G; base += NT * kB) {
+      float4 v[kB][2];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int g = base + b * NT + t;
+        const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+        const int m = r0 + r, kk = k0 + kq;
+        v[b][0] = v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < G && m < R) {
+          const float* p = X + (long long)m * s_r + kk;
+          if (kk + 7 < K) {
+            v[b][0] = __ldg(reinterpret_cast<const float4*>(p));
+            v[b][1] = __ldg(reinterpret_cast<const float4*>(p) + 1);
+          } else {
+            float e[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) e[j] = kk + j < K ? __ldg(p + j) : 0.f;
+            v[b][0] = make_float4(e[0], e[1], e[2], e[3]);
+            v[b][1] = make_float4(e[4], e[5], e[6], e[7]);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int g = base + b * NT + t;
+        if (g >= G) continue;
+        const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+        uint4 w;
+        w.x = pack_bf16x2(v[b][0].x, v[b][0].y);
+        w.y = pack_bf16x2(v[b][0].z, v[b][0].w);
+        w.z = pack_bf16x2(v[b][1].x, v[b][1].y);
+        w.w = pack_bf16x2(v[b][1].z, v[b][1].w);
+        *reinterpret_cast<uint4*>(dst + core_offset(r, kq)) = w;
+      }
+    }
+  } else if (s_r == 1 && aligned && (s_k & 3) == 0) {
+    const int quads = rows / 4, G = quads * 8;
+    for (int g = t; g < G; g += NT) {
+      const int r4 = (g % quads) * 4, kq = (g / quads) * 8;
+      const int m = r0 + r4;
+      float4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int kk = k0 + kq + j;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kk < K && m < R) {
+          const float* p = X + m + (long long)kk * s_k;
+          if (m + 3 < R) {
+            v[j] = __ldg(reinterpret_cast<const float4*>(p));
+          } else {
+            v[j].x = __ldg(p);
+            if (m + 1 < R) v[j].y = __ldg(p + 1);
+            if (m + 2 < R) v[j].z = __ldg(p + 2);
+          }
+        }
+      }
+      uint4 w;
+      w.x = pack_bf16x2(v[0].x, v[1].x);
+      w.y = pack_bf16x2(v[2].x, v[3].x);
+      w.z = pack_bf16x2(v[4].x, v[5].x);
+      w.w = pack_bf16x2(v[6].x, v[7].x);
+      *reinterpret_cast<uint4*>(dst + core_offset(r4, kq)) = w;
+      w.x = pack_bf16x2(v[0].y, v[1].y);
+      w.y = pack_bf16x2(v[2].y, v[3].y);
+      w.z = pack_bf16x2(v[4].y, v[5].y);
+      w.w = pack_bf16x2(v[6].y, v[7].y);
+      *reinterpret_cast<uint4*>(dst + core_offset(r4 + 1, kq)) = w;
+      w.x = pack_bf16x2(v[0].z, v[1].z);
+      w.y = pack_bf16x2(v[2].z, v[3].z);
+      w.z = pack_bf16x2(v[4].z, v[5].z);
+      w.w = pack_bf16x2(v[6].z, v[7].z);
+      *reinterpret_cast<uint4*>(dst + core_offset(r4 + 2, kq)) = w;
+      w.x = pack_bf16x2(v[0].w, v[1].w);
+      w.y = pack_bf16x2(v[2].w, v[3].w);
+      w.z = pack_bf16x2(v[4].w, v[5].w);
+      w.w = pack_bf16x2(v[6].w, v[7].w);
+      *reinterpret_cast<uint4*>(dst + core_offset(r4 + 3, kq)) = w;
+    }
+  } else {
+    for (int e = t; e < rows * kKT; e += NT) {
+      const int r = e / kKT, k = e % kKT;
+      const int m = r0 + r, kk = k0 + k;
+      const float v = (m < R && kk < K) ? X[(long long)m * s_r + (long long)kk * s_k] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(dst + core_offset(r, k)) = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// B (rows n in [r0, r0 + rows), all nk slices of 64 k) staged once per CTA by
+// all its threads: the same tasks as ws_stage, numbered across the slices
+// so that each thread keeps several tasks' loads in flight (4 tasks of two
+// 16-byte loads, or 2 tasks of eight).
+__device__ __forceinline__ void ws_stage_b(unsigned char* dst, const float* __restrict__ X,
+                                           long long s_r, long long s_k, int r0, int R,
+                                           int rows, int nk, int K, int t) {
+  constexpr int NT = ws::kThreads;
+  const bool aligned = (reinterpret_cast<unsigned long long>(X) & 15u) == 0;
+  const size_t slice_bytes = (size_t)rows * 128;
+  if (s_k == 1 && aligned && (s_r & 3) == 0) {
+    const int Gs = rows * 8, G = nk * Gs;
+    constexpr int kB = 4;
+    for (int base = 0; base < G; base += NT * kB) {
+      float4 v[kB][2];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int gt = base + b * NT + t;
+        const int sl = gt / Gs, g = gt % Gs;
+        const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+        const int m = r0 + r, kk = sl * kKT + kq;
+        v[b][0] = v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gt < G && m < R) {
+          const float* p = X + (long long)m * s_r + kk;
+          if (kk + 7 < K) {
+            v[b][0] = __ldg(reinterpret_cast<const float4*>(p));
+            v[b][1] = __ldg(reinterpret_cast<const float4*>(p) + 1);
+          } else {
+            float e[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) e[j] = kk + j < K ? __ldg(p + j) : 0.f;
+            v[b][0] = make_float4(e[0], e[1], e[2], e[3]);
+            v[b][1] = make_float4(e[4], e[5], e[6], e[7]);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int gt = base + b * NT + t;
+        if (gt >= G) continue;
+        const int sl = gt / Gs, g = gt % Gs;
+        const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+        uint4 w;
+        w.x = pack_bf16x2(v[b][0].x, v[b][0].y);
+        w.y = pack_bf16x2(v[b][0].z, v[b][0].w);
+        w.z = pack_bf16x2(v[b][1].x, v[b][1].y);
+        w.w = pack_bf16x2(v[b][1].z, v[b][1].w);
+        *reinterpret_cast<uint4*>(dst + sl * slice_bytes + core_offset(r, kq)) = w;
+      }
+    }
+  } else if (s_r == 1 && aligned && (s_k & 3) == 0) {
+    const int quads = rows / 4, Gs = quads * 8, G = nk * Gs;
+    constexpr int kB = 2;
+    for (int base = 0; base < G; base += NT * kB) {
+      float4 v[kB][8];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int gt = base + b * NT + t;
+        const int sl = gt / Gs, g = gt % Gs;
+        const int r4 = (g % quads) * 4, kq = (g / quads) * 8;
+        const int m = r0 + r4;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int kk = sl * kKT + kq + j;
+          v[b][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (gt < G && kk < K && m < R) {
+            const float* p = X + m + (long long)kk * s_k;
+            if (m + 3 < R) {
+              v[b][j] = __ldg(reinterpret_cast<const float4*>(p));
+            } else {
+              v[b][j].x = __ldg(p);
+              if (m + 1 < R) v[b][j].y = __ldg(p + 1);
+              if (m + 2 < R) v[b][j].z = __ldg(p + 2);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int gt = base + b * NT + t;
+        if (gt >= G) continue;
+        const int sl = gt / Gs, g = gt % Gs;
+        const int r4 = (g % quads) * 4, kq = (g / quads) * 8;
+        unsigned char* d = dst + sl * slice_bytes;
+        const float4* u = v[b];
+        *reinterpret_cast<uint4*>(d + core_offset(r4, kq)) =
+            make_uint4(pack_bf16x2(u[0].x, u[1].x), pack_bf16x2(u[2].x, u[3].x),
+                       pack_bf16x2(u[4].x, u[5].x), pack_bf16x2(u[6].x, u[7].x));
+        *reinterpret_cast<uint4*>(d + core_offset(r4 + 1, kq)) =
+            make_uint4(pack_bf16x2(u[0].y, u[1].y), pack_bf16x2(u[2].y, u[3].y),
+                       pack_bf16x2(u[4].y, u[5].y), pack_bf16x2(u[6].y, u[7].y));
+        *reinterpret_cast<uint4*>(d + core_offset(r4 + 2, kq)) =
+            make_uint4(pack_bf16x2(u[0].z, u[1].z), pack_bf16x2(u[2].z, u[3].z),
+                       pack_bf16x2(u[4].z, u[5].z), pack_bf16x2(u[6].z, u[7].z));
+        *reinterpret_cast<uint4*>(d + core_offset(r4 + 3, kq)) =
+            make_uint4(pack_bf16x2(u[0].w, u[1].w), pack_bf16x2(u[2].w, u[3].w),
+                       pack_bf16x2(u[4].w, u[5].w), pack_bf16x2(u[6].w, u[7].w));
+      }
+    }
+  } else {
+    for (int sl = 0; sl < nk; ++sl)
+      ws_stage<NT>(dst + sl * slice_bytes, X, s_r, s_k, r0, R, rows, sl * kKT, K, t);
+  }
+}
+
+// The K-contiguous A slice (128 x 64) of the producers split into a load and
+// a store phase, so that a producer thread keeps the loads of two slices in
+// flight: task b of thread t is group g = 256 b + t of ws_stage's mapping.
+struct ASlice {
+  float4 v[4][2];
+};
+__device__ __forceinline__ void ws_load_a(ASlice& x, const float* __restrict__ X, long long s_r,
+                                          int r0, int R, int k0, int K, int t) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int g = b * ws::kProd + t;
+    const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+    const int m = r0 + r, kk = k0 + kq;
+    x.v[b][0] = x.v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < R) {
+      const float* p = X + (long long)m * s_r + kk;
+      if (kk + 7 < K) {
+        x.v[b][0] = __ldg(reinterpret_cast<const float4*>(p));
+        x.v[b][1] = __ldg(reinterpret_cast<const float4*>(p) + 1);
+      } else {
+        float e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) e[j] = kk + j < K ? __ldg(p + j) : 0.f;
+        x.v[b][0] = make_float4(e[0], e[1], e[2], e[3]);
+        x.v[b][1] = make_float4(e[4], e[5], e[6], e[7]);
+      }
+    }
+  }
+}
+__device__ __forceinline__ void ws_store_a(unsigned char* dst, const ASlice& x, int t) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int g = b * ws::kProd + t;
+    const int r = (g >> 6) * 8 + (g & 7), kq = ((g >> 3) & 7) * 8;
+    uint4 w;
+    w.x = pack_bf16x2(x.v[b][0].x, x.v[b][0].y);
+    w.y = pack_bf16x2(x.v[b][0].z, x.v[b][0].w);
+    w.z = pack_bf16x2(x.v[b][1].x, x.v[b][1].y);
+    w.w = pack_bf16x2(x.v[b][1].z, x.v[b][1].w);
+    *reinterpret_cast<uint4*>(dst + core_offset(r, kq)) = w;
+  }
+}
+
+// g.ws_bn: columns per CTA (a multiple of 16, <= 256); K <= 256.
+__global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  WsSmem& sm = *reinterpret_cast<WsSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bn = g.ws_bn;
+  const int n0 = (int)blockIdx.y * bn;
+  const int nk = (g.K + kKT - 1) / kKT;
+  const int mt = (g.M + kM - 1) / kM;
+  unsigned acc_cols = 32;
+  while ((int)acc_cols < bn) acc_cols <<= 1;
+  volatile int* give_up = &sm.give_up;
+
+  if (tid == 0) {
+    for (int s = 0; s < ws::kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.full[s])),
+                   "r"(ws::kProd)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.empty[s]))
+                   : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.acc_full[b]))
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(
+                       smem_u32(&sm.acc_empty[b])),
+                   "r"(32 * ws::kEpiWarps)
+                   : "memory");
+    }
+    sm.give_up = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == ws::kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&sm.tmem_base)),
+                 "r"(2 * acc_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  // B (bn x K) and the bias of this column block, staged once by every thread
+  ws_stage_b(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0, g.N, bn, nk, g.K,
+             tid);
+  for (int n = tid; n < bn; n += ws::kThreads)
+    sm.bias[n] = (g.bias && n0 + n < g.N) ? g.bias[n0 + n] : 0.f;
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const unsigned tmem = sm.tmem_base;
+  const unsigned long long wait_ns = mma_wait_limit();
+
+  if (warp >= ws::kEpiWarps && warp < ws::kMmaWarp) {
+    // producers: A slices into the ring, two at a time where A is
+    // K-contiguous (both slices' loads in flight before either is stored)
+    const int pt = tid - 32 * ws::kEpiWarps;
+    const bool pair = g.sa_k == 1 && (g.sa_m & 3) == 0 &&
+                      (reinterpret_cast<unsigned long long>(g.A) & 15u) == 0;
+    const int my_tiles = (mt - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int total = my_tiles * nk;
+    bool ok = true;
+    for (int q = 0; q < total; q += pair ? 2 : 1) {
+      const int nq = pair && q + 1 < total ? 2 : 1;
+      for (int i = 0; i < nq && ok; ++i) {
+        const int use = (q + i) / ws::kStages;
+        ok = ws_wait(smem_u32(&sm.empty[(q + i) % ws::kStages]), (use & 1) ^ 1, wait_ns,
+                     give_up);
+      }
+      if (!ok) break;
+      const int mi0 = (int)blockIdx.x + (q / nk) * (int)gridDim.x, s0 = q % nk;
+      if (pair) {
+        ASlice x0, x1;
+        ws_load_a(x0, g.A, g.sa_m, mi0 * kM, g.M, s0 * kKT, g.K, pt);
+        if (nq == 2) {
+          const int mi1 = (int)blockIdx.x + ((q + 1) / nk) * (int)gridDim.x, s1 = (q + 1) % nk;
+          ws_load_a(x1, g.A, g.sa_m, mi1 * kM, g.M, s1 * kKT, g.K, pt);
+        }
+        ws_store_a(reinterpret_cast<unsigned char*>(sm.a[q % ws::kStages]), x0, pt);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(smem_u32(&sm.full[q % ws::kStages]));
+        if (nq == 2) {
+          ws_store_a(reinterpret_cast<unsigned char*>(sm.a[(q + 1) % ws::kStages]), x1, pt);
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(smem_u32(&sm.full[(q + 1) % ws::kStages]));
+        }
+      } else {
+        ws_stage<ws::kProd>(reinterpret_cast<unsigned char*>(sm.a[q % ws::kStages]), g.A,
+                            g.sa_m, g.sa_k, mi0 * kM, g.M, kM, s0 * kKT, g.K, pt);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(smem_u32(&sm.full[q % ws::kStages]));
+      }
+    }
+    if (!ok) {
+      *give_up = 1;
+      atomicExch(g.err, 1);
+    }
+  } else if (warp == ws::kMmaWarp) {
+    if (lane == 0) {
+      const unsigned idesc = instr_desc(bn);
+      const unsigned b_base = smem_u32(sm.b);
+      unsigned last_bar = 0, last_par = 0;
+      int q = 0, j = 0;
+      bool ok = true;
+      for (int mi = blockIdx.x; mi < mt && ok; mi += gridDim.x, ++j) {
+        const int acc = j & 1, use_acc = j >> 1;
+        if (!ws_wait(smem_u32(&sm.acc_empty[acc]), (use_acc & 1) ^ 1, wait_ns, give_up)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned d_tmem = tmem + (unsigned)acc * acc_cols;
+        for (int s = 0; s < nk; ++s, ++q) {
+          const int st = q % ws::kStages, use = q / ws::kStages;
+          if (!ws_wait(smem_u32(&sm.full[st]), use & 1, wait_ns, give_up)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const unsigned a_base = smem_u32(sm.a[st]);
+#pragma unroll
+          for (int kk = 0; kk < kKT / 16; ++kk) {
+            const unsigned long long da = smem_desc(a_base + kk * 256, 128, 1024);
+            const unsigned long long db =
+                smem_desc(b_base + (unsigned)(s * bn * 128 + kk * 256), 128, 1024);
+            const unsigned accum = (s > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+                "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                : "memory");
+          }
+          last_bar = smem_u32(&sm.empty[st]);
+          last_par = (unsigned)(use & 1);
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  last_bar)
+              : "memory");
+        }
+        if (!ok) break;
+        last_bar = smem_u32(&sm.acc_full[acc]);
+        last_par = (unsigned)(use_acc & 1);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                last_bar)
+            : "memory");
+      }
+      if (!ok) {
+        *give_up = 1;
+        atomicExch(g.err, 1);
+      }
+      // the accumulators are released only after the last MMA has completed
+      if (last_bar != 0) mbar_wait(last_bar, last_par, kWaitNs);
+    }
+  } else {
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (rows
+    // of the tile), the 32-column chunks w / 4, w / 4 + 2, ...  Lane l
+    // reads row l; the 32 x 32 block goes through the warp's shared-memory
+    // buffer with its 16-byte chunks swizzled (chunk i of row r at slot
+    // i ^ (r & 7)), so the writes (8 lanes: 8 rows, one chunk) and the reads
+    // (8 lanes: one row, 8 chunks) both touch 8 different bank groups; each
+    // lane then owns 4 consecutive columns of rows r = 4 i + l / 8, so a
+    // store instruction writes 4 rows x 128 bytes.
+    const bool vec = (g.sc_m & 3) == 0 && (reinterpret_cast<unsigned long long>(g.C) & 15u) == 0;
+    const bool hvec =
+        g.H && (g.sh_m & 3) == 0 && (reinterpret_cast<unsigned long long>(g.H) & 15u) == 0;
+    float* buf = sm.ctile[warp];
+    const int cq = (lane & 7) * 4;  // this lane's 4 columns in phase 2
+    int j = 0;
+    bool ok = true;
+    for (int mi = blockIdx.x; mi < mt && ok; mi += gridDim.x, ++j) {
+      const int acc = j & 1, use_acc = j >> 1;
+      ok = __all_sync(0xffffffffu,
+                      ws_wait(smem_u32(&sm.acc_full[acc]), use_acc & 1, wait_ns, give_up));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int quad = warp & 3;
+      const int row0 = mi * kM + quad * 32;
+      for (int c0 = (warp >> 2) * 32; c0 < bn; c0 += 64) {
+        unsigned r[32];
+        const unsigned taddr =
+            tmem + ((unsigned)(quad * 32) << 16) + (unsigned)acc * acc_cols + (unsigned)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+            "%26, %27, %28, %29, %30, %31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+              "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          *reinterpret_cast<uint4*>(buf + lane * 32 + 4 * (i ^ (lane & 7))) =
+              make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+        __syncwarp();
+        const int c = c0 + cq;      // column within the block
+        const int n = n0 + c;       // column of C
+        float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!g.H && c < bn) bq = *reinterpret_cast<const float4*>(sm.bias + c);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 4 * i + (lane >> 3);
+          const int m = row0 + rr;
+          float4 v = *reinterpret_cast<const float4*>(buf + rr * 32 + 4 * ((lane & 7) ^ (rr & 7)));
+          if (m >= g.M || c >= bn || n >= g.N) continue;
+          const bool full4 = c + 3 < bn && n + 3 < g.N;
+          if (g.H) {
+            float4 h;
+            const float* hp = g.H + (long long)m * g.sh_m + n;
+            if (hvec && full4) {
+              h = __ldg(reinterpret_cast<const float4*>(hp));
+            } else {
+              h.x = hp[0];
+              h.y = n + 1 < g.N ? hp[1] : 0.f;
+              h.z = n + 2 < g.N ? hp[2] : 0.f;
+              h.w = n + 3 < g.N ? hp[3] : 0.f;
+            }
+            v.x *= 1.f - h.x * h.x;
+            v.y *= 1.f - h.y * h.y;
+            v.z *= 1.f - h.z * h.z;
+            v.w *= 1.f - h.w * h.w;
+          } else {
+            v.x += bq.x;
+            v.y += bq.y;
+            v.z += bq.z;
+            v.w += bq.w;
+            // tanh on the special-function unit: its error (about 2^-11
+            // relative) is below the BF16 rounding of the operands
+            if (g.act == 1) {
+              asm("tanh.approx.f32 %0, %0;" : "+f"(v.x));
+              asm("tanh.approx.f32 %0, %0;" : "+f"(v.y));
+              asm("tanh.approx.f32 %0, %0;" : "+f"(v.z));
+              asm("tanh.approx.f32 %0, %0;" : "+f"(v.w));
+            }
+          }
+          float* cp = g.C + (long long)m * g.sc_m + n;
+          if (vec && full4) {
+            *reinterpret_cast<float4*>(cp) = v;
+          } else {
+            cp[0] = v.x;
+            if (c + 1 < bn && n + 1 < g.N) cp[1] = v.y;
+            if (c + 2 < bn && n + 2 < g.N) cp[2] = v.z;
+            if (c + 3 < bn && n + 3 < g.N) cp[3] = v.w;
+          }
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(smem_u32(&sm.acc_empty[acc]));
+    }
+    if (!ok) {
+      *give_up = 1;
+      if (lane == 0) atomicExch(g.err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == ws::kMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(2 * acc_cols)
+                 : "memory");
+}
+
 // K split for products with few row tiles and many K slices (linear
 // epilogues only: no bias, no activation); C is zeroed and the CTAs add.
+static int sm_count();
 static int choose_splits(const GemmArgs& g) {
-  static int sms_dev[kMaxDevices] = {};
-  int& sms = sms_dev[device_slot()];
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
+  const int sms = sm_count();
   if (g.bias || g.act || g.sc_m != g.N) return 1;  // contiguous C: one memset zeroes it
   const int mt = (g.M + kM - 1) / kM, nk = (g.K + kKT - 1) / kKT;
   int want = (2 * sms) / mt;  // about two CTAs per SM in all
@@ -384,7 +967,49 @@ static int choose_splits(const GemmArgs& g) {
   return (nk + per - 1) / per;  // no split left without slices
 }
 
+static int sm_count() {
+  static int sms_dev[kMaxDevices] = {};
+  int& sms = sms_dev[device_slot()];
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
+// k_gemm_ws launch: the column block is halved (down to 16 columns) while
+// the row tiles alone leave SMs idle; the grid's x extent is at most the SMs
+// per column block (persistent CTAs over the row tiles).
+static cudaError_t launch_gemm_ws(GemmArgs g, cudaStream_t s) {
+  static bool attr_dev[kMaxDevices] = {};
+  bool& attr = attr_dev[device_slot()];
+  const int bytes = (int)sizeof(WsSmem);
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int sms = sm_count();
+  const int n_mma = (g.N + 15) / 16 * 16;
+  const int mt = (g.M + kM - 1) / kM;
+  int nt = 1;
+  while ((long long)mt * nt * 2 <= sms && n_mma / (nt * 2) >= 16) nt *= 2;
+  g.ws_bn = ((n_mma + nt - 1) / nt + 15) / 16 * 16;
+  nt = (g.N + g.ws_bn - 1) / g.ws_bn;
+  int gx = sms / nt;
+  if (gx < 1) gx = 1;
+  if (gx > mt) gx = mt;
+  g.splits = 1;
+  k_gemm_ws<<<dim3((unsigned)gx, (unsigned)nt), ws::kThreads, bytes, s>>>(g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
+  if (g_in.N < 1 || g_in.N > kNMax || g_in.M < 1 || g_in.K < 1) return cudaErrorInvalidValue;
+  if (g_in.K <= ws::kKMax) return launch_gemm_ws(g_in, s);
   GemmArgs g = g_in;
   g.splits = choose_splits(g);
   static bool attr_dev[kMaxDevices] = {};
@@ -399,7 +1024,6 @@ cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (g.N < 1 || g.N > kNMax || g.M < 1 || g.K < 1) return cudaErrorInvalidValue;
   if (g.splits > 1) {
     cudaError_t e = cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.N, s);
     if (e != cudaSuccess) return e;

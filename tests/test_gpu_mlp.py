@@ -43,7 +43,10 @@ def _gemm(A, B, transpose_a=False, transpose_b=False):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 16, 64), (129, 17, 65), (300, 200, 130),
-                                   (257, 256, 1000), (5, 256, 7), (1000, 64, 16)])
+                                   (257, 256, 1000), (5, 256, 7), (1000, 64, 16),
+                                   # several row tiles per persistent CTA: both
+                                   # accumulators and every ring stage reused
+                                   (40000, 256, 256), (40003, 16, 5), (20000, 100, 200)])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_gemm_matches_fp64_product_of_bf16_operands(M, N, K, ta, tb):
     rng = np.random.default_rng(M * 7919 + N * 31 + K)
