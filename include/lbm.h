@@ -338,10 +338,10 @@ lbm_status lbm_batch_set_f(lbm_ctx *ctx, int case_index, const float *f);
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* One time step that allocates no device memory, for callers that cannot
-   call cudaMalloc (code that runs while a stream is being captured into a
-   CUDA graph, services whose device memory is fixed at start-up, embedders
-   that own every device buffer).  The paper has no counterpart: it is a
-   deployment variant of the two-pass step above, with the same result.
+   call cudaMalloc (services whose device memory is fixed at start-up,
+   embedders that own every device buffer).  The paper has no counterpart:
+   it is a deployment variant of the two-pass step above, with the same
+   result.
    f_in: f_i^k(x, t) after streaming, float32 [2][19][N], device memory;
    f_out: receives f_i^k(x, t + 1) in the same layout, device memory, must
    not overlap f_in.  p->storage and p->kernel are ignored (FP32).  Work is
@@ -354,10 +354,9 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
    and a call looks it up again when the CUDA context current on the device
    is not the one of the last lookup (after cudaDeviceReset, or when an
    embedder makes a context of its own current, the library is loaded again
-   at another address); make the first call on a device, and the first
-   after such a change, before any stream capture.  All calls on
-   a device share the array and it keeps the last call's contents (every
-   entry a call reads is written by that call first), so calls that overlap
+   at another address).  All calls on a device share the array and it
+   keeps the last call's contents (every entry a call reads is written by
+   that call first), so calls that overlap
    on the GPU -- e.g. on two streams at once -- race.  Errors (LBM_ERR_ARG,
    LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the calling
    thread; f_in or f_out in host memory, or in device memory of a GPU other

@@ -1,9 +1,8 @@
 // lbm_step_noalloc: one time step that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, memory-budgeted or pre-allocated services that forbid new
-// device allocations after start-up, and embedders that own every device
-// buffer themselves.  For them this entry point runs the two-pass form of
+// Some callers cannot call cudaMalloc: memory-budgeted or pre-allocated
+// services that forbid new device allocations after start-up, and
+// embedders that own every device buffer themselves.  For them this entry point runs the two-pass form of
 // the step (phase-field pass, then collision) on caller-owned input and
 // output population arrays, with its only scratch -- the phase field of
 // rho^N and the correction fluxes, 16 bytes per cell -- in the file-scope

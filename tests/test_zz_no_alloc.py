@@ -1,7 +1,7 @@
 """lbm_step_noalloc: the allocation-free step entry point.
 
-It exists for callers that cannot call cudaMalloc (stream capture in
-progress, device memory fixed at start-up, embedders owning all buffers).
+It exists for callers that cannot call cudaMalloc (device memory fixed at
+start-up, embedders owning all buffers).
 This file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes when run alone in a fresh
 process.  The checks: two calls in a row, each compared with the context
