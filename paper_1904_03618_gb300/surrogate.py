@@ -87,28 +87,45 @@ def sample_impacts(n: int, setup: ImpactSetup, seed: int = 2024, ranges: dict = 
     return out
 
 
-def impact_case(s: dict, setup: ImpactSetup):
-    """lbm_params and initial fields (rho_R, rho_B, u) of one impact."""
+def impact_params(s: dict, setup: ImpactSetup):
+    """lbm_params of one impact."""
     nx, ny, nz = setup.box
     R, U0 = setup.radius, setup.speed
     lam = s["density_ratio"]
     tR, tB, alpha_R = relaxation_times(s, setup)
     sigma = lam * U0 * U0 * 2 * R / s["weber"]
     A = P.A_from_sigma(sigma)
-    prm = lbm.make_params(nx, ny, nz, wall=(0, 0, 1), improved=True, storage=setup.storage,
-                          rho_in_R=lam, rho_in_B=1.0, alpha_R=alpha_R, alpha_B=ALPHA_B,
-                          tau_R=tR, tau_B=tB, A_R=A, A_B=A, beta=setup.beta, delta=0.98,
-                          wetting=True, contact_angle_deg=s["theta_deg"],
-                          ref_R=0.0, ref_B=1.0)
-    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
-                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return lbm.make_params(nx, ny, nz, wall=(0, 0, 1), improved=True, storage=setup.storage,
+                           rho_in_R=lam, rho_in_B=1.0, alpha_R=alpha_R, alpha_B=ALPHA_B,
+                           tau_R=tR, tau_B=tB, A_R=A, A_B=A, beta=setup.beta, delta=0.98,
+                           wetting=True, contact_angle_deg=s["theta_deg"],
+                           ref_R=0.0, ref_B=1.0)
+
+
+def impact_fields(s: dict, setup: ImpactSetup):
+    """Initial fields (rho_R, rho_B, u) of one impact, float32 (z, y, x): a
+    sphere of radius R, `gap` layers above the floor, moving at -U0 in z.
+    The sphere test runs on broadcast coordinates (integers and halves,
+    exact in float32), so a 256 x 256 x 160 box costs its three fields and
+    no coordinate grids."""
+    nx, ny, nz = setup.box
+    R, U0 = setup.radius, setup.speed
+    lam = s["density_ratio"]
     c = ((nx - 1) / 2.0, (ny - 1) / 2.0, setup.gap + R)
+    x = np.arange(nx, dtype=np.float32)[None, None, :]
+    y = np.arange(ny, dtype=np.float32)[None, :, None]
+    z = np.arange(nz, dtype=np.float32)[:, None, None]
     inside = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= R * R
-    rho_R = np.where(inside, lam, 0.0)
-    rho_B = np.where(inside, 0.0, 1.0)
-    u = np.zeros((3, nz, ny, nx))
+    rho_R = np.where(inside, np.float32(lam), np.float32(0.0))
+    rho_B = np.where(inside, np.float32(0.0), np.float32(1.0))
+    u = np.zeros((3, nz, ny, nx), dtype=np.float32)
     u[2][inside] = -U0
-    return prm, (rho_R, rho_B, u)
+    return rho_R, rho_B, u
+
+
+def impact_case(s: dict, setup: ImpactSetup):
+    """lbm_params and initial fields (rho_R, rho_B, u) of one impact."""
+    return impact_params(s, setup), impact_fields(s, setup)
 
 
 @dataclass
@@ -137,12 +154,13 @@ def run_impacts(samples: list, setup: ImpactSetup, chunk: int = 512, device=None
     cells = 0.0
     for c0 in range(0, len(samples), chunk):
         part = samples[c0:c0 + chunk]
-        cases = [impact_case(s, setup) for s in part]
         stream = torch.cuda.Stream(dev)
-        b = lbm.Batch([p for p, _ in cases], device=dev, stream=stream)
+        b = lbm.Batch([impact_params(s, setup) for s in part], device=dev, stream=stream)
         try:
-            for k, (_, f) in enumerate(cases):
-                b.init_fields(k, *f)
+            # fields built one case at a time: a chunk of full-size boxes
+            # would otherwise hold tens of GB of host arrays
+            for k, s in enumerate(part):
+                b.init_fields(k, *impact_fields(s, setup))
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             done = 0
