@@ -176,9 +176,11 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """The step kernels' sources and the launch rules that pick their tile
+    and z chunk (the DRAM bytes per cell depend on both)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("lbm_fused.cuh", "lbm_fused_tma.cuh", "lbm_device.cuh"):
+    for f in ("lbm_fused.cuh", "lbm_fused_tma.cuh", "lbm_device.cuh", "lbm_dispatch.cu"):
         h.update(open(os.path.join(ROOT, "paper_1904_03618_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

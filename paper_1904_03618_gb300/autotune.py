@@ -26,7 +26,10 @@ from . import lbm
 # (tile_y, hold) shapes; z chunks are tried for each
 SINGLE_SHAPES = [(8, 2), (8, 7), (8, 8), (16, 8), (16, 7), (8, 3), (8, 0), (16, 1), (16, 4)]
 BATCH_SHAPES = [(12, 7), (8, 2), (15, 7), (15, 8), (8, 7), (8, 0), (16, 1)]
-ZCHUNKS = [8, 12, 16, 24, 32]
+# z chunks: longer chunks pay fewer halo planes, and beyond about 48 planes
+# the CTAs of neighbouring columns drift apart (their shared halo lines miss
+# in L2); the timing decides
+ZCHUNKS = [8, 12, 16, 24, 32, 48, 64]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1904_03618_gb300",
                              "autotune.json")

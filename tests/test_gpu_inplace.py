@@ -77,6 +77,9 @@ CASES = {
     "original_model": (37, 10, 8, dict(improved=False)),
     "one_cell_y_walls": (5, 1, 3, dict(wall=(0, 1, 0))),
     "two_cells": (2, 3, 2, {}),
+    # several blocks along x (ragged) and more rows and planes
+    "blocks_rows_planes": (170, 37, 19, {}),
+    "blocks_rows_planes_walls": (170, 37, 19, dict(wall=(1, 1, 1))),
 }
 
 
@@ -254,6 +257,8 @@ def test_rayleigh_taylor_512x512x2048_in_place():
     for z in (0, 1, nz - 2, nz - 1):                   # wall layers
         cells += [(int(rng.integers(nx)), int(rng.integers(ny)), z) for _ in range(3)]
     cells += [(0, 0, nz // 2), (nx - 1, ny - 1, nz // 2), (0, ny - 1, 2 * nx)]  # seams
+    # block boundaries along x (128-thread blocks)
+    cells += [(127, 15, 127), (128, 16, 128), (255, 47, 255), (256, 48, 256)]
     wall = pd["wall"]
     dims = (nx, ny, nz)
     for start in (0, 1):                               # step 1 from even, step 2 from odd
