@@ -630,11 +630,13 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
 
 extern "C" lbm_status lbm_create(const lbm_params* p, void* cuda_stream,
                                  lbm_ctx** out) {
+  lbm::NvtxRange nvtx_range_("lbm_create");
   return create_ctx(p, 1, cuda_stream, out);
 }
 
 extern "C" lbm_status lbm_create_batch(const lbm_params* cases, int ncases,
                                        void* cuda_stream, lbm_ctx** out) {
+  lbm::NvtxRange nvtx_range_("lbm_create_batch");
   return create_ctx(cases, ncases, cuda_stream, out);
 }
 
@@ -741,6 +743,7 @@ static lbm_status settle_diag(lbm_ctx* c, int b) {
 
 extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_R,
                                             const float* rho_B, const float* u) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_init_fields");
   if (!c) return LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
@@ -773,6 +776,7 @@ extern "C" lbm_status lbm_batch_init_fields(lbm_ctx* c, int k, const float* rho_
 extern "C" lbm_status lbm_init_fields(lbm_ctx* c, const float* rho_R,
                                       const float* rho_B, const float* u,
                                       const unsigned char* solid) {
+  lbm::NvtxRange nvtx_range_("lbm_init_fields");
   if (!c) return LBM_ERR_ARG;
   if (solid) return fail(c, LBM_ERR_ARG, "solid masks are not supported; use wall[]");
   return lbm_batch_init_fields(c, 0, rho_R, rho_B, u);
@@ -855,6 +859,7 @@ static lbm_status ensure_graph(lbm_ctx* c) {
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
+  lbm::NvtxRange nvtx_range_("lbm_step");
   if (!c) return LBM_ERR_ARG;
   if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
   for (int k = 0; k < c->ncases; ++k)
@@ -904,6 +909,7 @@ static bool case_ready(lbm_ctx* c, int k) { return c->cases[k].initialized != 0;
 
 extern "C" lbm_status lbm_batch_moments(lbm_ctx* c, int k, float* rho_R,
                                         float* rho_B, float* u) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_moments");
   if (!c) return LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
@@ -941,6 +947,7 @@ extern "C" lbm_status lbm_batch_moments(lbm_ctx* c, int k, float* rho_R,
 
 extern "C" lbm_status lbm_moments(lbm_ctx* c, float* rho_R, float* rho_B,
                                   float* u) {
+  lbm::NvtxRange nvtx_range_("lbm_moments");
   return lbm_batch_moments(c, 0, rho_R, rho_B, u);
 }
 
@@ -954,6 +961,7 @@ static lbm_status enqueue_diag(lbm_ctx* c, int k, cudaStream_t s) {
 }
 
 extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_diagnostics");
   if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
@@ -978,6 +986,7 @@ extern "C" lbm_status lbm_batch_diagnostics(lbm_ctx* c, int k, double out[16]) {
 }
 
 extern "C" lbm_status lbm_step_diagnostics_async(lbm_ctx* c, int n, double* out) {
+  lbm::NvtxRange nvtx_range_("lbm_step_diagnostics_async");
   if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
   if (!c->dstream) {
     LBM_CUDA(c, cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking),
@@ -1005,6 +1014,7 @@ extern "C" lbm_status lbm_step_diagnostics_async(lbm_ctx* c, int n, double* out)
 }
 
 extern "C" lbm_status lbm_sync(lbm_ctx* c) {
+  lbm::NvtxRange nvtx_range_("lbm_sync");
   if (!c) return LBM_ERR_ARG;
   if (c->dstream) LBM_CUDA(c, cudaStreamSynchronize(c->dstream), "stream sync");
   for (int q = 0; q < 2; ++q) c->diag_pend[q] = false;
@@ -1019,6 +1029,7 @@ extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, double out[16]) {
 
 extern "C" lbm_status lbm_batch_footprint(lbm_ctx* c, int axis, int index,
                                           long long* counts) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_footprint");
   if (!c || !counts) return c ? fail(c, LBM_ERR_ARG, "counts is NULL") : LBM_ERR_ARG;
   if (axis < 0 || axis > 2) return fail(c, LBM_ERR_ARG, "axis must be 0, 1 or 2");
   for (int k = 0; k < c->ncases; ++k) {
@@ -1045,6 +1056,7 @@ extern "C" lbm_status lbm_batch_footprint(lbm_ctx* c, int axis, int index,
 }
 
 extern "C" lbm_status lbm_batch_get_f(lbm_ctx* c, int k, float* f) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_get_f");
   if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
@@ -1074,6 +1086,7 @@ extern "C" lbm_status lbm_batch_get_f(lbm_ctx* c, int k, float* f) {
 extern "C" lbm_status lbm_get_f(lbm_ctx* c, float* f) { return lbm_batch_get_f(c, 0, f); }
 
 extern "C" lbm_status lbm_batch_set_f(lbm_ctx* c, int k, const float* f) {
+  lbm::NvtxRange nvtx_range_("lbm_batch_set_f");
   if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
   lbm_status st = check_case(c, k);
   if (st != LBM_OK) return st;
@@ -1107,6 +1120,7 @@ extern "C" size_t lbm_population_bytes(const lbm_ctx* c) {
 }
 
 extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
+  lbm::NvtxRange nvtx_range_("lbm_get_populations");
   if (!c || !dst) return c ? fail(c, LBM_ERR_ARG, "dst is NULL") : LBM_ERR_ARG;
   for (int k = 0; k < c->ncases; ++k)
     if (!case_ready(c, k)) return fail(c, LBM_ERR_STATE, "lbm_get_populations before init");
@@ -1119,6 +1133,7 @@ extern "C" lbm_status lbm_get_populations(lbm_ctx* c, void* dst) {
 }
 
 extern "C" lbm_status lbm_set_populations(lbm_ctx* c, const void* src) {
+  lbm::NvtxRange nvtx_range_("lbm_set_populations");
   if (!c || !src) return c ? fail(c, LBM_ERR_ARG, "src is NULL") : LBM_ERR_ARG;
   {
     lbm_status st = settle_diag(c, -1);
@@ -1177,10 +1192,12 @@ static lbm_status plane_copy(lbm_ctx* c, int z0, int n, void* host_side, bool to
 }
 
 extern "C" lbm_status lbm_get_planes(lbm_ctx* c, int z0, int n, void* dst) {
+  lbm::NvtxRange nvtx_range_("lbm_get_planes");
   return plane_copy(c, z0, n, dst, true);
 }
 
 extern "C" lbm_status lbm_set_planes(lbm_ctx* c, int z0, int n, const void* src) {
+  lbm::NvtxRange nvtx_range_("lbm_set_planes");
   return plane_copy(c, z0, n, const_cast<void*>(src), false);
 }
 

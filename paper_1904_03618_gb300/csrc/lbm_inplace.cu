@@ -251,6 +251,7 @@ StepArgs fp32_args(const lbm_params* p, long long N) {
 extern "C" lbm_status lbm_inplace_init(const lbm_params* p, const float* rho_R,
                                        const float* rho_B, const float* u, float* f,
                                        void* cuda_stream) {
+  lbm::NvtxRange nvtx_range_("lbm_inplace_init");
   using namespace lbm;
   clear_thread_error();
   lbm_status st =
@@ -277,6 +278,7 @@ extern "C" lbm_status lbm_inplace_init(const lbm_params* p, const float* rho_R,
 
 extern "C" lbm_status lbm_step_inplace(const lbm_params* p, float* f, int parity, int nsteps,
                                        void* scratch, void* cuda_stream) {
+  lbm::NvtxRange nvtx_range_("lbm_step_inplace");
   using namespace lbm;
   clear_thread_error();
   lbm_status st =
@@ -324,6 +326,7 @@ extern "C" lbm_status lbm_step_inplace(const lbm_params* p, float* f, int parity
 extern "C" lbm_status lbm_inplace_read(const lbm_params* p, const float* f, int parity,
                                        float* f_out, float* rho_R, float* rho_B, float* u,
                                        void* cuda_stream) {
+  lbm::NvtxRange nvtx_range_("lbm_inplace_read");
   using namespace lbm;
   clear_thread_error();
   lbm_status st =

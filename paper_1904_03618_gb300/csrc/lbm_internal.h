@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
@@ -20,6 +21,16 @@ inline int device_slot() {
   return d;
 }
 
+
+// NVTX range around a host entry point: the calls show up by name on the
+// Nsight Systems timeline; without an attached tool a push / pop is a
+// check of one pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kDiagSlots = 13;  // accumulated slots of lbm_diagnostics
 

@@ -1292,6 +1292,7 @@ static lbm_status check_err(lbm_mlp* m) {
 }
 
 extern "C" lbm_status lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y) {
+  lbm::NvtxRange nvtx_range_("lbm_mlp_forward");
   if (!m || !x || !y) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
   lbm_status st = check_batch(m, batch);
   if (st != LBM_OK) return st;
@@ -1363,6 +1364,7 @@ static lbm_status mlp_backward(lbm_mlp* m, const float* x, const float* t, int b
 
 extern "C" lbm_status lbm_mlp_loss_grad(lbm_mlp* m, const float* x, const float* t, int batch,
                                         float* loss, float* grad) {
+  lbm::NvtxRange nvtx_range_("lbm_mlp_loss_grad");
   if (!m || !x || !t) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
   lbm_status st = check_batch(m, batch);
   if (st != LBM_OK) return st;
@@ -1379,6 +1381,7 @@ extern "C" lbm_status lbm_mlp_loss_grad(lbm_mlp* m, const float* x, const float*
 
 extern "C" lbm_status lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* t, int batch,
                                          float lr, float* loss) {
+  lbm::NvtxRange nvtx_range_("lbm_mlp_train_step");
   if (!m || !x || !t) return m ? mlp_fail(m, LBM_ERR_ARG, "NULL pointer") : LBM_ERR_ARG;
   lbm_status st = check_batch(m, batch);
   if (st != LBM_OK) return st;
@@ -1402,6 +1405,7 @@ extern "C" lbm_status lbm_gemm_bf16(const float* A, long long sa_m, long long sa
                                     const float* B, long long sb_k, long long sb_n, float* C,
                                     long long sc_m, int M, int N, int K, int* err,
                                     void* cuda_stream) {
+  lbm::NvtxRange nvtx_range_("lbm_gemm_bf16");
   if (!A || !B || !C || !err || M < 1 || N < 1 || N > kNMax || K < 1)
     return LBM_ERR_ARG;
   GemmArgs g;
