@@ -496,6 +496,17 @@ lbm_status lbm_test_set_wait_limits(unsigned long long stage_ns,
 void lbm_test_fail_allocation(int n);
 long long lbm_test_live_allocations(void);
 
+/* Testing hook of the checked build (the library compiled with
+   -DLBM_CHECKED, a stand-in for a memory checker, which is not run on the
+   GPUs this library is tested on); the paper has no counterpart.  In that
+   build the step kernels test every computed population index (pulls,
+   stores, the seam and plate writes) against its buffer and the TMA copies'
+   x coordinates against the 16-byte rule before the access, count a
+   failure and skip the access.  *checked: 1 in the checked build, 0
+   otherwise; *out_of_range: the failures counted since ctx was created (0
+   in a normal build).  Synchronises ctx's stream. */
+lbm_status lbm_test_index_checks(lbm_ctx *ctx, int *checked, unsigned *out_of_range);
+
 /* Text of the last error on ctx (never NULL; "" after success).  With
    ctx == NULL, the last error of a failed lbm_create in this thread. */
 const char *lbm_last_error(const lbm_ctx *ctx);

@@ -54,6 +54,7 @@ struct lbm_ctx {
   lbm::BatchCase* d_cases;  // device case table of the batched kernel
   unsigned long long* foot; // per-case plane counts (lbm_batch_footprint)
   int* d_flags;             // device error word of the kernels' bounded waits
+  unsigned* d_oob;          // checked builds: out-of-range index count
   bool tma_ok[3];           // tensor maps built, per tile kind (single lattice)
   CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
   CUtensorMap smaps[2][2][6];  // [tile: 0 = 34 x 15, 1 = 34 x 12][buffer][map]: SEAM forms
@@ -137,6 +138,21 @@ void host_free(void* p) {
 
 extern "C" void lbm_test_fail_allocation(int n) { g_fail_countdown.store(n > 0 ? n : 0); }
 extern "C" long long lbm_test_live_allocations(void) { return g_live_allocs.load(); }
+
+extern "C" lbm_status lbm_test_index_checks(lbm_ctx* c, int* checked, unsigned* out_of_range) {
+  if (!c || !checked || !out_of_range) return c ? fail(c, LBM_ERR_ARG, "NULL output") : LBM_ERR_ARG;
+#ifdef LBM_CHECKED
+  *checked = 1;
+  LBM_CUDA(c, cudaMemcpyAsync(out_of_range, c->d_oob, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              c->stream),
+           "cudaMemcpyAsync");
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+#else
+  *checked = 0;
+  *out_of_range = 0;
+#endif
+  return LBM_OK;
+}
 
 extern "C" lbm_status lbm_test_set_wait_limits(unsigned long long stage_ns,
                                                unsigned long long mma_ns) {
@@ -368,6 +384,7 @@ static void release(lbm_ctx* c) {
   lbm::dev_free(c->d_cases);
   lbm::dev_free(c->foot);
   lbm::dev_free(c->d_flags);
+  lbm::dev_free(c->d_oob);
   for (int b = 0; b < 2; ++b)
     for (int w = 0; w < 3; ++w) lbm::dev_free(c->d_bmaps[b][w]);
   for (int b = 0; b < 2; ++b) lbm::dev_free(c->d_seam_bmaps[b]);
@@ -507,6 +524,14 @@ static lbm_status create_ctx(const lbm_params* ps, int ncases, void* cuda_stream
         cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess)
       st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the error word failed");
   }
+#ifdef LBM_CHECKED
+  if (st == LBM_OK) {
+    if (lbm::dev_alloc((void**)&c->d_oob, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->d_oob, 0, sizeof(unsigned)) != cudaSuccess)
+      st = fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the index-check count failed");
+    for (int k = 0; k < ncases && st == LBM_OK; ++k) c->cases[k].args.oob = c->d_oob;
+  }
+#endif
   if (st == LBM_OK && ncases == 1 && c->kernel == LBM_KERNEL_FUSED &&
       lbm::tma_eligible(c->cases[0].args, c->storage)) {
     for (int w = 0; w < 3; ++w) {

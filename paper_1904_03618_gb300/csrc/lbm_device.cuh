@@ -52,7 +52,27 @@ struct StepArgs {
   float gx, gy, gz;             // gravity
   // deviation storage offsets ref_k * phi_i^k for (rest, axis, diagonal)
   float offR0, offR1, offR2, offB0, offB1, offB2;
+  // checked builds (LBM_CHECKED): count of out-of-range indices, else null
+  unsigned* oob;
 };
+
+// Checked builds (compiled with -DLBM_CHECKED, the stand-in for a memory
+// checker): the step kernels test every computed population index against
+// its buffer before the access, count an index out of range in *a.oob and
+// skip that access.  Normal builds compile the test away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool index_ok(const StepArgs& a, unsigned long long i,
+                                         unsigned long long n) {
+  if (i < n) return true;
+  if (a.oob) atomicAdd(a.oob, 1u);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool index_ok(const StepArgs&, unsigned long long,
+                                                   unsigned long long) {
+  return true;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // D3Q19 lattice of Eq. 5, as compile-time functions of the direction index.
@@ -213,7 +233,10 @@ struct PullPairs {
                                              const StepArgs& a, const ColOff& c,
                                              const PlaneOff& p, float* fR,
                                              float* fB) {
-    float2 v = Store<T>::to_float2(__ldg(src + pull_index<true, I>((unsigned)a.plane, c, p)));
+    const unsigned q = pull_index<true, I>((unsigned)a.plane, c, p);
+    float2 v = make_float2(0.f, 0.f);
+    if (index_ok(a, q, 19ull * (unsigned long long)a.plane))
+      v = Store<T>::to_float2(__ldg(src + q));
     if (Store<T>::kDeviation) {
       v.x += dev_offset<I>(a, 0);
       v.y += dev_offset<I>(a, 1);
@@ -242,6 +265,7 @@ template <typename T>
 __device__ __forceinline__ void store_cell(T* __restrict__ dst,
                                            const StepArgs& a, unsigned c,
                                            const float* fR, const float* fB) {
+  if (!index_ok(a, c, (unsigned long long)a.plane)) return;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     float r = fR[i], b = fB[i];

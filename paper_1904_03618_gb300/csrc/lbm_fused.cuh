@@ -54,7 +54,9 @@ struct PullReduce {
                                              unsigned plane, const StepArgs& a,
                                              const ColOff& c, const PlaneOff& p,
                                              float* f, float2& rho) {
-    float2 v = Store<T>::to_float2(__ldg(src + pull_index<WALLS, I>(plane, c, p)));
+    const unsigned q = pull_index<WALLS, I>(plane, c, p);
+    float2 v = make_float2(0.f, 0.f);
+    if (index_ok(a, q, 19ull * plane)) v = Store<T>::to_float2(__ldg(src + q));
     add_offsets<T, I>(a, v);
     rho = __fadd2_rn(rho, v);
     f[I] = v.x + v.y;
@@ -101,10 +103,11 @@ struct PullAsync {
                                              unsigned plane, const ColOff& c,
                                              const PlaneOff& p,
                                              typename Store<T>::Pair* raw,
-                                             int stride) {
-    cp_async<sizeof(typename Store<T>::Pair)>(raw + I * stride,
-                                               src + pull_index<WALLS, I>(plane, c, p));
-    PullAsync<T, WALLS, I + 1>::run(src, plane, c, p, raw, stride);
+                                             int stride, const StepArgs& a) {
+    const unsigned q = pull_index<WALLS, I>(plane, c, p);
+    if (index_ok(a, q, 19ull * plane))
+      cp_async<sizeof(typename Store<T>::Pair)>(raw + I * stride, src + q);
+    PullAsync<T, WALLS, I + 1>::run(src, plane, c, p, raw, stride, a);
   }
 };
 template <typename T, bool WALLS>
@@ -112,7 +115,8 @@ struct PullAsync<T, WALLS, 19> {
   __device__ __forceinline__ static void run(const typename Store<T>::Pair*,
                                              unsigned, const ColOff&,
                                              const PlaneOff&,
-                                             typename Store<T>::Pair*, int) {}
+                                             typename Store<T>::Pair*, int,
+                                             const StepArgs&) {}
 };
 
 // Stores the recoloured populations of Eq. 10-11 of one cell, one pair of
@@ -148,6 +152,7 @@ __device__ __forceinline__ void store_recoloured(T* dst, unsigned plane,
                                                  const StepArgs& a, unsigned c,
                                                  const Recolour& rc,
                                                  const float* fs) {
+  if (!index_ok(a, c, plane)) return;
   float r0 = rc.wr * fs[0], b0 = rc.wb * fs[0];
   if (Store<T>::kDeviation) {
     r0 -= dev_offset<0>(a, 0);
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(kTileW* kAsyncBY, 2)
     const bool ok = g.plane_ok(a, zl);
     if (ok)
       PullAsync<T, WALLS, 0>::run(srcp, plane, g.co, g.plane(a, wrap1(zl, a.nz)), raw,
-                                  kRawStride);
+                                  kRawStride, a);
     cp_async_commit();
     return ok;
   };

@@ -634,6 +634,17 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
   auto issue_one = [&](int k) {  // one thread
     const int zl = zb - 1 + k;
     const unsigned m = mb(k);
+#ifdef LBM_CHECKED
+    // the copies' x coordinates (x0 and x0 - 2 for 8-byte pairs, rounded
+    // down to 4 pairs for 4-byte pairs; the seam strips' from nx) must start
+    // on 16 bytes: a misaligned one is counted and its plane not copied
+    // (the stage wait then gives up and reports)
+    if (tma_pair_bytes<T>() == 8 ? ((x0 & 1) != 0 || (SEAM && (a.nx & 1) != 0))
+                                 : (SEAM && (a.nx & 3) != 0)) {
+      index_ok(a, 1, 0);
+      return;
+    }
+#endif
     if (staged(zl)) {
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m),
                    "r"(TX)

@@ -41,7 +41,8 @@ struct ScatterAll {
       r -= dev_offset<I>(a, 0);
       b -= dev_offset<I>(a, 1);
     }
-    Store<T>::store2(dst + 2 * (size_t)pull_index<true, I>((unsigned)a.plane, co, po), r, b);
+    const unsigned q = pull_index<true, I>((unsigned)a.plane, co, po);
+    if (index_ok(a, q, 19ull * (unsigned long long)a.plane)) Store<T>::store2(dst + 2 * (size_t)q, r, b);
     ScatterAll<T, I + 1>::run(dst, a, co, po, fR, fB);
   }
 };
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(kAuxBlock)
     }
   }
   // write the entering populations (both colours) to their pull slots
+  if (!index_ok(a, c, (unsigned long long)a.plane)) return;
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
     if (en(i) != 1) continue;

@@ -1,8 +1,11 @@
 """Python binding of the C ABI in ``include/lbm.h`` (ctypes).
 
 Argument marshalling only: every step of the computation runs in the CUDA
-library ``_lib/liblbm.so`` built by ``__graft_entry__.build()``.  If that
-library is missing this module raises on import -- there is no CPU fallback.
+library ``_lib/liblbm.so`` built by ``__graft_entry__.build()`` (or the
+build named by the environment variable ``LBM_LIBRARY``, e.g. the
+index-checked ``_lib/liblbm_checked.so`` of
+``__graft_entry__.build_checked()``).  If that library is missing this
+module raises on import -- there is no CPU fallback.
 
 Functions carry the C names (``lbm_create``, ``lbm_init_fields``,
 ``lbm_step``, ``lbm_moments``, ``lbm_diagnostics``, ``lbm_get_f``,
@@ -22,7 +25,7 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "_lib", "liblbm.so")
 
 if not os.path.exists(LIB_PATH):
     raise RuntimeError(
