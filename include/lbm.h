@@ -200,6 +200,26 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, double out[16]);
    Errors: LBM_ERR_ARG (out NULL, n < 0), LBM_ERR_STATE, LBM_ERR_CUDA. */
 lbm_status lbm_step_diagnostics_async(lbm_ctx *ctx, int n, double *out);
 
+/* Monitored stepping with the diagnostics computed inside the step: n >= 0
+   steps (as lbm_step), where step k (k = 0 .. n-1) also reports the
+   diagnostics of the state it reads -- the state after k steps of this
+   call -- into out[16 k .. 16 k + 15] (the slots of lbm_diagnostics; slot
+   [12] = the steps completed before that state), out being pinned host or
+   device memory (pageable host memory makes the copies synchronous).  For
+   a single lattice on the seam forms' default tiles (FP32 periodic in x
+   and y, FP16 / BF16 periodic in x and y with nx a multiple of 4) the step
+   kernel sums them from the moments it already holds, so monitoring adds
+   no pass over the populations: per warp in FP32 (the masses and momentum
+   to about 1e-7 relative, not the compensated sums of lbm_diagnostics),
+   across warps and CTAs in FP64, by atomics (the last bits can vary from
+   run to run); the counts, max |u| and centroid as lbm_diagnostics.  Other
+   contexts run the lbm_diagnostics pass before each step.  Queued on the
+   context stream without a host wait: out is valid after lbm_sync.  The
+   state after the last step is not reported (lbm_diagnostics gives it).
+   Errors: LBM_ERR_ARG (out NULL, n < 0, a batch), LBM_ERR_STATE,
+   LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_step_monitored(lbm_ctx *ctx, int n, double *out);
+
 /* Waits until all work queued by the context (its stream and the stream of
    the asynchronous diagnostics) has finished. */
 lbm_status lbm_sync(lbm_ctx *ctx);

@@ -55,6 +55,8 @@ struct lbm_ctx {
   unsigned long long* foot; // per-case plane counts (lbm_batch_footprint)
   int* d_flags;             // device error word of the kernels' bounded waits
   unsigned* d_oob;          // checked builds: out-of-range index count
+  lbm::MonAcc* d_mon;       // monitored steps: the step's diagnostics record
+  double* d_mon_out;        // its 16 slots
   bool tma_ok[3];           // tensor maps built, per tile kind (single lattice)
   CUtensorMap tmaps[2][3][2];  // [buffer][tile kind][map]: TMA maps
   CUtensorMap smaps[2][2][6];  // [tile: 0 = 34 x 15, 1 = 34 x 12][buffer][map]: SEAM forms
@@ -385,6 +387,8 @@ static void release(lbm_ctx* c) {
   lbm::dev_free(c->foot);
   lbm::dev_free(c->d_flags);
   lbm::dev_free(c->d_oob);
+  lbm::dev_free(c->d_mon);
+  lbm::dev_free(c->d_mon_out);
   for (int b = 0; b < 2; ++b)
     for (int w = 0; w < 3; ++w) lbm::dev_free(c->d_bmaps[b][w]);
   for (int b = 0; b < 2; ++b) lbm::dev_free(c->d_seam_bmaps[b]);
@@ -807,7 +811,9 @@ extern "C" lbm_status lbm_init_fields(lbm_ctx* c, const float* rho_R,
   return lbm_batch_init_fields(c, 0, rho_R, rho_B, u);
 }
 
-static lbm_status launch_step(lbm_ctx* c, int from) {
+// mon (monitored steps, the seam forms' default tiles only): the step also
+// sums the diagnostics of the state it reads into *mon.
+static lbm_status launch_step(lbm_ctx* c, int from, lbm::MonAcc* mon = nullptr) {
   const void* src = c->pop[from];
   void* dst = c->pop[from ^ 1];
   cudaError_t e;
@@ -835,12 +841,12 @@ static lbm_status launch_step(lbm_ctx* c, int from) {
            (c->fused.tile_y == 15 || c->fused.tile_y == 12))
     e = lbm::launch_fused_tma_seam16(c->storage, src, dst, c->cases[0].args, c->fused.tile_y,
                                      c->smaps16[c->fused.tile_y == 15 ? 0 : 1][from],
-                                     c->fused.zchunk, c->d_flags, c->stream);
+                                     c->fused.zchunk, c->d_flags, c->stream, mon);
   else if (c->seam_ok && ((c->fused.hold == 8 && c->fused.tile_y == 15) ||
                            (c->fused.hold == 7 && c->fused.tile_y == 12)))
     e = lbm::launch_fused_tma_seam(src, dst, c->cases[0].args, c->fused.tile_y,
                                    c->smaps[c->fused.tile_y == 15 ? 0 : 1][from],
-                                   c->fused.zchunk, c->d_flags, c->stream);
+                                   c->fused.zchunk, c->d_flags, c->stream, mon);
   else if (c->fused.hold == 7 || c->fused.hold == 8) {
     const int w = lbm::tma_kind(c->fused.tile_y);
     e = w >= 0 && c->tma_ok[w]
@@ -1034,6 +1040,60 @@ extern "C" lbm_status lbm_step_diagnostics_async(lbm_ctx* c, int n, double* out)
            "cudaMemcpyAsync of the diagnostics");
   LBM_CUDA(c, cudaEventRecord(c->diag_ev[c->cur], c->dstream), "cudaEventRecord");
   c->diag_pend[c->cur] = true;
+  c->err[0] = 0;
+  return LBM_OK;
+}
+
+// The monitored form exists for the seam kernels' default tiles, with z
+// chunks of at most 255 planes (a thread's counts are packed in bytes).
+static bool monitor_fused(const lbm_ctx* c) {
+  const int zc = c->fused.zchunk > 0 ? c->fused.zchunk : c->cases[0].p.nz;
+  return c->ncases == 1 && c->kernel == LBM_KERNEL_FUSED && c->fused.hold == 7 && zc <= 255 &&
+         ((c->seam_ok && c->storage == LBM_F32 && c->fused.tile_y == 12) ||
+          (c->seam16_ok && c->storage != LBM_F32 && c->fused.tile_y == 15));
+}
+
+extern "C" lbm_status lbm_step_monitored(lbm_ctx* c, int n, double* out) {
+  lbm::NvtxRange nvtx_range_("lbm_step_monitored");
+  if (!c || !out) return c ? fail(c, LBM_ERR_ARG, "out is NULL") : LBM_ERR_ARG;
+  if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
+  if (c->ncases != 1)
+    return fail(c, LBM_ERR_ARG, "lbm_step_monitored: single-lattice contexts only");
+  if (!c->cases[0].initialized) return fail(c, LBM_ERR_STATE, "lbm_step_monitored before init");
+  lbm_status st = settle_diag(c, -1);
+  if (st != LBM_OK) return st;
+  const bool fused = monitor_fused(c);
+  if (fused && !c->d_mon) {
+    if (lbm::dev_alloc((void**)&c->d_mon, sizeof(lbm::MonAcc)) != cudaSuccess ||
+        lbm::dev_alloc((void**)&c->d_mon_out, sizeof(double) * 16) != cudaSuccess) {
+      cudaGetLastError();
+      lbm::dev_free(c->d_mon);
+      c->d_mon = nullptr;
+      return fail(c, LBM_ERR_OOM, "cudaMalloc of the monitor record failed");
+    }
+    LBM_CUDA(c, cudaMemsetAsync(c->d_mon, 0, sizeof(lbm::MonAcc), c->stream), "cudaMemsetAsync");
+  }
+  for (int k = 0; k < n; ++k) {
+    double* o = out + 16 * (size_t)k;
+    if (fused) {
+      if ((st = launch_step(c, c->cur, c->d_mon)) != LBM_OK) return st;
+      LBM_CUDA(c, lbm::launch_monitor_out(c->d_mon, c->d_flags, (double)c->steps, c->d_mon_out,
+                                          c->stream),
+               "monitor kernel");
+      LBM_CUDA(c, cudaMemcpyAsync(o, c->d_mon_out, sizeof(double) * 16, cudaMemcpyDefault,
+                                  c->stream),
+               "cudaMemcpyAsync of the monitor");
+    } else {
+      // other kernel forms: the diagnostics pass over the state, then the step
+      if ((st = enqueue_diag(c, 0, c->stream)) != LBM_OK) return st;
+      LBM_CUDA(c, cudaMemcpyAsync(o, c->diag_out, sizeof(double) * 16, cudaMemcpyDefault,
+                                  c->stream),
+               "cudaMemcpyAsync of the diagnostics");
+      if ((st = launch_step(c, c->cur)) != LBM_OK) return st;
+    }
+    c->cur ^= 1;
+    c->steps += 1;
+  }
   c->err[0] = 0;
   return LBM_OK;
 }

@@ -273,12 +273,13 @@ cudaError_t tma_build_seam16_maps(int storage, const void* base, const StepArgs&
 
 cudaError_t launch_fused_tma_seam16(int storage, const void* src, void* dst, const StepArgs& a,
                                     int tile_y, const CUtensorMap* maps4, int zchunk, int* err,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, MonAcc* mon) {
   if (storage == 1)
-    return launch_fused_tma_seam16_storage<__half>(src, dst, a, tile_y, maps4, zchunk, err, s);
+    return launch_fused_tma_seam16_storage<__half>(src, dst, a, tile_y, maps4, zchunk, err, s,
+                                                   mon);
   if (storage == 2)
     return launch_fused_tma_seam16_storage<__nv_bfloat16>(src, dst, a, tile_y, maps4, zchunk,
-                                                          err, s);
+                                                          err, s, mon);
   return cudaErrorInvalidValue;
 }
 

@@ -540,6 +540,110 @@ __host__ __device__ constexpr int tma_issuer() {
   return (TW - 2) * (BY - 2);
 }
 
+// Monitored steps: per plane, every warp folds its lanes' diagnostics of
+// the state the step reads (lanes without an interior cell add zeros) with
+// FP32 shuffles, and lane 0 adds the folds into the warp's own slot of the
+// CTA's record (FP32, the masses with Kahan compensation: no atomics, no FP64 -- the
+// FP64 pipe is narrow on this GPU and a per-plane FP64 fold cost the step
+// more than its collision; per-thread sums held in registers over the
+// chunk cost it a quarter, through register pressure).  After the chunk
+// the kernel adds the slots in FP64 into the step's global record.  The
+// momentum is the raw sum_i e_i f_i (the velocity without its half-force
+// shift); a NaN or an infinity in any population reaches rho or u, so
+// their finiteness marks the cell; rho^N is the cell's phase-field entry
+// of the window.
+constexpr int kMonWarps = 16;  // warps of the largest monitored CTA (34 x 15)
+struct MonSlot {
+  float s[8], c[8];  // sums and their Kahan compensations (MonAcc::d order)
+  unsigned n[4];
+  unsigned u2bits;
+};
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+// Every lane of the warp calls it once per plane.
+__device__ __forceinline__ void monitor_warp(MonSlot* slots, bool on, const Macro& m, float phi,
+                                             int x, int y, int z, int tid) {
+  float v[8];
+  unsigned cnt = 0u;
+  float u2 = 0.f;
+  if (on) {
+    const bool finite = isfinite(m.rho) && isfinite(m.ux) && isfinite(m.uy) && isfinite(m.uz);
+    v[0] = m.rR;
+    v[1] = m.rB;
+    v[2] = m.rho * m.ux - 0.5f * m.Fx;
+    v[3] = m.rho * m.uy - 0.5f * m.Fy;
+    v[4] = m.rho * m.uz - 0.5f * m.Fz;
+    v[5] = m.rR * (float)x;
+    v[6] = m.rR * (float)y;
+    v[7] = m.rR * (float)z;
+    cnt = (finite ? 0u : 1u) | ((m.rho <= 0.f ? 1u : 0u) << 8) |
+          ((phi > 0.f ? 1u : 0u) << 16) | ((m.rR < 0.f || m.rB < 0.f ? 1u : 0u) << 24);
+    if (finite) u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.f;
+  }
+  constexpr unsigned full = 0xffffffffu;
+  // the fold in pairs: two shuffles and one paired FP32 add per pair
+  float2 p[4] = {make_float2(v[0], v[1]), make_float2(v[2], v[3]), make_float2(v[4], v[5]),
+                 make_float2(v[6], v[7])};
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      p[k] = __fadd2_rn(p[k], make_float2(__shfl_xor_sync(full, p[k].x, off),
+                                          __shfl_xor_sync(full, p[k].y, off)));
+  // the four counts of a warp (at most 32 each) fit their bytes
+  cnt = __reduce_add_sync(full, cnt);
+  const unsigned ub = __reduce_max_sync(full, __float_as_uint(u2));
+  if ((tid & 31) == 0) {
+    MonSlot& w = slots[tid >> 5];
+    // compensated adds for the colour masses, whose drift is what a monitor
+    // watches; plain FP32 adds for the rest
+    kahan_add(w.s[0], w.c[0], p[0].x);
+    kahan_add(w.s[1], w.c[1], p[0].y);
+    w.s[2] += p[1].x;
+    w.s[3] += p[1].y;
+    w.s[4] += p[2].x;
+    w.s[5] += p[2].y;
+    w.s[6] += p[3].x;
+    w.s[7] += p[3].y;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w.n[k] += (cnt >> (8 * k)) & 0xffu;
+    w.u2bits = max(w.u2bits, ub);
+  }
+}
+// The CTA's record (kMonWarps slots): cleared before the chunk, added into
+// the step's global record after it (both bracketed by the kernel's
+// barriers).
+__device__ __forceinline__ void monitor_clear(MonSlot* slots, int tid) {
+  for (int i = tid; i < kMonWarps; i += 32) {
+    MonSlot& w = slots[i];
+    for (int k = 0; k < 8; ++k) w.s[k] = w.c[k] = 0.f;
+    for (int k = 0; k < 4; ++k) w.n[k] = 0u;
+    w.u2bits = 0u;
+  }
+}
+__device__ __forceinline__ void monitor_flush(const MonSlot* slots, MonAcc* g, int tid) {
+  if (tid < 8) {
+    double v = 0.0;
+    for (int w = 0; w < kMonWarps; ++w) v += (double)slots[w].s[tid] - (double)slots[w].c[tid];
+    atomicAdd(&g->d[tid], v);
+  } else if (tid < 12) {
+    unsigned v = 0u;
+    for (int w = 0; w < kMonWarps; ++w) v += slots[w].n[tid - 8];
+    atomicAdd(&g->n[tid - 8], v);
+  } else if (tid == 12) {
+    unsigned v = 0u;
+    for (int w = 0; w < kMonWarps; ++w) v = max(v, slots[w].u2bits);
+    atomicMax(&g->u2bits, v);
+  }
+}
+
 // One work item of the TMA-staged step: tile (bx, by) of the lattice `a`,
 // planes [zb, ze).  The CTA's stage mbarriers are initialised; G0 counts
 // the fills of the CTA's earlier items (their stage use), so that the
@@ -551,13 +655,14 @@ __host__ __device__ constexpr int tma_issuer() {
 // seam only; its lanes whose sources lie beyond the high seam pull from
 // global memory.
 template <typename T, bool WALLS, int TW, int BY, int NS, bool SEAM = false,
-          bool FALLBACK = false>
+          bool FALLBACK = false, bool MON = false>
 __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restrict__ dst,
                                           const StepArgs& a, const CUtensorMap* map0,
                                           const CUtensorMap* map1, int bx, int by, int zb,
                                           int ze, unsigned char* smem, unsigned G0,
                                           int* __restrict__ err, unsigned long long wait_ns,
-                                          const SeamStripMaps* strips = nullptr) {
+                                          const SeamStripMaps* strips = nullptr,
+                                          MonSlot* mon = nullptr) {
   static_assert(!SEAM || tma_pair_bytes<T>() == 8 || (TW - 2) % 4 == 0,
                 "the 16-bit SEAM form needs tile columns on 16-byte boundaries");
   constexpr int SB = tma_stage_bytes<T, TW, BY, SEAM>();
@@ -765,7 +870,32 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     }
     // the stage of fill k is consumed by every thread: refill it
     if (k + NS < K) issue(k + NS);
-    if (g.interior) {
+    if constexpr (MON) {
+      // the same work with the cell's diagnostics folded between the
+      // gradients and the collision, where every lane of a warp meets
+      const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
+      float4 ctr = make_float4(0.f, 0.f, 0.f, 0.f);
+      float Gx = 0.f, Gy = 0.f, Gz = 0.f, Qx = 0.f, Qy = 0.f, Qz = 0.f;
+      Macro m = {};
+      if (g.interior) {
+        window_gradients<BY, TW>(win, z, ty, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, ctr,
+                                 Gx, Gy, Gz, Qx, Qy, Qz);
+        if (WALLS && a.wetting)
+          wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
+        m = HV == 24 ? macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4])
+                     : macro_total(a, cf, ch[0], ch[1]);
+      }
+      monitor_warp(mon, g.interior, m, ctr.x, g.cx, g.cy, z, tid);
+      if (g.interior) {
+        const Recolour rc = collide_total<false>(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
+        store_recoloured<T>(dst, plane, a,
+                            (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1], rc, cf);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) cf[i] = hold[i][ty - 1][tx - 1];
+#pragma unroll
+        for (int i = 0; i < HV - 19; ++i) ch[i] = hold[19 + i][ty - 1][tx - 1];
+      }
+    } else if (g.interior) {
       const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
       float4 ctr;
       float Gx, Gy, Gz, Qx, Qy, Qz;
@@ -824,7 +954,8 @@ __global__ void __launch_bounds__(TW* BY, (tma_ctas_per_sm<TW, BY>()))
 // SEAM form (FP32, periodic in x and y, one stage): the source buffer's six
 // tensor maps (main TW, main TW + 2, x strip, y strip TW, y strip TW + 2,
 // corner), each a kernel parameter of its own like the other forms' maps.
-template <int TW, int BY, int NS, bool WALLS>
+// MON: also the diagnostics of the state read, added into *gmon.
+template <int TW, int BY, int NS, bool WALLS, bool MON = false>
 __global__ void __launch_bounds__(TW* BY, 1)
     k_fused_tma_seam(const float* __restrict__ src, float* __restrict__ dst,
                      const __grid_constant__ StepArgs a,
@@ -834,7 +965,7 @@ __global__ void __launch_bounds__(TW* BY, 1)
                      const __grid_constant__ CUtensorMap mys0,
                      const __grid_constant__ CUtensorMap mys1,
                      const __grid_constant__ CUtensorMap mcs, int zchunk,
-                     int* __restrict__ err) {
+                     int* __restrict__ err, MonAcc* __restrict__ gmon) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int zb = blockIdx.z * zchunk;
   const int ze = min(zb + zchunk, a.nz);
@@ -843,39 +974,52 @@ __global__ void __launch_bounds__(TW* BY, 1)
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
     return;
   }
+  const int tid = threadIdx.y * TW + threadIdx.x;
+  MonSlot* macc = nullptr;  // the CTA's record, a slot per warp (monitored form only)
+  if constexpr (MON) {
+    static_assert(TW * BY <= 32 * kMonWarps, "one record slot per warp");
+    __shared__ MonSlot macc_s[kMonWarps];
+    macc = macc_s;
+    if (tid < 32) monitor_clear(macc, tid);
+  }
   tma_init_barriers(tma_mbar_bytes<float, TW, BY, NS, true>(smem), NS);
   __syncthreads();
   const SeamStripMaps strips = {&mxs, &mys0, &mys1, &mcs};
-  tma_chunk<float, WALLS, TW, BY, NS, true>(src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y,
-                                            zb, ze, smem, 0u, err, tma_wait_limit(), &strips);
+  const bool ok = tma_chunk<float, WALLS, TW, BY, NS, true, false, MON>(
+      src, dst, a, &map0, &map1, blockIdx.x, blockIdx.y, zb, ze, smem, 0u, err,
+      tma_wait_limit(), &strips, macc);
+  if constexpr (MON) {
+    __syncthreads();
+    if (ok) monitor_flush(macc, gmon, tid);
+  }
 }
 
-template <int TW, int BY, int NS, bool WALLS>
+template <int TW, int BY, int NS, bool WALLS, bool MON = false>
 static cudaError_t launch_tma_seam_v(const void* src, void* dst, const StepArgs& a,
                                      const CUtensorMap* maps6, int zc, int* err,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, MonAcc* mon = nullptr) {
   static_assert(tma_fits<float, TW, BY, NS, true>(), "SEAM stages do not fit");
   static bool attr_set[kMaxDevices] = {};
   const int dv = device_slot();
   constexpr int bytes = tma_smem_bytes<float, TW, BY, NS, true>();
   if (!attr_set[dv]) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS, WALLS>,
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam<TW, BY, NS, WALLS, MON>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set[dv] = true;
   }
   dim3 blk(TW, BY);
   dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
-  k_fused_tma_seam<TW, BY, NS, WALLS><<<grd, blk, bytes, s>>>((const float*)src, (float*)dst, a, maps6[0],
-                                                   maps6[1], maps6[2], maps6[3], maps6[4],
-                                                   maps6[5], zc, err);
+  k_fused_tma_seam<TW, BY, NS, WALLS, MON><<<grd, blk, bytes, s>>>(
+      (const float*)src, (float*)dst, a, maps6[0], maps6[1], maps6[2], maps6[3], maps6[4],
+      maps6[5], zc, err, mon);
   return cudaGetLastError();
 }
 
 // 16-bit SEAM form (FP16 / BF16 deviation storage, periodic in x and y,
 // walls in z allowed): the source buffer's four maps (main W16 x BY, x strip
 // 4 x BY, y strip W16 x 2, corner 4 x 2) as kernel parameters.
-template <typename T, int TW, int BY, int NS, bool WALLS>
+template <typename T, int TW, int BY, int NS, bool WALLS, bool MON = false>
 __global__ void __launch_bounds__(TW* BY, 1)
     k_fused_tma_seam16(const T* __restrict__ src, T* __restrict__ dst,
                        const __grid_constant__ StepArgs a,
@@ -883,7 +1027,7 @@ __global__ void __launch_bounds__(TW* BY, 1)
                        const __grid_constant__ CUtensorMap mxs,
                        const __grid_constant__ CUtensorMap mys,
                        const __grid_constant__ CUtensorMap mcs, int zchunk,
-                       int* __restrict__ err) {
+                       int* __restrict__ err, MonAcc* __restrict__ gmon) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int zb = blockIdx.z * zchunk;
   const int ze = min(zb + zchunk, a.nz);
@@ -892,31 +1036,44 @@ __global__ void __launch_bounds__(TW* BY, 1)
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 2);
     return;
   }
+  const int tid = threadIdx.y * TW + threadIdx.x;
+  MonSlot* macc = nullptr;  // the CTA's record, a slot per warp (monitored form only)
+  if constexpr (MON) {
+    static_assert(TW * BY <= 32 * kMonWarps, "one record slot per warp");
+    __shared__ MonSlot macc_s[kMonWarps];
+    macc = macc_s;
+    if (tid < 32) monitor_clear(macc, tid);
+  }
   tma_init_barriers(tma_mbar_bytes<T, TW, BY, NS, true>(smem), NS);
   __syncthreads();
   const SeamStripMaps strips = {&mxs, &mys, &mys, &mcs};
-  tma_chunk<T, WALLS, TW, BY, NS, true>(src, dst, a, &map0, &map0, blockIdx.x, blockIdx.y, zb,
-                                        ze, smem, 0u, err, tma_wait_limit(), &strips);
+  const bool ok = tma_chunk<T, WALLS, TW, BY, NS, true, false, MON>(
+      src, dst, a, &map0, &map0, blockIdx.x, blockIdx.y, zb, ze, smem, 0u, err,
+      tma_wait_limit(), &strips, macc);
+  if constexpr (MON) {
+    __syncthreads();
+    if (ok) monitor_flush(macc, gmon, tid);
+  }
 }
 
-template <typename T, int TW, int BY, int NS, bool WALLS>
+template <typename T, int TW, int BY, int NS, bool WALLS, bool MON = false>
 static cudaError_t launch_tma_seam16_v(const void* src, void* dst, const StepArgs& a,
                                        const CUtensorMap* maps4, int zc, int* err,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, MonAcc* mon = nullptr) {
   static_assert(tma_fits<T, TW, BY, NS, true>(), "16-bit SEAM stages do not fit");
   static bool attr_set[kMaxDevices] = {};
   const int dv = device_slot();
   constexpr int bytes = tma_smem_bytes<T, TW, BY, NS, true>();
   if (!attr_set[dv]) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam16<T, TW, BY, NS, WALLS>,
+    cudaError_t e = cudaFuncSetAttribute(k_fused_tma_seam16<T, TW, BY, NS, WALLS, MON>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr_set[dv] = true;
   }
   dim3 blk(TW, BY);
   dim3 grd((a.nx + TW - 3) / (TW - 2), (a.ny + BY - 3) / (BY - 2), (a.nz + zc - 1) / zc);
-  k_fused_tma_seam16<T, TW, BY, NS, WALLS><<<grd, blk, bytes, s>>>(
-      (const T*)src, (T*)dst, a, maps4[0], maps4[1], maps4[2], maps4[3], zc, err);
+  k_fused_tma_seam16<T, TW, BY, NS, WALLS, MON><<<grd, blk, bytes, s>>>(
+      (const T*)src, (T*)dst, a, maps4[0], maps4[1], maps4[2], maps4[3], zc, err, mon);
   return cudaGetLastError();
 }
 
@@ -924,9 +1081,16 @@ static cudaError_t launch_tma_seam16_v(const void* src, void* dst, const StepArg
 template <typename T>
 cudaError_t launch_fused_tma_seam16_storage(const void* src, void* dst, const StepArgs& a,
                                             int tile_y, const CUtensorMap* maps4, int zchunk,
-                                            int* err, cudaStream_t s) {
+                                            int* err, cudaStream_t s, MonAcc* mon) {
   const int zc = zchunk > 0 ? zchunk : a.nz;
   const bool zwalls = a.wz != 0;
+  if (mon) {  // monitored form: the default 34 x 15 tile only
+    if (tile_y != 15) return cudaErrorInvalidValue;
+    return zwalls ? launch_tma_seam16_v<T, 34, 15, 2, true, true>(src, dst, a, maps4, zc, err,
+                                                                 s, mon)
+                  : launch_tma_seam16_v<T, 34, 15, 2, false, true>(src, dst, a, maps4, zc,
+                                                                  err, s, mon);
+  }
   if (tile_y == 15)
     return zwalls ? launch_tma_seam16_v<T, 34, 15, 2, true>(src, dst, a, maps4, zc, err, s)
                   : launch_tma_seam16_v<T, 34, 15, 2, false>(src, dst, a, maps4, zc, err, s);

@@ -34,6 +34,20 @@ struct NvtxRange {
 
 constexpr int kDiagSlots = 13;  // accumulated slots of lbm_diagnostics
 
+// Diagnostics summed inside a monitored step (lbm_step_monitored) over the
+// state the step reads: one record per CTA in shared memory, added into one
+// global record per step.
+struct MonAcc {
+  double d[8];      // red mass, blue mass, momentum x, y, z, red-mass moments x, y, z
+  unsigned n[4];    // cells: non-finite, total density <= 0, red (rho^N > 0), a colour < 0
+  unsigned u2bits;  // largest |u|^2 as float bits (>= 0, so the bits order like the values)
+  unsigned pad_[3];
+};
+// Writes the 16 slots of lbm_diagnostics from a step's record (slot 12 =
+// steps, slot 14 = the error word) to out and clears the record.
+cudaError_t launch_monitor_out(MonAcc* acc, const int* flags, double steps, double* out,
+                               cudaStream_t s);
+
 // Host helpers of the C-ABI layer.  Errors without a context are recorded
 // for lbm_last_error(NULL) of the calling thread.
 lbm_status validate_params(const lbm_params* p);
@@ -117,9 +131,11 @@ cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int
 bool seam_eligible(const StepArgs& a, int storage);
 cudaError_t tma_build_seam_maps(const void* base, const StepArgs& a, int tile_y,
                                 CUtensorMap maps[6]);
+// mon (monitored form, tile_y 12 only; else nullptr): the step also adds
+// the diagnostics of the state it reads into *mon.
 cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
                                   const CUtensorMap* maps6, int zchunk, int* err,
-                                  cudaStream_t s);
+                                  cudaStream_t s, MonAcc* mon = nullptr);
 // 16-bit SEAM forms (FP16 / BF16, 34 x 15 or 34 x 12 threads, two stages;
 // tile_y 15 or 12): periodic in x and y (walls in z allowed), nx a multiple
 // of 4, nx >= 34 and ny >= 15.  Four maps over the source buffer: main (38
@@ -131,10 +147,10 @@ cudaError_t tma_build_seam16_maps(int storage, const void* base, const StepArgs&
 template <typename T>
 cudaError_t launch_fused_tma_seam16_storage(const void* src, void* dst, const StepArgs& a,
                                             int tile_y, const CUtensorMap* maps4, int zchunk,
-                                            int* err, cudaStream_t s);
+                                            int* err, cudaStream_t s, MonAcc* mon);
 cudaError_t launch_fused_tma_seam16(int storage, const void* src, void* dst, const StepArgs& a,
                                     int tile_y, const CUtensorMap* maps4, int zchunk, int* err,
-                                    cudaStream_t s);
+                                    cudaStream_t s, MonAcc* mon = nullptr);
 // z chunk of the 34 x 12 two-stage SEAM form: the one whose list schedule of
 // CTAs over the SMs ends first.
 int seam12_zchunk(const StepArgs& a, int sms);

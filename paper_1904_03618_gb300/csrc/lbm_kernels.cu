@@ -673,4 +673,30 @@ cudaError_t launch_twopass(int storage, const void* src, void* dst,
   LBM_DISPATCH(storage, launch_twopass_t, src, dst, a, mom, s)
 }
 
+// A monitored step's record -> the 16 slots of lbm_diagnostics (steps: the
+// steps completed before the state the step read); the record is cleared
+// for the next step.
+__global__ void k_monitor_out(MonAcc* __restrict__ acc, const int* __restrict__ flags,
+                              double steps, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < 5; ++k) out[k] = acc->d[k];
+  out[5] = (double)acc->n[0];
+  out[6] = (double)acc->n[1];
+  out[7] = sqrt((double)__uint_as_float(acc->u2bits));
+  out[8] = (double)acc->n[2];
+  for (int k = 5; k < 8; ++k) out[4 + k] = acc->d[0] > 0.0 ? acc->d[k] / acc->d[0] : acc->d[k];
+  out[12] = steps;
+  out[13] = (double)acc->n[3];
+  out[14] = (double)*flags;
+  out[15] = 0.0;
+  for (int k = 0; k < 8; ++k) acc->d[k] = 0.0;
+  for (int k = 0; k < 4; ++k) acc->n[k] = 0u;
+  acc->u2bits = 0u;
+}
+cudaError_t launch_monitor_out(MonAcc* acc, const int* flags, double steps, double* out,
+                               cudaStream_t s) {
+  k_monitor_out<<<1, 32, 0, s>>>(acc, flags, steps, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lbm

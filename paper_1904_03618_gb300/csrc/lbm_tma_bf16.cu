@@ -13,5 +13,5 @@ template bool tma_config_fits_storage<__nv_bfloat16>(int, int);
 template cudaError_t tma_set_wait_ns<__nv_bfloat16>(unsigned long long);
 template cudaError_t launch_fused_tma_seam16_storage<__nv_bfloat16>(const void*, void*, const StepArgs&,
                                                          int, const CUtensorMap*, int, int*,
-                                                         cudaStream_t);
+                                                         cudaStream_t, MonAcc*);
 }  // namespace lbm

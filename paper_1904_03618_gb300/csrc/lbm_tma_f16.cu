@@ -13,5 +13,5 @@ template bool tma_config_fits_storage<__half>(int, int);
 template cudaError_t tma_set_wait_ns<__half>(unsigned long long);
 template cudaError_t launch_fused_tma_seam16_storage<__half>(const void*, void*, const StepArgs&,
                                                          int, const CUtensorMap*, int, int*,
-                                                         cudaStream_t);
+                                                         cudaStream_t, MonAcc*);
 }  // namespace lbm

@@ -16,9 +16,15 @@ template cudaError_t tma_set_wait_ns<float>(unsigned long long);
 // one stage, 34 x 12 with two.
 cudaError_t launch_fused_tma_seam(const void* src, void* dst, const StepArgs& a, int tile_y,
                                   const CUtensorMap* maps6, int zchunk, int* err,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, MonAcc* mon) {
   const int zc = zchunk > 0 ? zchunk : a.nz;
   const bool zwalls = a.wz != 0;  // x and y are periodic (seam_eligible)
+  if (mon) {  // monitored form: the default 34 x 12 tile only
+    if (tile_y != 12) return cudaErrorInvalidValue;
+    return zwalls ? launch_tma_seam_v<34, 12, 2, true, true>(src, dst, a, maps6, zc, err, s, mon)
+                  : launch_tma_seam_v<34, 12, 2, false, true>(src, dst, a, maps6, zc, err, s,
+                                                              mon);
+  }
   if (tile_y == 15)
     return zwalls ? launch_tma_seam_v<34, 15, 1, true>(src, dst, a, maps6, zc, err, s)
                   : launch_tma_seam_v<34, 15, 1, false>(src, dst, a, maps6, zc, err, s);

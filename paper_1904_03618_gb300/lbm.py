@@ -87,6 +87,8 @@ _lib.lbm_diagnostics.argtypes = [_ctx_p, ctypes.POINTER(ctypes.c_double)]
 _lib.lbm_diagnostics.restype = ctypes.c_int
 _lib.lbm_step_diagnostics_async.argtypes = [_ctx_p, ctypes.c_int, _fp]
 _lib.lbm_step_diagnostics_async.restype = ctypes.c_int
+_lib.lbm_step_monitored.argtypes = [_ctx_p, ctypes.c_int, _fp]
+_lib.lbm_step_monitored.restype = ctypes.c_int
 _lib.lbm_sync.argtypes = [_ctx_p]
 _lib.lbm_sync.restype = ctypes.c_int
 _lib.lbm_get_f.argtypes = [_ctx_p, _fp]
@@ -175,7 +177,7 @@ _lib.lbm_last_error.argtypes = [_ctx_p]
 _lib.lbm_last_error.restype = ctypes.c_char_p
 
 EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
-            "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
+            "lbm_diagnostics", "lbm_step_diagnostics_async", "lbm_step_monitored", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_population_bytes",
             "lbm_get_populations", "lbm_set_populations", "lbm_plane_bytes",
             "lbm_get_planes", "lbm_set_planes",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_default_fused_config",
@@ -329,6 +331,17 @@ def lbm_step_diagnostics_async(ctx, n, out):
     if isinstance(out, torch.Tensor) and (out.dtype != torch.float64 or out.numel() < 16):
         raise ValueError("out must hold 16 float64 values")
     _check(ctx, _lib.lbm_step_diagnostics_async(ctx, int(n), _addr(out)))
+
+
+def lbm_step_monitored(ctx, n, out):
+    """Queues n steps, step k reporting the diagnostics of the state it
+    reads into ``out[k]`` (16 float64 per step: a pinned CPU tensor or a
+    device tensor of at least 16 n values); ``out`` is valid after
+    :func:`lbm_sync`."""
+    if isinstance(out, torch.Tensor) and (out.dtype != torch.float64 or
+                                          out.numel() < 16 * int(n)):
+        raise ValueError("out must hold 16 n float64 values")
+    _check(ctx, _lib.lbm_step_monitored(ctx, int(n), _addr(out)))
 
 
 def lbm_sync(ctx):
