@@ -540,14 +540,14 @@ __host__ __device__ constexpr int tma_issuer() {
   return (TW - 2) * (BY - 2);
 }
 
-// Monitored steps: per plane, every warp folds its lanes' diagnostics of
-// the state the step reads (lanes without an interior cell add zeros) with
-// FP32 shuffles, and lane 0 adds the folds into the warp's own slot of the
-// CTA's record (FP32, the masses with Kahan compensation: no atomics, no FP64 -- the
-// FP64 pipe is narrow on this GPU and a per-plane FP64 fold cost the step
-// more than its collision; per-thread sums held in registers over the
-// chunk cost it a quarter, through register pressure).  After the chunk
-// the kernel adds the slots in FP64 into the step's global record.  The
+// Monitored steps: each lane adds the diagnostics of its interior cell's
+// state (the state the step reads) to FP32 sums in registers; every
+// kMonFold planes (and after the last) each warp folds its lanes with FP32
+// shuffles (paired adds) and lane 0 adds the fold into the warp's own slot
+// of the CTA's record (FP32, the colour masses with Kahan compensation: no
+// atomics and no FP64 -- the FP64 pipe is narrow on this GPU; a per-plane
+// FP64 fold cost the step more than its collision).  After the chunk the
+// kernel adds the slots in FP64 into the step's global record.  The
 // momentum is the raw sum_i e_i f_i (the velocity without its half-force
 // shift); a NaN or an infinity in any population reaches rho or u, so
 // their finiteness marks the cell; rho^N is the cell's phase-field entry
@@ -564,58 +564,60 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   c = (t - s) - y;
   s = t;
 }
-// Every lane of the warp calls it once per plane.
-__device__ __forceinline__ void monitor_warp(MonSlot* slots, bool on, const Macro& m, float phi,
-                                             int x, int y, int z, int tid) {
-  float v[8];
-  unsigned cnt = 0u;
-  float u2 = 0.f;
-  if (on) {
-    const bool finite = isfinite(m.rho) && isfinite(m.ux) && isfinite(m.uy) && isfinite(m.uz);
-    v[0] = m.rR;
-    v[1] = m.rB;
-    v[2] = m.rho * m.ux - 0.5f * m.Fx;
-    v[3] = m.rho * m.uy - 0.5f * m.Fy;
-    v[4] = m.rho * m.uz - 0.5f * m.Fz;
-    v[5] = m.rR * (float)x;
-    v[6] = m.rR * (float)y;
-    v[7] = m.rR * (float)z;
-    cnt = (finite ? 0u : 1u) | ((m.rho <= 0.f ? 1u : 0u) << 8) |
-          ((phi > 0.f ? 1u : 0u) << 16) | ((m.rR < 0.f || m.rB < 0.f ? 1u : 0u) << 24);
-    if (finite) u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = 0.f;
-  }
+// A lane's sums over the planes since the warp last folded.  A lane keeps
+// its column (x, y) over the chunk, so its red-mass moments in x and y are
+// x and y times its red mass: only the z moment has a sum of its own.
+constexpr int kMonFold = 4;  // planes per fold (the packed counts stay below 256)
+struct MonLane {
+  float2 p[3] = {};   // (red mass, blue mass), (momentum x, y), (momentum z, sum rho_R z)
+  unsigned cnt = 0u;  // bytes: non-finite, rho <= 0, red, a colour < 0
+  float u2 = 0.f;     // largest finite |u|^2
+};
+__device__ __forceinline__ void monitor_lane_add(MonLane& l, const Macro& m, float phi, int z) {
+  const bool finite = isfinite(m.rho) && isfinite(m.ux) && isfinite(m.uy) && isfinite(m.uz);
+  l.p[0] = __fadd2_rn(l.p[0], make_float2(m.rR, m.rB));
+  l.p[1] = __fadd2_rn(l.p[1], make_float2(m.rho * m.ux - 0.5f * m.Fx,
+                                          m.rho * m.uy - 0.5f * m.Fy));
+  l.p[2] = __fadd2_rn(l.p[2], make_float2(m.rho * m.uz - 0.5f * m.Fz, m.rR * (float)z));
+  l.cnt += (finite ? 0u : 1u) | ((m.rho <= 0.f ? 1u : 0u) << 8) |
+           ((phi > 0.f ? 1u : 0u) << 16) | ((m.rR < 0.f || m.rB < 0.f ? 1u : 0u) << 24);
+  if (finite) l.u2 = fmaxf(l.u2, m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+}
+// Folds the warp's lanes (x, y: the lane's column; a lane without interior
+// cells has zero sums) into its slot and clears the lanes' sums; every lane
+// of the warp calls it.
+__device__ __forceinline__ void monitor_fold(MonSlot* slots, MonLane& l, int x, int y,
+                                             int tid) {
   constexpr unsigned full = 0xffffffffu;
+  float2 q[4] = {l.p[0], l.p[1], make_float2(l.p[2].x, l.p[0].x * (float)x),
+                 make_float2(l.p[0].x * (float)y, l.p[2].y)};
   // the fold in pairs: two shuffles and one paired FP32 add per pair
-  float2 p[4] = {make_float2(v[0], v[1]), make_float2(v[2], v[3]), make_float2(v[4], v[5]),
-                 make_float2(v[6], v[7])};
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      p[k] = __fadd2_rn(p[k], make_float2(__shfl_xor_sync(full, p[k].x, off),
-                                          __shfl_xor_sync(full, p[k].y, off)));
-  // the four counts of a warp (at most 32 each) fit their bytes
-  cnt = __reduce_add_sync(full, cnt);
-  const unsigned ub = __reduce_max_sync(full, __float_as_uint(u2));
+      q[k] = __fadd2_rn(q[k], make_float2(__shfl_xor_sync(full, q[k].x, off),
+                                          __shfl_xor_sync(full, q[k].y, off)));
+  // the four counts of a warp (at most 32 kMonFold each) fit their bytes
+  const unsigned cnt = __reduce_add_sync(full, l.cnt);
+  const unsigned ub = __reduce_max_sync(full, __float_as_uint(l.u2));
   if ((tid & 31) == 0) {
     MonSlot& w = slots[tid >> 5];
     // compensated adds for the colour masses, whose drift is what a monitor
     // watches; plain FP32 adds for the rest
-    kahan_add(w.s[0], w.c[0], p[0].x);
-    kahan_add(w.s[1], w.c[1], p[0].y);
-    w.s[2] += p[1].x;
-    w.s[3] += p[1].y;
-    w.s[4] += p[2].x;
-    w.s[5] += p[2].y;
-    w.s[6] += p[3].x;
-    w.s[7] += p[3].y;
+    kahan_add(w.s[0], w.c[0], q[0].x);
+    kahan_add(w.s[1], w.c[1], q[0].y);
+    w.s[2] += q[1].x;
+    w.s[3] += q[1].y;
+    w.s[4] += q[2].x;
+    w.s[5] += q[2].y;
+    w.s[6] += q[3].x;
+    w.s[7] += q[3].y;
 #pragma unroll
     for (int k = 0; k < 4; ++k) w.n[k] += (cnt >> (8 * k)) & 0xffu;
     w.u2bits = max(w.u2bits, ub);
   }
+  l = MonLane();
 }
 // The CTA's record (kMonWarps slots): cleared before the chunk, added into
 // the step's global record after it (both bracketed by the kernel's
@@ -851,6 +853,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     }
     if (K > 2) issue(2);
   }
+  MonLane ml;  // monitored form: this lane's sums since the last fold
   for (int k = 2; k < K; ++k) {
     const int z = zb + k - 2;  // plane that collides; plane z + 1 is filled
     float nf[19], nh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -870,32 +873,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     }
     // the stage of fill k is consumed by every thread: refill it
     if (k + NS < K) issue(k + NS);
-    if constexpr (MON) {
-      // the same work with the cell's diagnostics folded between the
-      // gradients and the collision, where every lane of a warp meets
-      const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
-      float4 ctr = make_float4(0.f, 0.f, 0.f, 0.f);
-      float Gx = 0.f, Gy = 0.f, Gz = 0.f, Qx = 0.f, Qy = 0.f, Qz = 0.f;
-      Macro m = {};
-      if (g.interior) {
-        window_gradients<BY, TW>(win, z, ty, tx, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, ctr,
-                                 Gx, Gy, Gz, Qx, Qy, Qz);
-        if (WALLS && a.wetting)
-          wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
-        m = HV == 24 ? macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4])
-                     : macro_total(a, cf, ch[0], ch[1]);
-      }
-      monitor_warp(mon, g.interior, m, ctr.x, g.cx, g.cy, z, tid);
-      if (g.interior) {
-        const Recolour rc = collide_total<false>(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
-        store_recoloured<T>(dst, plane, a,
-                            (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1], rc, cf);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) cf[i] = hold[i][ty - 1][tx - 1];
-#pragma unroll
-        for (int i = 0; i < HV - 19; ++i) ch[i] = hold[19 + i][ty - 1][tx - 1];
-      }
-    } else if (g.interior) {
+    if (g.interior) {
       const bool zlo = WALLS && a.wz && z == 0, zhi = WALLS && a.wz && z == a.nz - 1;
       float4 ctr;
       float Gx, Gy, Gz, Qx, Qy, Qz;
@@ -905,6 +883,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
         wetting_rule(a, g.xlo, g.xhi, g.ylo, g.yhi, zlo, zhi, Gx, Gy, Gz);
       const Macro m = HV == 24 ? macro_held(a, ch[0], ch[1], ch[2], ch[3], ch[4])
                                : macro_total(a, cf, ch[0], ch[1]);
+      if constexpr (MON) monitor_lane_add(ml, m, ctr.x, z);
       const Recolour rc = collide_total<false>(a, cf, m, ctr.x, Gx, Gy, Gz, Qx, Qy, Qz);
       store_recoloured<T>(dst, plane, a, (unsigned)z * g.plane_cells + g.co.yo[1] + g.co.xo[1],
                           rc, cf);
@@ -913,6 +892,9 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
 #pragma unroll
       for (int i = 0; i < HV - 19; ++i) ch[i] = hold[19 + i][ty - 1][tx - 1];
     }
+    if constexpr (MON)
+      if ((k - 2) % kMonFold == kMonFold - 1 || k == K - 1)
+        monitor_fold(mon, ml, g.cx, g.cy, tid);
   }
   return true;
 }
