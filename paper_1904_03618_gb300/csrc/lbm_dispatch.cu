@@ -142,13 +142,8 @@ bool tma_default_config(const StepArgs& a, int storage, int sms, const bool kind
 // beyond the array read as zero.
 // One tensor map over a population buffer seen as [direction][z][y][x]
 // pairs, with a box of w x h pairs (one plane, one direction).
-static cudaError_t encode_box(int storage, const void* base, const StepArgs& a, unsigned w,
-                              unsigned h, CUtensorMap* map) {
-  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeFn encode = nullptr;
+cudaError_t tensor_map_encoder(EncodeTiledFn* out) {
+  static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -156,8 +151,17 @@ static cudaError_t encode_box(int storage, const void* base, const StepArgs& a, 
                                                      cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
       return e != cudaSuccess ? e : cudaErrorNotSupported;
-    encode = (EncodeFn)fn;
+    encode = (EncodeTiledFn)fn;
   }
+  *out = encode;
+  return cudaSuccess;
+}
+
+static cudaError_t encode_box(int storage, const void* base, const StepArgs& a, unsigned w,
+                              unsigned h, CUtensorMap* map) {
+  EncodeTiledFn encode = nullptr;
+  const cudaError_t e = tensor_map_encoder(&encode);
+  if (e != cudaSuccess) return e;
   const cuuint64_t E = (cuuint64_t)pair_bytes(storage);
   const cuuint64_t dims[4] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz, 19};
   const cuuint64_t strides[3] = {E * a.nx, E * a.nx * a.ny, E * (cuuint64_t)a.plane};

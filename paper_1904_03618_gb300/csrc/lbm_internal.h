@@ -119,6 +119,12 @@ FusedConfig default_fused_config(const StepArgs& a, int storage);
 // FP32, nx a multiple of 4 for 16-bit storage); maps[2] are the two tensor
 // maps of the source buffer for the tile (tma_build_maps).
 bool tma_eligible(const StepArgs& a, int storage);
+// The driver's cuTensorMapEncodeTiled, looked up once.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+cudaError_t tensor_map_encoder(EncodeTiledFn* out);
 int tma_kind(int tile_y);  // -1 for a tile_y without a TMA form
 cudaError_t tma_build_maps(int storage, const void* base, const StepArgs& a, int kind,
                            CUtensorMap maps[2]);

@@ -25,7 +25,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cstddef>
+#include <cstdint>
 #include <new>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -373,8 +376,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
 //   - B (bn columns x K, BF16) is staged once per CTA and stays resident;
 //   - a CTA walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 //     of its column block blockIdx.y;
-//   - 8 producer warps load the FP32 A slices (128 x 64), round them to BF16
-//     and write them into a 4-stage ring (full / empty mbarriers);
+//   - the FP32 A slices (128 x 64) reach a 4-stage BF16 ring (full / empty
+//     mbarriers) one of two ways.  Where A's rows are K-contiguous with a
+//     16-byte multiple stride (the TMA form, column blocks <= 128), one
+//     thread issues tensor copies of each slice into a two-stage FP32 ring
+//     and 8 converter warps round it to BF16; elsewhere 8 producer warps
+//     load, round and store the slices themselves;
 //   - one thread issues the tcgen05.mma of each slice into one of two TMEM
 //     accumulators and commits them to the slice's empty barrier, and the
 //     finished tile to its accumulator's full barrier;
@@ -393,6 +400,8 @@ constexpr int kMmaWarp = kEpiWarps + kProdWarps;  // warp 16
 constexpr int kThreads = 32 * (kMmaWarp + 1);     // 544
 constexpr int kStages = 4;
 constexpr int kKMax = 256;
+constexpr int kStagesT = 2;  // the TMA form: BF16 ring stages
+constexpr int kFStages = 3;  // the TMA form: FP32 ring stages (96 KB in flight)
 }  // namespace ws
 
 struct WsSmem {
@@ -404,6 +413,35 @@ struct WsSmem {
   unsigned tmem_base;
   int give_up;
 };
+// The TMA form (k_gemm_ws<true>): column blocks of at most 128, and the FP32
+// A slices arrive by tensor copies -- two 32-k boxes of 128 rows each, with
+// the 128-byte swizzle (16-byte chunk c of row r at chunk c ^ (r & 7)) --
+// into a three-stage FP32 ring that the converter warps turn into a
+// two-stage BF16 ring (the MMA of a slice takes a fraction of a copy's
+// latency, so the bytes go to copies in flight).  The FP32 ring starts on a
+// 1024-byte boundary (the swizzle's period).
+constexpr int kTmaBn = 128;
+struct WsSmemT {
+  __nv_bfloat16 b[kTmaBn * ws::kKMax];       // 64 KB
+  __nv_bfloat16 a[ws::kStagesT][kM * kKT];   // 32 KB
+  float af[ws::kFStages][2][kM * 32];        // 96 KB: stage, 32-k box, 128 rows x 32
+  float bias[kNMax];
+  float ctile[ws::kEpiWarps][32 * 32];
+  unsigned long long full[ws::kStagesT], empty[ws::kStagesT], acc_full[2], acc_empty[2];
+  unsigned long long ffull[ws::kFStages], fempty[ws::kFStages];  // copies landed / consumed
+  unsigned tmem_base;
+  int give_up;
+};
+static_assert(offsetof(WsSmemT, af) % 1024 == 0, "the swizzled boxes need 1024-byte alignment");
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(unsigned addr) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
@@ -685,10 +723,23 @@ __device__ __forceinline__ void ws_store_a(unsigned char* dst, const ASlice& x, 
   }
 }
 
-// g.ws_bn: columns per CTA (a multiple of 16, <= 256); K <= 256.
-__global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
+// g.ws_bn: columns per CTA (a multiple of 16, <= 256; <= kTmaBn for TA);
+// K <= 256.  TA: the A slices arrive by tensor copies of amap (warp 17 lane
+// 0 issues them; the producer warps convert), else the producer warps load
+// them.
+template <bool TA>
+__global__ void __launch_bounds__(TA ? ws::kThreads + 32 : ws::kThreads, 1)
+    k_gemm_ws(GemmArgs g, const __grid_constant__ CUtensorMap amap) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  WsSmem& sm = *reinterpret_cast<WsSmem*>(smem_raw);
+  using S = std::conditional_t<TA, WsSmemT, WsSmem>;
+  constexpr int NTH = TA ? ws::kThreads + 32 : ws::kThreads;
+  constexpr int NS = TA ? ws::kStagesT : ws::kStages;  // BF16 ring stages
+  constexpr int kTmaWarp = ws::kMmaWarp + 1;
+  // the TMA form's swizzled boxes need a 1024-byte aligned base (the
+  // launch allocates 1 KB more)
+  unsigned char* base = smem_raw;
+  if constexpr (TA) base += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  S& sm = *reinterpret_cast<S*>(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bn = g.ws_bn;
   const int n0 = (int)blockIdx.y * bn;
@@ -699,7 +750,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
   volatile int* give_up = &sm.give_up;
 
   if (tid == 0) {
-    for (int s = 0; s < ws::kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.full[s])),
                    "r"(ws::kProd)
                    : "memory");
@@ -724,10 +775,42 @@ __global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  // B (bn x K) and the bias of this column block, staged once by every thread
-  ws_stage_b(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0, g.N, bn, nk, g.K,
-             tid);
-  for (int n = tid; n < bn; n += ws::kThreads)
+  const int my_tiles = (mt - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int total = my_tiles * nk;  // A slices this CTA consumes
+  // the TMA form: the copy thread owns the FP32 ring's barriers and has its
+  // first kFStages copies in flight while the others stage B
+  [[maybe_unused]] auto issue_a = [&](auto& smr, int q) {
+    const int st2 = q % ws::kFStages;
+    const int mi = (int)blockIdx.x + (q / nk) * (int)gridDim.x, k0 = (q % nk) * kKT;
+    const unsigned mb = smem_u32(&smr.ffull[st2]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb),
+                 "r"((unsigned)(2 * kM * 32 * sizeof(float)))
+                 : "memory");
+    tma_load_2d(smem_u32(smr.af[st2][0]), &amap, k0, mi * kM, mb);
+    tma_load_2d(smem_u32(smr.af[st2][1]), &amap, k0 + 32, mi * kM, mb);
+  };
+  int pre = 0;
+  if constexpr (TA) {
+    if (warp == kTmaWarp && lane == 0) {
+      for (int b = 0; b < ws::kFStages; ++b) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.ffull[b]))
+                     : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.fempty[b])),
+                     "r"(ws::kProd)
+                     : "memory");
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      pre = total < ws::kFStages ? total : ws::kFStages;
+      for (int q = 0; q < pre; ++q) issue_a(sm, q);
+    }
+  }
+  // B (bn x K) and the bias of this column block, staged once by every
+  // thread but the copy warp's
+  if (tid < ws::kThreads)
+    ws_stage_b(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0, g.N, bn, nk,
+               g.K, tid);
+  for (int n = tid; n < bn; n += NTH)
     sm.bias[n] = (g.bias && n0 + n < g.N) ? g.bias[n0 + n] : 0.f;
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -736,14 +819,79 @@ __global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
   const unsigned tmem = sm.tmem_base;
   const unsigned long long wait_ns = mma_wait_limit();
 
-  if (warp >= ws::kEpiWarps && warp < ws::kMmaWarp) {
+  if (TA && warp >= ws::kEpiWarps && warp < ws::kMmaWarp) {
+    // converters: each FP32 slice (two swizzled 32-k boxes) into the BF16
+    // ring; task g = (row r, 8-k group kg) as in ws_stage, whose eight lanes
+    // of a quarter-warp read eight rows of one chunk column -- eight
+    // different swizzled chunks, no bank conflict -- and write eight rows of
+    // one core-matrix column
+    if constexpr (TA) {
+      const int pt = tid - 32 * ws::kEpiWarps;
+      bool ok = true;
+      for (int q = 0; q < total && ok; ++q) {
+        const int st = q % NS, use = q / NS;
+        const int st2 = q % ws::kFStages, use2 = q / ws::kFStages;
+        ok = ws_wait(smem_u32(&sm.empty[st]), (use & 1) ^ 1, wait_ns, give_up) &&
+             ws_wait(smem_u32(&sm.ffull[st2]), use2 & 1, wait_ns, give_up);
+        if (!ok) break;
+        unsigned char* dst = reinterpret_cast<unsigned char*>(sm.a[st]);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int g = b * ws::kProd + pt;
+          const int r = (g >> 6) * 8 + (g & 7), kg = (g >> 3) & 7;
+          const float* row = sm.af[st2][kg >> 2] + r * 32;
+          const int c0 = (kg & 3) * 2, sw = r & 7;
+          const float4 v0 = *reinterpret_cast<const float4*>(row + 4 * (c0 ^ sw));
+          const float4 v1 = *reinterpret_cast<const float4*>(row + 4 * ((c0 + 1) ^ sw));
+          uint4 w;
+          w.x = pack_bf16x2(v0.x, v0.y);
+          w.y = pack_bf16x2(v0.z, v0.w);
+          w.z = pack_bf16x2(v1.x, v1.y);
+          w.w = pack_bf16x2(v1.z, v1.w);
+          *reinterpret_cast<uint4*>(dst + core_offset(r, kg * 8)) = w;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(smem_u32(&sm.full[st]));
+        mbar_arrive(smem_u32(&sm.fempty[st2]));
+      }
+      if (!ok) {
+        *give_up = 1;
+        atomicExch(g.err, 1);
+      }
+    }
+  } else if (TA && warp == kTmaWarp) {
+    // the tensor copies of the FP32 slices, kFStages ahead of the
+    // converters; before leaving, the last copies issued are waited for
+    // (at the full limit), so that none lands after the CTA has gone
+    if constexpr (TA) {
+      if (lane == 0) {
+        int issued = pre;
+        bool ok = true;
+        for (int q = pre; q < total; ++q) {
+          const int use2 = q / ws::kFStages;
+          if (!ws_wait(smem_u32(&sm.fempty[q % ws::kFStages]), (use2 & 1) ^ 1, wait_ns,
+                       give_up)) {
+            ok = false;
+            break;
+          }
+          issue_a(sm, q);
+          ++issued;
+        }
+        if (!ok) {
+          *give_up = 1;
+          atomicExch(g.err, 1);
+        }
+        for (int q = issued - ws::kFStages < 0 ? 0 : issued - ws::kFStages; q < issued; ++q)
+          mbar_wait(smem_u32(&sm.ffull[q % ws::kFStages]),
+                    (unsigned)((q / ws::kFStages) & 1), kWaitNs);
+      }
+    }
+  } else if (!TA && warp >= ws::kEpiWarps && warp < ws::kMmaWarp) {
     // producers: A slices into the ring, two at a time where A is
     // K-contiguous (both slices' loads in flight before either is stored)
     const int pt = tid - 32 * ws::kEpiWarps;
     const bool pair = g.sa_k == 1 && (g.sa_m & 3) == 0 &&
                       (reinterpret_cast<unsigned long long>(g.A) & 15u) == 0;
-    const int my_tiles = (mt - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int total = my_tiles * nk;
     bool ok = true;
     for (int q = 0; q < total; q += pair ? 2 : 1) {
       const int nq = pair && q + 1 < total ? 2 : 1;
@@ -796,7 +944,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1) k_gemm_ws(GemmArgs g) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const unsigned d_tmem = tmem + (unsigned)acc * acc_cols;
         for (int s = 0; s < nk; ++s, ++q) {
-          const int st = q % ws::kStages, use = q / ws::kStages;
+          const int st = q % NS, use = q / NS;
           if (!ws_wait(smem_u32(&sm.full[st]), use & 1, wait_ns, give_up)) {
             ok = false;
             break;
@@ -982,29 +1130,62 @@ static int sm_count() {
 // k_gemm_ws launch: the column block is halved (down to 16 columns) while
 // the row tiles alone leave SMs idle; the grid's x extent is at most the SMs
 // per column block (persistent CTAs over the row tiles).
-static cudaError_t launch_gemm_ws(GemmArgs g, cudaStream_t s) {
+// The A map of the TMA form: FP32 A seen as K x M (K innermost), boxes of
+// 32 x 128 with the 128-byte swizzle; rows and columns beyond A read as
+// zero.
+static bool encode_a_map(const GemmArgs& g, CUtensorMap* map) {
+  if (g.sa_k != 1 || (g.sa_m & 3) != 0 || (reinterpret_cast<uintptr_t>(g.A) & 15u) != 0 ||
+      g.M < kM || g.K < 32)
+    return false;
+  EncodeTiledFn encode = nullptr;
+  if (tensor_map_encoder(&encode) != cudaSuccess) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)g.K, (cuuint64_t)g.M};
+  const cuuint64_t strides[1] = {(cuuint64_t)g.sa_m * sizeof(float)};
+  const cuuint32_t box[2] = {32, (cuuint32_t)kM};
+  const cuuint32_t es[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(g.A), dims, strides,
+                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool TA>
+static cudaError_t launch_ws_form(const GemmArgs& g, const CUtensorMap& amap, int gx, int nt,
+                                  cudaStream_t s) {
   static bool attr_dev[kMaxDevices] = {};
   bool& attr = attr_dev[device_slot()];
-  const int bytes = (int)sizeof(WsSmem);
+  const int bytes = TA ? (int)sizeof(WsSmemT) + 1024 : (int)sizeof(WsSmem);
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_gemm_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<TA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  k_gemm_ws<TA><<<dim3((unsigned)gx, (unsigned)nt), TA ? ws::kThreads + 32 : ws::kThreads, bytes,
+                  s>>>(g, amap);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_gemm_ws(GemmArgs g, cudaStream_t s) {
   const int sms = sm_count();
   const int n_mma = (g.N + 15) / 16 * 16;
   const int mt = (g.M + kM - 1) / kM;
+  // the TMA form wherever A's layout allows one (K-contiguous rows of a
+  // 16-byte multiple, at least one full row tile and one 32-k box)
+  CUtensorMap amap;
+  memset(&amap, 0, sizeof(amap));
+  const bool ta = encode_a_map(g, &amap);
   int nt = 1;
   while ((long long)mt * nt * 2 <= sms && n_mma / (nt * 2) >= 16) nt *= 2;
+  if (ta)
+    while ((n_mma + nt - 1) / nt > kTmaBn) nt *= 2;
   g.ws_bn = ((n_mma + nt - 1) / nt + 15) / 16 * 16;
   nt = (g.N + g.ws_bn - 1) / g.ws_bn;
   int gx = sms / nt;
   if (gx < 1) gx = 1;
   if (gx > mt) gx = mt;
   g.splits = 1;
-  k_gemm_ws<<<dim3((unsigned)gx, (unsigned)nt), ws::kThreads, bytes, s>>>(g);
-  return cudaGetLastError();
+  return ta ? launch_ws_form<true>(g, amap, gx, nt, s) : launch_ws_form<false>(g, amap, gx, nt, s);
 }
 
 cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {

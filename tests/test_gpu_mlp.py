@@ -46,7 +46,11 @@ def _gemm(A, B, transpose_a=False, transpose_b=False):
                                    (257, 256, 1000), (5, 256, 7), (1000, 64, 16),
                                    # several row tiles per persistent CTA: both
                                    # accumulators and every ring stage reused
-                                   (40000, 256, 256), (40003, 16, 5), (20000, 100, 200)])
+                                   (40000, 256, 256), (40003, 16, 5), (20000, 100, 200),
+                                   # the TMA-fed form (A K-contiguous, rows of a
+                                   # 16-byte multiple): K ends inside a 32-k box,
+                                   # M inside a row tile, column blocks < 128
+                                   (1000, 48, 40), (333, 96, 100), (40001, 200, 252)])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_gemm_matches_fp64_product_of_bf16_operands(M, N, K, ta, tb):
     rng = np.random.default_rng(M * 7919 + N * 31 + K)
