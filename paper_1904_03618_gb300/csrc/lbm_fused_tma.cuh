@@ -585,9 +585,13 @@ __device__ __forceinline__ void monitor_lane_add(MonLane& l, const Macro& m, flo
 }
 // Folds the warp's lanes (x, y: the lane's column; a lane without interior
 // cells has zero sums) into its slot and clears the lanes' sums; every lane
-// of the warp calls it.
+// of the warp calls it.  The CTA's last warp can be partial (34 x 12 and
+// 34 x 15 threads): its missing lanes count as exited, which the full-mask
+// shuffles allow, but a lane whose partner is missing reads an undefined
+// value, so that warp's fold -- ring cells only, whose sums are zero -- is
+// not stored.  nthreads: the CTA's threads.
 __device__ __forceinline__ void monitor_fold(MonSlot* slots, MonLane& l, int x, int y,
-                                             int tid) {
+                                             int tid, int nthreads) {
   constexpr unsigned full = 0xffffffffu;
   float2 q[4] = {l.p[0], l.p[1], make_float2(l.p[2].x, l.p[0].x * (float)x),
                  make_float2(l.p[0].x * (float)y, l.p[2].y)};
@@ -601,7 +605,7 @@ __device__ __forceinline__ void monitor_fold(MonSlot* slots, MonLane& l, int x, 
   // the four counts of a warp (at most 32 kMonFold each) fit their bytes
   const unsigned cnt = __reduce_add_sync(full, l.cnt);
   const unsigned ub = __reduce_max_sync(full, __float_as_uint(l.u2));
-  if ((tid & 31) == 0) {
+  if ((tid & 31) == 0 && (tid & ~31) + 32 <= nthreads) {
     MonSlot& w = slots[tid >> 5];
     // compensated adds for the colour masses, whose drift is what a monitor
     // watches; plain FP32 adds for the rest
@@ -894,7 +898,7 @@ __device__ __forceinline__ bool tma_chunk(const T* __restrict__ src, T* __restri
     }
     if constexpr (MON)
       if ((k - 2) % kMonFold == kMonFold - 1 || k == K - 1)
-        monitor_fold(mon, ml, g.cx, g.cy, tid);
+        monitor_fold(mon, ml, g.cx, g.cy, tid, TW * BY);
   }
   return true;
 }
