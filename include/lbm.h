@@ -527,6 +527,19 @@ long long lbm_test_live_allocations(void);
    in a normal build).  Synchronises ctx's stream. */
 lbm_status lbm_test_index_checks(lbm_ctx *ctx, int *checked, unsigned *out_of_range);
 
+/* Testing hook of the surrogate GEMM's launch plan; the paper has no
+   counterpart.  For a product of lbm_gemm_bf16 with K <= 256 (the
+   persistent warp-specialised kernel), out = {form, columns per CTA,
+   column blocks, CTAs per column block} as a launch on a GPU with `sms`
+   SMs would take them: form 1 is the TMA-fed form (A K-contiguous, sa_k =
+   1, with a row stride sa_m a multiple of 4 floats, a_aligned16 nonzero
+   for a 16-byte aligned A, M >= 128 and K >= 32; it falls back to form 0
+   when the driver cannot encode the tensor map), form 0 the register
+   form.  Host only: no CUDA call.  LBM_ERR_ARG for out == NULL, M, N, K
+   or sms out of range (N <= 256, K <= 256). */
+lbm_status lbm_test_gemm_plan(int M, int N, int K, long long sa_m, long long sa_k,
+                              int a_aligned16, int sms, int out[4]);
+
 /* Text of the last error on ctx (never NULL; "" after success).  With
    ctx == NULL, the last error of a failed lbm_create in this thread. */
 const char *lbm_last_error(const lbm_ctx *ctx);

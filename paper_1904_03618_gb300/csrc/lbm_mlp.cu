@@ -1127,16 +1127,39 @@ static int sm_count() {
   return sms;
 }
 
-// k_gemm_ws launch: the column block is halved (down to 16 columns) while
-// the row tiles alone leave SMs idle; the grid's x extent is at most the SMs
-// per column block (persistent CTAs over the row tiles).
+// k_gemm_ws launch plan (host only).  The TMA form wherever A's layout
+// allows one: K-contiguous rows whose stride is a 16-byte multiple, a
+// 16-byte aligned base, at least one full row tile and one 32-k box.  The
+// column block is halved (down to 16 columns) while the row tiles alone
+// leave SMs idle, and in the TMA form until it is at most kTmaBn; the
+// grid's x extent is at most the SMs per column block (persistent CTAs over
+// the row tiles).
+struct WsPlan {
+  bool ta;
+  int bn, nt, gx;  // columns per CTA, column blocks, CTAs per column block
+};
+static WsPlan ws_plan(int M, int N, int K, long long sa_m, long long sa_k, bool a_aligned16,
+                      int sms) {
+  WsPlan p;
+  p.ta = sa_k == 1 && (sa_m & 3) == 0 && a_aligned16 && M >= kM && K >= 32;
+  const int n_mma = (N + 15) / 16 * 16;
+  const int mt = (M + kM - 1) / kM;
+  int nt = 1;
+  while ((long long)mt * nt * 2 <= sms && n_mma / (nt * 2) >= 16) nt *= 2;
+  if (p.ta)
+    while ((n_mma + nt - 1) / nt > kTmaBn) nt *= 2;
+  p.bn = ((n_mma + nt - 1) / nt + 15) / 16 * 16;
+  p.nt = (N + p.bn - 1) / p.bn;
+  p.gx = sms / p.nt;
+  if (p.gx < 1) p.gx = 1;
+  if (p.gx > mt) p.gx = mt;
+  return p;
+}
+
 // The A map of the TMA form: FP32 A seen as K x M (K innermost), boxes of
 // 32 x 128 with the 128-byte swizzle; rows and columns beyond A read as
 // zero.
 static bool encode_a_map(const GemmArgs& g, CUtensorMap* map) {
-  if (g.sa_k != 1 || (g.sa_m & 3) != 0 || (reinterpret_cast<uintptr_t>(g.A) & 15u) != 0 ||
-      g.M < kM || g.K < 32)
-    return false;
   EncodeTiledFn encode = nullptr;
   if (tensor_map_encoder(&encode) != cudaSuccess) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)g.K, (cuuint64_t)g.M};
@@ -1168,24 +1191,16 @@ static cudaError_t launch_ws_form(const GemmArgs& g, const CUtensorMap& amap, in
 
 static cudaError_t launch_gemm_ws(GemmArgs g, cudaStream_t s) {
   const int sms = sm_count();
-  const int n_mma = (g.N + 15) / 16 * 16;
-  const int mt = (g.M + kM - 1) / kM;
-  // the TMA form wherever A's layout allows one (K-contiguous rows of a
-  // 16-byte multiple, at least one full row tile and one 32-k box)
+  const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15u) == 0;
+  WsPlan p = ws_plan(g.M, g.N, g.K, g.sa_m, g.sa_k, aligned, sms);
   CUtensorMap amap;
   memset(&amap, 0, sizeof(amap));
-  const bool ta = encode_a_map(g, &amap);
-  int nt = 1;
-  while ((long long)mt * nt * 2 <= sms && n_mma / (nt * 2) >= 16) nt *= 2;
-  if (ta)
-    while ((n_mma + nt - 1) / nt > kTmaBn) nt *= 2;
-  g.ws_bn = ((n_mma + nt - 1) / nt + 15) / 16 * 16;
-  nt = (g.N + g.ws_bn - 1) / g.ws_bn;
-  int gx = sms / nt;
-  if (gx < 1) gx = 1;
-  if (gx > mt) gx = mt;
+  if (p.ta && !encode_a_map(g, &amap))  // no tensor map: the register form
+    p = ws_plan(g.M, g.N, g.K, g.sa_m, g.sa_k, false, sms);
+  g.ws_bn = p.bn;
   g.splits = 1;
-  return ta ? launch_ws_form<true>(g, amap, gx, nt, s) : launch_ws_form<false>(g, amap, gx, nt, s);
+  return p.ta ? launch_ws_form<true>(g, amap, p.gx, p.nt, s)
+              : launch_ws_form<false>(g, amap, p.gx, p.nt, s);
 }
 
 cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
@@ -1579,6 +1594,18 @@ extern "C" lbm_status lbm_mlp_train_step(lbm_mlp* m, const float* x, const float
              "cudaMemcpyAsync");
     return check_err(m);
   }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_test_gemm_plan(int M, int N, int K, long long sa_m, long long sa_k,
+                                         int a_aligned16, int sms, int out[4]) {
+  if (!out || M < 1 || N < 1 || N > kNMax || K < 1 || K > ws::kKMax || sms < 1)
+    return LBM_ERR_ARG;
+  const WsPlan p = ws_plan(M, N, K, sa_m, sa_k, a_aligned16 != 0, sms);
+  out[0] = p.ta ? 1 : 0;
+  out[1] = p.bn;
+  out[2] = p.nt;
+  out[3] = p.gx;
   return LBM_OK;
 }
 

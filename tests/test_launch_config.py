@@ -98,3 +98,53 @@ def test_query_equals_the_live_context(kw):
     finally:
         lat.close()
     assert lbm.lbm_default_fused_config(p, sms) == live
+
+
+# lbm_test_gemm_plan: the surrogate GEMM's launch plan for K <= 256, worked
+# out by hand from the rule (TMA form for K-contiguous A with a 16-byte
+# multiple row stride, a 16-byte aligned base, M >= 128 and K >= 32; column
+# block halved while 2 * row tiles * blocks <= SMs and the halves keep 16
+# columns, and in the TMA form until it is <= 128; CTAs per block = SMs /
+# blocks, at most the row tiles).
+# (M, N, K, sa_m, sa_k, aligned, sms) -> (form, columns, blocks, CTAs per block)
+GEMM_PLANS = [
+    ((65536, 256, 256, 256, 1, 1, 152), (1, 128, 2, 76)),       # forward H W
+    ((65536, 256, 256, 256, 1, 1, 148), (1, 128, 2, 74)),
+    ((65536, 256, 5, 5, 1, 1, 152), (0, 256, 1, 152)),          # input layer: 20-byte rows
+    ((65536, 256, 256, 1, 65536, 1, 152), (0, 256, 1, 152)),    # A stored K x M
+    ((65536, 256, 256, 256, 1, 0, 152), (0, 256, 1, 152)),      # A not 16-byte aligned
+    ((300, 200, 130, 130, 1, 1, 152), (0, 32, 7, 3)),           # row stride 130 floats
+    ((100, 64, 64, 64, 1, 1, 152), (0, 16, 4, 1)),              # less than one row tile
+    ((256, 256, 256, 256, 1, 1, 152), (1, 16, 16, 2)),          # a batch-256 training layer
+    ((40001, 200, 252, 252, 1, 1, 152), (1, 112, 2, 76)),       # ragged M, N and K
+]
+
+
+@pytest.mark.parametrize("args,want", GEMM_PLANS)
+def test_gemm_launch_plan(args, want):
+    import ctypes
+    L = lbm._lib
+    L.lbm_test_gemm_plan.argtypes = [ctypes.c_int] * 3 + [ctypes.c_longlong] * 2 + \
+        [ctypes.c_int] * 2 + [ctypes.POINTER(ctypes.c_int)]
+    L.lbm_test_gemm_plan.restype = ctypes.c_int
+    out = (ctypes.c_int * 4)()
+    assert L.lbm_test_gemm_plan(*args, out) == lbm.LBM_OK
+    assert tuple(out) == want
+    form, bn, nt, gx = want
+    M, N = args[0], args[1]
+    assert bn % 16 == 0 and (bn <= 128 if form else bn <= 256)
+    assert (nt - 1) * bn < N <= nt * bn                 # every column in one block
+    assert nt * gx <= args[6] and gx <= (M + 127) // 128
+
+
+def test_gemm_launch_plan_rejects_bad_arguments():
+    import ctypes
+    L = lbm._lib
+    L.lbm_test_gemm_plan.argtypes = [ctypes.c_int] * 3 + [ctypes.c_longlong] * 2 + \
+        [ctypes.c_int] * 2 + [ctypes.POINTER(ctypes.c_int)]
+    L.lbm_test_gemm_plan.restype = ctypes.c_int
+    out = (ctypes.c_int * 4)()
+    for M, N, K, sms in [(0, 16, 16, 152), (16, 0, 16, 152), (16, 257, 16, 152),
+                         (16, 16, 0, 152), (16, 16, 257, 152), (16, 16, 16, 0)]:
+        assert L.lbm_test_gemm_plan(M, N, K, K, 1, 1, sms, out) == lbm.LBM_ERR_ARG
+    assert L.lbm_test_gemm_plan(16, 16, 16, 16, 1, 1, 152, None) == lbm.LBM_ERR_ARG
