@@ -528,15 +528,18 @@ long long lbm_test_live_allocations(void);
 lbm_status lbm_test_index_checks(lbm_ctx *ctx, int *checked, unsigned *out_of_range);
 
 /* Testing hook of the surrogate GEMM's launch plan; the paper has no
-   counterpart.  For a product of lbm_gemm_bf16 with K <= 256 (the
-   persistent warp-specialised kernel), out = {form, columns per CTA,
-   column blocks, CTAs per column block} as a launch on a GPU with `sms`
-   SMs would take them: form 1 is the TMA-fed form (A K-contiguous, sa_k =
-   1, with a row stride sa_m a multiple of 4 floats, a_aligned16 nonzero
-   for a 16-byte aligned A, M >= 128 and K >= 32; it falls back to form 0
-   when the driver cannot encode the tensor map), form 0 the register
-   form.  Host only: no CUDA call.  LBM_ERR_ARG for out == NULL, M, N, K
-   or sms out of range (N <= 256, K <= 256). */
+   counterpart.  out = {form, columns per CTA, column blocks or K splits,
+   CTAs per column block or per split} as lbm_gemm_bf16 would launch the
+   product on a GPU with `sms` SMs.  K <= 256 (the persistent
+   warp-specialised kernel, B resident): form 1 is the TMA-fed form (A
+   K-contiguous, sa_k = 1, with a row stride sa_m a multiple of 4 floats,
+   a_aligned16 nonzero for a 16-byte aligned A, M >= 128 and K >= 32; it
+   falls back to form 0 when the driver cannot encode the tensor map), form
+   0 the register form.  K > 256 (a plain product, as lbm_gemm_bf16 makes):
+   form 2, the register form split over ceil(K / 256) grid slices of 256
+   K each that add into C; form 3 (zeros after it), the one-tile-per-CTA
+   kernel, when the slices would exceed 65,535.  Host only: no CUDA call.
+   LBM_ERR_ARG for out == NULL, M, N, K or sms out of range (N <= 256). */
 lbm_status lbm_test_gemm_plan(int M, int N, int K, long long sa_m, long long sa_k,
                               int a_aligned16, int sms, int out[4]);
 

@@ -579,10 +579,10 @@ __device__ __forceinline__ void ws_stage(unsigned char* dst, const float* __rest
 // all its threads: the same tasks as ws_stage, numbered across the slices
 // so that each thread keeps several tasks' loads in flight (4 tasks of two
 // 16-byte loads, or 2 tasks of eight).
+template <int NT>
 __device__ __forceinline__ void ws_stage_b(unsigned char* dst, const float* __restrict__ X,
                                            long long s_r, long long s_k, int r0, int R,
                                            int rows, int nk, int K, int t) {
-  constexpr int NT = ws::kThreads;
   const bool aligned = (reinterpret_cast<unsigned long long>(X) & 15u) == 0;
   const size_t slice_bytes = (size_t)rows * 128;
   if (s_k == 1 && aligned && (s_r & 3) == 0) {
@@ -741,6 +741,15 @@ __global__ void __launch_bounds__(TA ? ws::kThreads + 32 : ws::kThreads, 1)
   if constexpr (TA) base += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
   S& sm = *reinterpret_cast<S*>(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // split K (gridDim.z > 1, the register form only): this CTA's products
+  // cover K range [z kKMax, (z + 1) kKMax) and add into the zeroed C
+  const bool split = gridDim.z > 1;
+  if (split) {
+    const int kb = (int)blockIdx.z * ws::kKMax;
+    g.A += (long long)kb * g.sa_k;
+    g.B += (long long)kb * g.sb_k;
+    g.K = min(ws::kKMax, g.K - kb);
+  }
   const int bn = g.ws_bn;
   const int n0 = (int)blockIdx.y * bn;
   const int nk = (g.K + kKT - 1) / kKT;
@@ -805,11 +814,15 @@ __global__ void __launch_bounds__(TA ? ws::kThreads + 32 : ws::kThreads, 1)
       for (int q = 0; q < pre; ++q) issue_a(sm, q);
     }
   }
-  // B (bn x K) and the bias of this column block, staged once by every
-  // thread but the copy warp's
-  if (tid < ws::kThreads)
-    ws_stage_b(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0, g.N, bn, nk,
-               g.K, tid);
+  // B (bn x K) of this column block, staged once: in the TMA form by every
+  // thread but the copy warp's, before the barrier; in the register form
+  // after it by the epilogue and MMA warps only (kBStagers threads, their
+  // own named barrier), while the producer warps already load A
+  constexpr int kBStagers = 32 * (ws::kEpiWarps + 1);
+  if (TA)
+    if (tid < ws::kThreads)
+      ws_stage_b<ws::kThreads>(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0,
+                               g.N, bn, nk, g.K, tid);
   for (int n = tid; n < bn; n += NTH)
     sm.bias[n] = (g.bias && n0 + n < g.N) ? g.bias[n0 + n] : 0.f;
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -818,6 +831,12 @@ __global__ void __launch_bounds__(TA ? ws::kThreads + 32 : ws::kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = sm.tmem_base;
   const unsigned long long wait_ns = mma_wait_limit();
+  if (!TA && (warp < ws::kEpiWarps || warp == ws::kMmaWarp)) {
+    ws_stage_b<kBStagers>(reinterpret_cast<unsigned char*>(sm.b), g.B, g.sb_n, g.sb_k, n0, g.N,
+                          bn, nk, g.K, warp < ws::kEpiWarps ? tid : tid - 32 * ws::kProdWarps);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kBStagers) : "memory");
+  }
 
   if (TA && warp >= ws::kEpiWarps && warp < ws::kMmaWarp) {
     // converters: each FP32 slice (two swizzled 32-k boxes) into the BF16
@@ -1073,7 +1092,16 @@ __global__ void __launch_bounds__(TA ? ws::kThreads + 32 : ws::kThreads, 1)
             }
           }
           float* cp = g.C + (long long)m * g.sc_m + n;
-          if (vec && full4) {
+          if (split) {
+            if (vec && full4) {
+              atomicAdd(reinterpret_cast<float4*>(cp), v);
+            } else {
+              atomicAdd(cp, v.x);
+              if (c + 1 < bn && n + 1 < g.N) atomicAdd(cp + 1, v.y);
+              if (c + 2 < bn && n + 2 < g.N) atomicAdd(cp + 2, v.z);
+              if (c + 3 < bn && n + 3 < g.N) atomicAdd(cp + 3, v.w);
+            }
+          } else if (vec && full4) {
             *reinterpret_cast<float4*>(cp) = v;
           } else {
             cp[0] = v.x;
@@ -1174,7 +1202,7 @@ static bool encode_a_map(const GemmArgs& g, CUtensorMap* map) {
 
 template <bool TA>
 static cudaError_t launch_ws_form(const GemmArgs& g, const CUtensorMap& amap, int gx, int nt,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int splits = 1) {
   static bool attr_dev[kMaxDevices] = {};
   bool& attr = attr_dev[device_slot()];
   const int bytes = TA ? (int)sizeof(WsSmemT) + 1024 : (int)sizeof(WsSmem);
@@ -1184,8 +1212,8 @@ static cudaError_t launch_ws_form(const GemmArgs& g, const CUtensorMap& amap, in
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gemm_ws<TA><<<dim3((unsigned)gx, (unsigned)nt), TA ? ws::kThreads + 32 : ws::kThreads, bytes,
-                  s>>>(g, amap);
+  k_gemm_ws<TA><<<dim3((unsigned)gx, (unsigned)nt, (unsigned)splits),
+                  TA ? ws::kThreads + 32 : ws::kThreads, bytes, s>>>(g, amap);
   return cudaGetLastError();
 }
 
@@ -1203,9 +1231,46 @@ static cudaError_t launch_gemm_ws(GemmArgs g, cudaStream_t s) {
               : launch_ws_form<false>(g, amap, p.gx, p.nt, s);
 }
 
+// Split-K plan (host only) for K > kKMax: the register form with one grid
+// z-slice per kKMax of K, the column block the whole (16-padded) N, and per
+// slice the CTAs the SMs leave for it, at most the row tiles.  Ineligible
+// (splits = 0): more than 65,535 slices.
+static WsPlan ws_split_plan(int M, int N, int K, int sms, int* splits) {
+  WsPlan p;
+  p.ta = false;
+  const long long sl = ((long long)K + ws::kKMax - 1) / ws::kKMax;
+  *splits = sl > 65535 ? 0 : (int)sl;
+  p.bn = (N + 15) / 16 * 16;
+  p.nt = 1;
+  const int mt = (M + kM - 1) / kM;
+  p.gx = *splits > 0 ? sms / *splits : 1;
+  if (p.gx < 1) p.gx = 1;
+  if (p.gx > mt) p.gx = mt;
+  return p;
+}
+
+// K > kKMax without an epilogue (no bias, activation or tanh derivative)
+// into a contiguous C: split K over the persistent kernel, partial
+// products added into C after one memset.
+static cudaError_t launch_gemm_ws_split(GemmArgs g, int splits, const WsPlan& p,
+                                        cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.N, s);
+  if (e != cudaSuccess) return e;
+  CUtensorMap amap;
+  memset(&amap, 0, sizeof(amap));
+  g.ws_bn = p.bn;
+  g.splits = 1;
+  return launch_ws_form<false>(g, amap, p.gx, p.nt, s, splits);
+}
+
 cudaError_t launch_gemm(const GemmArgs& g_in, cudaStream_t s) {
   if (g_in.N < 1 || g_in.N > kNMax || g_in.M < 1 || g_in.K < 1) return cudaErrorInvalidValue;
   if (g_in.K <= ws::kKMax) return launch_gemm_ws(g_in, s);
+  if (!g_in.bias && !g_in.act && !g_in.H && g_in.sc_m == g_in.N) {
+    int splits = 0;
+    const WsPlan p = ws_split_plan(g_in.M, g_in.N, g_in.K, sm_count(), &splits);
+    if (splits > 0) return launch_gemm_ws_split(g_in, splits, p, s);
+  }
   GemmArgs g = g_in;
   g.splits = choose_splits(g);
   static bool attr_dev[kMaxDevices] = {};
@@ -1599,8 +1664,21 @@ extern "C" lbm_status lbm_mlp_train_step(lbm_mlp* m, const float* x, const float
 
 extern "C" lbm_status lbm_test_gemm_plan(int M, int N, int K, long long sa_m, long long sa_k,
                                          int a_aligned16, int sms, int out[4]) {
-  if (!out || M < 1 || N < 1 || N > kNMax || K < 1 || K > ws::kKMax || sms < 1)
-    return LBM_ERR_ARG;
+  if (!out || M < 1 || N < 1 || N > kNMax || K < 1 || sms < 1) return LBM_ERR_ARG;
+  if (K > ws::kKMax) {
+    int splits = 0;
+    const WsPlan p = ws_split_plan(M, N, K, sms, &splits);
+    if (splits == 0) {
+      out[0] = 3;  // the one-tile-per-CTA kernel
+      out[1] = out[2] = out[3] = 0;
+      return LBM_OK;
+    }
+    out[0] = 2;
+    out[1] = p.bn;
+    out[2] = splits;
+    out[3] = p.gx;
+    return LBM_OK;
+  }
   const WsPlan p = ws_plan(M, N, K, sa_m, sa_k, a_aligned16 != 0, sms);
   out[0] = p.ta ? 1 : 0;
   out[1] = p.bn;

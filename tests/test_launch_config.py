@@ -117,6 +117,13 @@ GEMM_PLANS = [
     ((100, 64, 64, 64, 1, 1, 152), (0, 16, 4, 1)),              # less than one row tile
     ((256, 256, 256, 256, 1, 1, 152), (1, 16, 16, 2)),          # a batch-256 training layer
     ((40001, 200, 252, 252, 1, 1, 152), (1, 112, 2, 76)),       # ragged M, N and K
+    # K > 256: the register form split into slices of 256 K (columns, slices,
+    # CTAs per slice = SMs / slices, at most the row tiles)
+    ((256, 256, 65536, 1, 256, 1, 152), (2, 256, 256, 1)),      # weight gradient H^T dZ
+    ((257, 256, 1000, 1000, 1, 1, 152), (2, 256, 4, 3)),
+    ((300, 200, 300, 300, 1, 1, 152), (2, 208, 2, 3)),
+    ((4096, 64, 512, 512, 1, 1, 152), (2, 64, 2, 32)),
+    ((16, 16, 65535 * 256 + 1, 1, 16, 1, 152), (3, 0, 0, 0)),   # too many slices
 ]
 
 
@@ -131,8 +138,14 @@ def test_gemm_launch_plan(args, want):
     assert L.lbm_test_gemm_plan(*args, out) == lbm.LBM_OK
     assert tuple(out) == want
     form, bn, nt, gx = want
-    M, N = args[0], args[1]
-    assert bn % 16 == 0 and (bn <= 128 if form else bn <= 256)
+    M, N, K = args[0], args[1], args[2]
+    if form == 3:
+        return
+    assert bn % 16 == 0 and (bn <= 128 if form == 1 else bn <= 256)
+    if form == 2:                                       # nt: the K slices
+        assert (nt - 1) * 256 < K <= nt * 256 and bn >= N
+        assert gx == max(1, min(args[6] // nt, (M + 127) // 128))
+        return
     assert (nt - 1) * bn < N <= nt * bn                 # every column in one block
     assert nt * gx <= args[6] and gx <= (M + 127) // 128
 
@@ -145,6 +158,6 @@ def test_gemm_launch_plan_rejects_bad_arguments():
     L.lbm_test_gemm_plan.restype = ctypes.c_int
     out = (ctypes.c_int * 4)()
     for M, N, K, sms in [(0, 16, 16, 152), (16, 0, 16, 152), (16, 257, 16, 152),
-                         (16, 16, 0, 152), (16, 16, 257, 152), (16, 16, 16, 0)]:
+                         (16, 16, 0, 152), (16, 16, 16, 0)]:
         assert L.lbm_test_gemm_plan(M, N, K, K, 1, 1, sms, out) == lbm.LBM_ERR_ARG
     assert L.lbm_test_gemm_plan(16, 16, 16, 16, 1, 1, 152, None) == lbm.LBM_ERR_ARG
