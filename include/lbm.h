@@ -440,7 +440,7 @@ lbm_status lbm_inplace_read(const lbm_params *p, const float *f, int parity,
    sum((y - t)^2) / (batch * n_out) and Adam (beta1 0.9, beta2 0.999, eps
    1e-8).  It maps impact parameters to a spreading-factor series and screens
    parameter sweeps; the lattice Boltzmann step remains its fallback and the
-   judge of its error.  The paper has no counterpart.  Every matrix product
+   reference its error is measured against.  The paper has no counterpart.  Every matrix product
    runs on the 5th-generation tensor cores (tcgen05, BF16 operands, FP32
    accumulation); weights, gradients, Adam moments and activations are FP32.
    Parameters are one flat FP32 vector, layer by layer: W_l (fan_in x

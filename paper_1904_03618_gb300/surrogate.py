@@ -8,8 +8,8 @@ floor -- the cells of the first fluid layer where rho^N > 0, counted by
 lbm_batch_footprint -- gives D = 2 sqrt(area / pi) at K sample times.  The
 network (dense tanh layers, BF16 tensor-core GEMMs with FP32 accumulation,
 Adam on MSE; lbm_mlp_*) is trained on the GPU by the library's own forward
-and backward kernels.  The solver stays the fallback and the judge: the
-held-out error is measured against solver runs the network never saw.
+and backward kernels.  The solver stays the fallback and the reference:
+the held-out error is measured against solver runs the network never saw.
 
 The paper has no counterpart; it fixes only the step that produces the data.
 
