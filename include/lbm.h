@@ -475,8 +475,12 @@ const char *lbm_mlp_last_error(const lbm_mlp *m);
 /* The network's matrix product on its own: C(m, n) = sum_k A(m, k) B(k, n)
    with A(m, k) = A[m*sa_m + k*sa_k], B(k, n) = B[k*sb_k + n*sb_n],
    C[m*sc_m + n]; device pointers, operands rounded to BF16, FP32
-   accumulation, 1 <= N <= 256.  err (device int) is set to 1 if a bounded
-   wait gave up.  Queued on cuda_stream. */
+   accumulation, 1 <= N <= 256.  For K > 256 the product is split over K
+   and the partial sums are added into C with atomics (C is zeroed first),
+   so the FP32 summation order, and with it the last bits of C, can differ
+   from call to call; within the bound K 2^-24 sum_k |A(m, k) B(k, n)| of
+   the exact product of the rounded operands either way.  err (device int)
+   is set to 1 if a bounded wait gave up.  Queued on cuda_stream. */
 lbm_status lbm_gemm_bf16(const float *A, long long sa_m, long long sa_k,
                          const float *B, long long sb_k, long long sb_n,
                          float *C, long long sc_m, int M, int N, int K,
