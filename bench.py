@@ -576,7 +576,8 @@ def storage_variants_rt(lbm, dev, pd, rR, rB, u, args):
 
 def droplet_variants(lbm, dev, args):
     """The 128^3 moving droplet (density ratio 10): FP32, FP16 and BF16
-    deviation storage and the FP32 in-place step (one population array),
+    deviation storage and the FP32 and FP16 in-place step (one population
+    array),
     device-resident MLUPS and the fraction of the HBM roofline at the
     algorithmic 304 / 152 bytes per cell update; 16-bit and in-place drift
     against the FP32 run after `variant_steps` steps."""
@@ -605,34 +606,37 @@ def droplet_variants(lbm, dev, args):
         else:
             rec.update(err_vs_f32_after_steps=steps, **_drift(got, ref))
         out[storage] = rec
-    # the in-place step: one FP32 population array (AA access pattern), a
-    # phase-field pass and the in-place collision per step; its fraction is
-    # taken at the 304 B/cell of the method, not at the 488 B/cell the two
-    # passes move
-    p = lbm.make_params(storage="f32", kernel=args.kernel, **pd)
-    s = torch.cuda.Stream(dev)
-    ip = lbm.InPlaceLattice(p, device=dev, stream=s)
-    ip.init_fields(rR, rB, u)
-    ip.step(args.warmup)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(timed):
-        ip.step(1)
-    e1.record(s)
-    s.synchronize()
-    ms = e0.elapsed_time(e1) / timed
-    ip.init_fields(rR, rB, u)
-    ip.step(steps)
-    got = ip.moments()
-    ip.close()
-    mlups = N / (ms * 1e-3) / 1e6
-    out["inplace_f32"] = {
-        "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
-        "roofline_frac": mlups * 1e6 * 304 / (peak * 1e9),
-        "algorithmic_bytes_per_cell": 304, "moved_bytes_per_cell": 488,
-        "memory_bytes_per_cell": 168, "gpu_launches_per_step": 2,
-        "err_vs_f32_after_steps": steps, **_drift(got, ref)}
+    # the in-place step: one population array (AA access pattern), FP32 and
+    # FP16 deviation storage, a phase-field pass and the in-place collision
+    # per step; its fraction is taken at the method's 304 / 152 B/cell, not
+    # at the 488 / 260 B/cell the two passes move
+    for storage in ("f32", "f16"):
+        p = lbm.make_params(storage=storage, kernel=args.kernel, **pd)
+        p.ref_R, p.ref_B = storage_references(storage, pd, rR, rB)
+        s = torch.cuda.Stream(dev)
+        ip = lbm.InPlaceLattice(p, device=dev, stream=s)
+        ip.init_fields(rR, rB, u)
+        ip.step(args.warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(timed):
+            ip.step(1)
+        e1.record(s)
+        s.synchronize()
+        ms = e0.elapsed_time(e1) / timed
+        ip.init_fields(rR, rB, u)
+        ip.step(steps)
+        got = ip.moments()
+        ip.close()
+        mlups = N / (ms * 1e-3) / 1e6
+        vb = ALG_BYTES[storage] // 2  # bytes of one cell's 38 values
+        out["inplace_" + storage] = {
+            "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
+            "roofline_frac": mlups * 1e6 * ALG_BYTES[storage] / (peak * 1e9),
+            "algorithmic_bytes_per_cell": ALG_BYTES[storage],
+            "moved_bytes_per_cell": 3 * vb + 32, "memory_bytes_per_cell": vb + 16,
+            "gpu_launches_per_step": 2, "err_vs_f32_after_steps": steps, **_drift(got, ref)}
     return out
 
 

@@ -387,14 +387,19 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
 /* ---- In-place step (AA access pattern) ----------------------------------
    The step of Eq. 1-2 (the same collision, forcing, perturbation,
    recolouring, walls, wetting rule and BGK option as lbm_step) on ONE
-   population array, float32 [2][19][N] (k = 0 red, 1 blue; cell = (z * ny
-   + y) * nx + x), updated in place: 152 bytes per cell plus a 16-byte
-   scratch, against 304 for the two buffers of a context.  Cell indices are
+   population array [2][19][N] (k = 0 red, 1 blue; cell = (z * ny + y) * nx
+   + x) of p->storage's values -- FP32 populations, or FP16 / BF16
+   deviations f - ref_k phi_i^k from the colour's rest state, with the
+   offsets of a context of the same parameters (p->ref_R, p->ref_B) --
+   updated in place: 152 bytes per cell in FP32 (76 in 16 bits) plus a
+   16-byte scratch, against 304 (152) for the two buffers of a context.  Cell indices are
    64-bit: nx*ny*nz is limited by device memory only (ny, nz <= 65535).  The
    paper streams between two arrays; this is a deployment variant with the
    same result up to FP32 rounding.
    A state has a parity.  Even (0): f[k][i][x] = f_i^k(x, t), after
-   streaming, the layout of lbm_set_f / lbm_get_f.  Odd (1): f[k][opp(i)][x]
+   streaming, the layout of lbm_set_f / lbm_get_f (stored as above).  Each
+   stored value keeps its direction's offset in both parities (opposite
+   directions share an offset).  Odd (1): f[k][opp(i)][x]
    = f_i^{k,+}(x, t - 1), the post-collision value before streaming, so
    f_i^k(x, t) is found at f[k][opp(i)][x - e_i], or at f[k][i][x] where
    x - e_i lies beyond a wall; e_i in the order of Eq. 5, where opp pairs
@@ -404,8 +409,9 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
    Each step runs two kernels: the phase field (rho^N, Qbar) of every cell
    into the scratch, then the in-place collision (488 bytes of memory
    traffic per cell, against 304 for lbm_step's fused kernel).
-   Moving plates (wall = 2) are rejected with LBM_ERR_ARG.  p->storage and
-   p->kernel are ignored (FP32).  All arrays are device memory of the
+   Moving plates (wall = 2) are rejected with LBM_ERR_ARG; p->kernel is
+   ignored.  f must be aligned to its value size.  All arrays are device
+   memory of the
    current GPU owned by the caller; work is queued on cuda_stream (a cudaStream_t, NULL = legacy
    default stream) and the calls return without waiting.  Errors
    (LBM_ERR_ARG, LBM_ERR_CUDA) are described by lbm_last_error(NULL) of the
@@ -416,13 +422,19 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const float *f_in,
    u (u_x, u_y, u_z planes, 3N floats) written into f as an even state.  f
    must not overlap the fields. */
 lbm_status lbm_inplace_init(const lbm_params *p, const float *rho_R,
-                            const float *rho_B, const float *u, float *f,
+                            const float *rho_B, const float *u, void *f,
                             void *cuda_stream);
+
+/* An even state from FP32 populations f_in[2][19][N] (the layout of
+   lbm_set_f), stored in p->storage's format (16-bit: the deviations rounded
+   to nearest even).  f must not overlap f_in. */
+lbm_status lbm_inplace_set(const lbm_params *p, const float *f_in, void *f,
+                           void *cuda_stream);
 
 /* nsteps >= 0 time steps of the state f of the given parity (0 or 1), in
    place.  scratch: N float4 (16 bytes per cell, 16-byte aligned), not
    overlapping f; its contents on entry are ignored. */
-lbm_status lbm_step_inplace(const lbm_params *p, float *f, int parity,
+lbm_status lbm_step_inplace(const lbm_params *p, void *f, int parity,
                             int nsteps, void *scratch, void *cuda_stream);
 
 /* Reads the state f of the given parity: f_out (may be NULL) receives
@@ -430,7 +442,7 @@ lbm_status lbm_step_inplace(const lbm_params *p, float *f, int parity,
    (each may be NULL) the moments of lbm_moments (u with the half-force
    shift of Eq. 4).  At least one output; none may overlap f or another
    output. */
-lbm_status lbm_inplace_read(const lbm_params *p, const float *f, int parity,
+lbm_status lbm_inplace_read(const lbm_params *p, const void *f, int parity,
                             float *f_out, float *rho_R, float *rho_B,
                             float *u, void *cuda_stream);
 

@@ -163,6 +163,8 @@ _lib.lbm_step_noalloc.restype = ctypes.c_int
 _lib.lbm_inplace_init.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, _fp, _fp,
                                   ctypes.c_void_p]
 _lib.lbm_inplace_init.restype = ctypes.c_int
+_lib.lbm_inplace_set.argtypes = [ctypes.POINTER(LbmParams), _fp, _fp, ctypes.c_void_p]
+_lib.lbm_inplace_set.restype = ctypes.c_int
 _lib.lbm_step_inplace.argtypes = [ctypes.POINTER(LbmParams), _fp, ctypes.c_int, ctypes.c_int,
                                   _fp, ctypes.c_void_p]
 _lib.lbm_step_inplace.restype = ctypes.c_int
@@ -182,7 +184,7 @@ EXPORTED = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments",
             "lbm_get_planes", "lbm_set_planes",
             "lbm_set_fused_config", "lbm_get_fused_config", "lbm_default_fused_config",
             "lbm_step_noalloc",
-            "lbm_inplace_init", "lbm_step_inplace", "lbm_inplace_read",
+            "lbm_inplace_init", "lbm_inplace_set", "lbm_step_inplace", "lbm_inplace_read",
             "lbm_create_batch", "lbm_num_cases", "lbm_batch_init_fields",
             "lbm_batch_moments", "lbm_batch_diagnostics", "lbm_batch_get_f",
             "lbm_batch_set_f", "lbm_batch_footprint", "lbm_set_graphs", "lbm_mlp_create", "lbm_mlp_num_params",
@@ -420,10 +422,17 @@ def _inplace_check(st):
 
 
 def lbm_inplace_init(params: LbmParams, rho_R, rho_B, u, f, stream=None):
-    """Equilibrium populations of the fields into f (float32 [2][19][N],
-    device) as an even in-place state; see include/lbm.h."""
+    """Equilibrium populations of the fields into f ([2][19][N] values of
+    params.storage, device) as an even in-place state; see include/lbm.h."""
     _inplace_check(_lib.lbm_inplace_init(ctypes.byref(params), _addr(rho_R), _addr(rho_B),
                                          _addr(u), _addr(f), _stream_arg(stream)))
+
+
+def lbm_inplace_set(params: LbmParams, f_in, f, stream=None):
+    """An even in-place state f from float32 populations f_in [2][19][N]
+    (stored in params.storage's format)."""
+    _inplace_check(_lib.lbm_inplace_set(ctypes.byref(params), _addr(f_in), _addr(f),
+                                        _stream_arg(stream)))
 
 
 def lbm_step_inplace(params: LbmParams, f, parity, nsteps, scratch, stream=None):
@@ -581,8 +590,9 @@ class Lattice:
 
 class InPlaceLattice:
     """One lattice stepped in place (one population array, AA access
-    pattern): 168 bytes of device memory per cell instead of 304, no limit
-    on the cell count beyond memory.  FP32; walls 0 or 1."""
+    pattern): 168 bytes of device memory per cell instead of 304 in FP32 (92
+    instead of 152 in FP16 / BF16 deviation storage), no limit on the cell
+    count beyond memory.  Walls 0 or 1."""
 
     def __init__(self, params: LbmParams, device=None, stream=None):
         self.device = torch.device(device or "cuda")
@@ -591,7 +601,9 @@ class InPlaceLattice:
         self.N = params.nx * params.ny * params.nz
         with torch.cuda.device(self.device):
             self.stream = stream or torch.cuda.current_stream(self.device)
-        self.f = torch.empty((2, 19) + self.shape, dtype=torch.float32, device=self.device)
+        dt = {STORAGE["f32"]: torch.float32, STORAGE["f16"]: torch.float16,
+              STORAGE["bf16"]: torch.bfloat16}[params.storage]
+        self.f = torch.empty((2, 19) + self.shape, dtype=dt, device=self.device)
         self.scratch = torch.empty((self.N, 4), dtype=torch.float32, device=self.device)
         # used on self.stream: the allocator must not reuse the memory while
         # work queued there may still touch it
@@ -620,11 +632,11 @@ class InPlaceLattice:
         self.stream.synchronize()
 
     def set_f(self, f):
-        """Sets an even state: f_i^k(x, t) as float32 [2][19][N]."""
+        """Sets an even state: f_i^k(x, t) as float32 [2][19][N] (stored in
+        the lattice's storage format)."""
         ft = self._t(f).reshape(self.f.shape)
         self._after_caller()
-        with torch.cuda.stream(self.stream):
-            self.f.copy_(ft)
+        lbm_inplace_set(self.params, ft, self.f, self.stream.cuda_stream)
         self.parity = 0
         self.stream.synchronize()
 
@@ -633,7 +645,7 @@ class InPlaceLattice:
                                        self.stream.cuda_stream)
 
     def get_f(self):
-        out = torch.empty_like(self.f)
+        out = torch.empty(self.f.shape, dtype=torch.float32, device=self.device)
         self._after_caller()
         lbm_inplace_read(self.params, self.f, self.parity, f_out=out,
                          stream=self.stream.cuda_stream)

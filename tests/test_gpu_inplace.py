@@ -6,7 +6,9 @@ read back through lbm_inplace_read -- against the oracle stepped once from
 the GPU's previous state, element by element, within the FP32 bar of the
 other parity tests (relative L-infinity 1e-5 per step); the moments; the
 odd layout as include/lbm.h documents it, read from the raw array; the
-context API on the same input; periodic, walled, gravity, wetting and BGK
+context API on the same input; FP16 / BF16 deviation storage against the
+oracle with the same storage rounding and against the context's 16-bit
+run; periodic, walled, gravity, wetting and BGK
 lattices and lattices of one to three cells along an axis; and the
 Rayleigh-Taylor lattice of the paper's Sec. IV.C at 512 x 512 x 2048 (537 M
 cells, beyond the two-buffer kernels' 226 M-cell limit) on sampled cells
@@ -20,6 +22,7 @@ import torch
 
 import oracle
 from paper_1904_03618_gb300 import lbm, params as P, workloads as wl
+from storage_emulation import offsets, stored
 from test_gpu_fullsize import _axis_window
 
 pytestmark = pytest.mark.gpu
@@ -178,6 +181,62 @@ def test_inplace_rejects_bad_device_arguments():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_inplace_read(p, f, 0, f_out=f[4:])
     assert "overlaps" in str(ei.value)
+
+
+# ---------------------------------------------------------------------------
+# FP16 / BF16 deviation storage in place.
+
+@pytest.mark.parametrize("storage,bars", [("f16", dict(emu=5e-4, ctx=5e-4)),
+                                          ("bf16", dict(emu=4e-3, ctx=4e-3))])
+def test_inplace_16_bit_storage(storage, bars):
+    """The in-place step on FP16 / BF16 deviations (the blue background
+    offset by rho_in_B phi_i^B, red stored as is): set_f rounds exactly as
+    the storage model of the two-buffer context does, and after 101 steps
+    (ending on an odd state, read back through lbm_inplace_read) the state is
+    within the FP32-versus-FP64 tie flips of the FP64 oracle with the same
+    storage rounding after every step -- several times closer than to the
+    unrounded oracle (on a GB300: FP16 relative L2 2.2e-4 against 1.4e-3,
+    BF16 1.7e-3 against 1.8e-2) -- and as close to the two-buffer context's
+    16-bit run from the same state.  Walls in z, gravity."""
+    nx, ny, nz = 40, 24, 20
+    pd = _pd(wall=(0, 0, 1), gravity=(0.0, 0.0, -1e-5))
+    rR, rB, u = wl.droplet(nx, ny, nz, 7.0, 3.0, 1.0, velocity=(0.02, -0.01, 0.0),
+                           noise=1e-3, seed=11)
+    op = oracle.params_from(dict(nx=nx, ny=ny, nz=nz, **pd))
+    ref_R, ref_B = 0.0, pd["rho_in_B"]
+    off = offsets(pd, ref_R, ref_B)
+    f0 = np.asarray(oracle.init(op, rR, rB, u), dtype=np.float32).astype(np.float64)
+    p = lbm.make_params(nx, ny, nz, storage=storage, **pd)
+    p.ref_R, p.ref_B = ref_R, ref_B
+    steps = 101
+
+    lat = lbm.InPlaceLattice(p, device=DEV)
+    lat.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    held = lat.get_f().double().cpu().numpy()
+    lat.step(steps)
+    assert lat.parity == 1
+    got = lat.get_f().double().cpu().numpy()
+    lat.close()
+    emu = stored(f0, storage, off)
+    assert np.array_equal(held, emu)
+    plain = emu.copy()
+    for _ in range(steps):
+        emu = stored(oracle.step(op, emu, 1), storage, off)
+    plain = oracle.step(op, plain, steps)
+    norm = np.linalg.norm(emu)
+    e_emu = np.linalg.norm(got - emu) / norm
+    e_plain = np.linalg.norm(got - plain) / norm
+    assert e_emu <= bars["emu"] and e_emu <= 0.25 * e_plain, (e_emu, e_plain)
+
+    ctx = lbm.Lattice(p, device=DEV)
+    ctx.set_f(torch.tensor(f0, dtype=torch.float32, device=DEV))
+    ctx.step(steps)
+    two = ctx.get_f().double().cpu().numpy()
+    ctx.close()
+    e_ctx = np.linalg.norm(got - two) / norm
+    print(storage, "in place: rel L2 vs emulated %.3e, vs unrounded %.3e, vs context %.3e"
+          % (e_emu, e_plain, e_ctx))
+    assert e_ctx <= bars["ctx"]
 
 
 # ---------------------------------------------------------------------------

@@ -21,38 +21,10 @@ import torch
 
 import oracle
 from paper_1904_03618_gb300 import lbm, workloads as wl
+from storage_emulation import offsets, stored
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
-
-
-def rest_weights(alpha):
-    """phi_i^k of the rest state (Eq. 5 at u = 0): alpha on the rest
-    population, (1 - alpha) / 12 on the axes, (1 - alpha) / 24 on the
-    diagonals (directions 1-6 and 7-18 of the oracle's order)."""
-    w = np.empty(19)
-    w[0] = alpha
-    w[1:7] = (1.0 - alpha) / 12.0
-    w[7:] = (1.0 - alpha) / 24.0
-    return w
-
-
-def to_bf16(x32):
-    b = x32.view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
-    return b.astype(np.uint32).view(np.float32)
-
-
-def stored(f, storage, off):
-    """The populations (2, 19, ...) as the GPU holds them; off[k][i] are the
-    FP32 offsets ref_k phi_i^k."""
-    out = np.empty_like(f)
-    for k in range(2):
-        o = off[k].reshape(19, 1, 1, 1)
-        d = f[k].astype(np.float32) - o
-        r = d.astype(np.float16).astype(np.float32) if storage == "f16" else to_bf16(d)
-        out[k] = (r + o).astype(np.float64)
-    return out
 
 
 @pytest.mark.parametrize("storage,bars", [
@@ -69,8 +41,7 @@ def test_storage_rounding_matches_the_emulated_oracle(storage, bars):
                            seed=11)
     p = oracle.params_from(pd)
     ref_R, ref_B = 0.0, pd["rho_in_B"]  # the blue background is offset
-    off = np.stack([(ref_R * rest_weights(pd["alpha_R"])).astype(np.float32),
-                    (ref_B * rest_weights(pd["alpha_B"])).astype(np.float32)])
+    off = offsets(pd, ref_R, ref_B)
     f0 = np.asarray(oracle.init(p, rR, rB, u), dtype=np.float32).astype(np.float64)
 
     params = lbm.make_params(storage=storage, **pd)
