@@ -372,16 +372,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(GemmArgs g) {
 
 // ---------------------------------------------------------------------------
 // Warp-specialised persistent GEMM for products whose whole B fits in shared
-// memory (K <= 256): every forward layer and every dZ W^T of the network.
+// memory (K <= 256): every forward layer and every dZ W^T of the network;
+// and, with one grid z-slice per 256 of K whose partial tiles are added into
+// a zeroed C, the plain products with K > 256 (weight gradients).
 //   - B (bn columns x K, BF16) is staged once per CTA and stays resident;
 //   - a CTA walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 //     of its column block blockIdx.y;
-//   - the FP32 A slices (128 x 64) reach a 4-stage BF16 ring (full / empty
+//   - the FP32 A slices (128 x 64) reach a BF16 ring (full / empty
 //     mbarriers) one of two ways.  Where A's rows are K-contiguous with a
 //     16-byte multiple stride (the TMA form, column blocks <= 128), one
-//     thread issues tensor copies of each slice into a two-stage FP32 ring
-//     and 8 converter warps round it to BF16; elsewhere 8 producer warps
-//     load, round and store the slices themselves;
+//     thread issues tensor copies of each slice into a three-stage FP32
+//     ring and 8 converter warps round it into a two-stage BF16 ring;
+//     elsewhere (the register form) 8 producer warps load, round and store
+//     the slices themselves into a four-stage ring, starting while the
+//     epilogue and MMA warps stage B;
 //   - one thread issues the tcgen05.mma of each slice into one of two TMEM
 //     accumulators and commits them to the slice's empty barrier, and the
 //     finished tile to its accumulator's full barrier;
