@@ -181,6 +181,21 @@ def test_inplace_rejects_bad_device_arguments():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_inplace_read(p, f, 0, f_out=f[4:])
     assert "overlaps" in str(ei.value)
+    with pytest.raises(lbm.LbmError) as ei:      # the FP32 input inside the state
+        lbm.lbm_inplace_set(p, f[4:], f)
+    assert "overlap" in str(ei.value)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_inplace_set(p, host, scratch.repeat(10))
+    assert "device memory" in str(ei.value)
+    p16 = lbm.make_params(8, 8, 8, storage="f16")
+    raw = torch.zeros(38 * 512 + 8, dtype=torch.float16, device=DEV)
+    fin = torch.zeros(38 * 512, device=DEV)
+    with pytest.raises(lbm.LbmError) as ei:      # 16-bit values one byte off
+        lbm._inplace_check(lbm._lib.lbm_inplace_set(
+            lbm.ctypes.byref(p16), fin.data_ptr(), raw.data_ptr() + 1, None))
+    assert "misaligned" in str(ei.value)
+    lbm.lbm_inplace_set(p16, fin, raw[2:])       # 2-byte aligned 16-bit values: accepted
+    torch.cuda.synchronize()
 
 
 # ---------------------------------------------------------------------------
